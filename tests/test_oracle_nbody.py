@@ -1,0 +1,114 @@
+"""Pins of the oracle's n-body step (arXiv 2302.08251, Sec. 5, Fig. 2).
+
+The paper shows the loop structure of the update (all j for each i, then store
+the velocity) and names the move phase; the interaction is the softened
+Newtonian one of the original LLAMA n-body (a reading, G = 1).  Pinned by
+physics that holds whatever way the sum is written: the inverse-square law far
+from the softening length, the linear core inside it, attraction, momentum
+conservation, symmetry, the move using the new velocity, and independence from
+the mapping the particles are read through.
+"""
+import numpy as np
+import pytest
+
+from paper_2302_08251_gb300 import synth
+from helpers import AFFINE, oracle_view
+
+EPS, DT = 0.01, 1e-4
+
+
+def particles_from(pos, vel, mass):
+    pos = np.asarray(pos, np.float32).reshape(-1, 3)
+    vel = np.asarray(vel, np.float32).reshape(-1, 3)
+    mass = np.asarray(mass, np.float32)
+    return [pos[:, 0], pos[:, 1], pos[:, 2], vel[:, 0], vel[:, 1], vel[:, 2], mass]
+
+
+def step(fields, mapping={"kind": "soa_mb"}, eps=EPS, dt=DT):
+    v = oracle_view(synth.PARTICLE, mapping, fields)
+    return v.nbody_step(eps, dt)
+
+
+def test_single_particle_keeps_its_velocity_and_drifts():
+    f = particles_from([0.25, -0.5, 0.125], [1.0, 2.0, -4.0], [0.75])
+    pos, vel = step(f)
+    assert np.array_equal(vel[0], [1.0, 2.0, -4.0])
+    np.testing.assert_allclose(pos[0], [0.25 + DT, -0.5 + 2 * DT, 0.125 - 4 * DT],
+                               rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("r", [1.0, 2.0, 16.0])
+def test_far_field_is_the_inverse_square_law(r):
+    # two bodies at rest, distance r >> eps: |dv| = dt * m_other / r^2
+    eps = 1e-6
+    m = np.float32(0.5)
+    f = particles_from([0, 0, 0, r, 0, 0], [0] * 6, [1.0, m])
+    pos, vel = step(f, eps=eps, dt=1.0)
+    np.testing.assert_allclose(vel[0], [m / r**2, 0, 0], rtol=1e-9)
+    np.testing.assert_allclose(vel[1], [-1.0 / r**2, 0, 0], rtol=1e-9)
+
+
+def test_inside_the_softening_length_the_pull_grows_linearly():
+    # Plummer softening: for r << eps the pull tends to m r / eps^3
+    eps = 1.0
+    for r in [1e-3, 2e-3]:
+        f = particles_from([0, 0, 0, 0, r, 0], [0] * 6, [1.0, 1.0])
+        _, vel = step(f, eps=eps, dt=1.0)
+        assert vel[0][1] == pytest.approx(r, rel=1e-5)
+
+
+def test_bodies_attract():
+    f = particles_from([-0.5, 0.1, 0, 0.5, 0.1, 0], [0] * 6, [1.0, 1.0])
+    pos, vel = step(f)
+    assert vel[0][0] > 0 and vel[1][0] < 0
+    assert pos[0][0] > -0.5 and pos[1][0] < 0.5
+
+
+def test_momentum_is_conserved():
+    n = 200
+    f = synth.particles(n, seed=13)
+    _, vel = step(f)
+    m = f[6].astype(np.float64)
+    v0 = np.stack(f[3:6], axis=1).astype(np.float64)
+    dp = (m[:, None] * (vel - v0)).sum(axis=0)
+    scale = (m[:, None] * np.abs(vel - v0)).sum(axis=0)
+    assert np.all(np.abs(dp) <= 1e-12 * scale)
+
+
+def test_symmetric_neighbours_cancel():
+    pts = [0, 0, 0]
+    for axis in range(3):
+        for s in (1, -1):
+            p = [0.0, 0.0, 0.0]
+            p[axis] = 0.5 * s
+            pts += p
+    f = particles_from(pts, [0.0] * 21, [1.0] * 7)
+    _, vel = step(f)
+    assert np.all(vel[0] == 0.0)
+
+
+def test_move_uses_the_updated_velocity():
+    n = 50
+    f = synth.particles(n, seed=21)
+    pos, vel = step(f)
+    p0 = np.stack(f[0:3], axis=1).astype(np.float64)
+    np.testing.assert_allclose(pos, p0 + DT * vel, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("mapping", AFFINE, ids=str)
+def test_result_does_not_depend_on_the_mapping(mapping):
+    n = 37
+    f = synth.particles(n, seed=2)
+    ref = step(f)
+    got = step(f, mapping)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+
+
+def test_partial_range_equals_the_slice_of_the_full_step():
+    n = 64
+    f = synth.particles(n, seed=8)
+    v = oracle_view(synth.PARTICLE, {"kind": "aos"}, f)
+    full = v.nbody_step(EPS, DT)
+    part = v.nbody_step(EPS, DT, 10, 20)
+    assert np.array_equal(full[0][10:20], part[0])
+    assert np.array_equal(full[1][10:20], part[1])
