@@ -1,0 +1,478 @@
+"""Benchmark of the mapping-driven re-layout path on GB300.
+
+One step = one pass over every re-layout row of the hot path, each on its
+full-size synthetic workload, through the C ABI (``llgb_copy``/``pack``/
+``unpack``):
+
+  C3  512x512x512 CFD records {rho,u,v,w,e: f32, flag: i16, id: u16}, u32
+      index type, static inner extents:
+        AoS -> SoA(mb), SoA(mb) -> AoS, SoA(mb) -> AoSoA32,
+        AoSoA32 -> SoA(mb), AoSoA8 -> AoSoA32
+  C1  2^26 INT6 records {a..d: u32, e,f: i32}, b = 12:
+        SoA(mb) -> BitpackIntSoA (pack), BitpackIntSoA -> SoA(mb) (unpack)
+  C2  2^25 MIXED_F records {x,y,z: f64, w: f32}, N(0, 1e3):
+        SoA(mb) -> BitpackFloatSoA(E8,M23), its unpack,
+        SoA(mb) -> Bytesplit(SoA), SoA(mb) -> ChangeType(f64->f32, SoA)
+
+value = algorithmic bytes (every source blob byte read + every destination
+blob byte written) of the step / device time of the step, in GB/s.  Every
+input is larger than L2, so no flush is needed between steps.  The n-body
+consumer (65,536 particles) is timed in its own loop and reported under
+"nbody".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs the whole per-GPU workload on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "re-layout GB/s (read+write) vs HBM peak"
+PROFILE = os.path.join(ROOT, "profiles", "copy_kernel_relayout_suite.md")
+
+
+# ------------------------------------------------------------ workload --
+
+def rows_spec():
+    from paper_2302_08251_gb300 import synth
+    c3 = dict(record=synth.CFD, n=512 ** 3, ext=(512, 512, 512), itype="u32",
+              static=(False, True, True), fields="cfd")
+    c1 = dict(record=synth.INT6, n=1 << 26, ext=(1 << 26,), itype="u32", static=None,
+              fields="int6")
+    c2 = dict(record=synth.MIXED_F, n=1 << 25, ext=(1 << 25,), itype="u32", static=None,
+              fields="mixed_f")
+    soa = {"kind": "soa_mb"}
+    aos = {"kind": "aos"}
+    a32 = {"kind": "aosoa", "lanes": 32}
+    a8 = {"kind": "aosoa", "lanes": 8}
+    bp12 = {"kind": "bitpack_int", "bits": 12}
+    bf = {"kind": "bitpack_float", "exp": 8, "man": 23}
+    bs = {"kind": "bytesplit", "inner": soa}
+    ct = {"kind": "changetype", "ct": [("f64", "f32")], "inner": soa}
+    return [
+        ("C3 AoS->SoA", c3, aos, soa),
+        ("C3 SoA->AoS", c3, soa, aos),
+        ("C3 SoA->AoSoA32", c3, soa, a32),
+        ("C3 AoSoA32->SoA", c3, a32, soa),
+        ("C3 AoSoA8->AoSoA32", c3, a8, a32),
+        ("C1 pack b=12", c1, soa, bp12),
+        ("C1 unpack b=12", c1, bp12, soa),
+        ("C2 pack E8M23", c2, soa, bf),
+        ("C2 unpack E8M23", c2, bf, soa),
+        ("C2 bytesplit", c2, soa, bs),
+        ("C2 changetype f64->f32", c2, soa, ct),
+    ]
+
+
+def key(m):
+    return json.dumps(m, sort_keys=True)
+
+
+class Workload:
+    """Device views for every row; sources are seeded and resident in HBM."""
+
+    def __init__(self, device, seed):
+        import torch
+        from paper_2302_08251_gb300 import llgb, synth
+        self.rows = []
+        self.records = {}
+        cache = {}  # (config name, mapping) -> source view
+        for name, cfg, src_map, dst_map in rows_spec():
+            cname = name.split()[0]
+            rec = self.records.setdefault(cname, llgb.Record(cfg["record"]))
+            kw = dict(index_type=cfg["itype"], static=cfg["static"])
+            base_key = (cname, key({"kind": "soa_mb"}))
+            if base_key not in cache:
+                fields = synth.device_fields(cfg["fields"], cfg["n"], seed, device=device)
+                blobs = [f.contiguous().view(torch.uint8) for f in fields]
+                cache[base_key] = llgb.View(rec, {"kind": "soa_mb"}, cfg["ext"], blobs=blobs, **kw)
+            src_key = (cname, key(src_map))
+            if src_key not in cache:
+                v = llgb.View(rec, src_map, cfg["ext"], **kw)
+                llgb.llgb_copy(cache[base_key], v)
+                cache[src_key] = v
+            src = cache[src_key]
+            dst = llgb.View(rec, dst_map, cfg["ext"], **kw)
+            nbytes = sum(src.blob_sizes) + sum(dst.blob_sizes)
+            self.rows.append(dict(name=name, cfg=cfg, src=src, dst=dst, bytes=nbytes,
+                                  src_map=src_map, dst_map=dst_map))
+        torch.cuda.synchronize()
+        self.bytes = sum(r["bytes"] for r in self.rows)
+
+    def step(self, stream, events=None):
+        from paper_2302_08251_gb300 import llgb
+        for k, r in enumerate(self.rows):
+            if events is not None:
+                events[k][0].record(stream)
+            llgb.llgb_copy(r["src"], r["dst"], stream)
+            if events is not None:
+                events[k][1].record(stream)
+
+
+# -------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during timing."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- helpers --
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("copy.cu", "fconv.cuh", "job.h"):
+        with open(os.path.join(ROOT, "paper_2302_08251_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-step DRAM traffic of the copy kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    got = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            got[k.strip()] = v.strip()
+    if got.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(got["dram_bytes_per_step"])
+    except (KeyError, ValueError):
+        return None
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------- CPU oracle --
+
+def oracle_sample(seconds_budget=12.0, seed=1):
+    """Time the oracle copy on a bounded sample of every row: the first
+    records of each workload, sized so the whole sample takes ~10-30 s."""
+    import numpy as np
+    import oracle
+    from paper_2302_08251_gb300 import synth
+    oracle.build()
+    total_bytes, total_time, parts = 0, 0.0, []
+    per_row = seconds_budget / len(rows_spec())
+    for name, cfg, src_map, dst_map in rows_spec():
+        m = 4096
+        while True:
+            rec = cfg["record"]
+            if cfg["fields"] == "int6":
+                fields = synth.int6(m, 12, seed)
+            elif cfg["fields"] == "mixed_f":
+                fields = synth.mixed_f(m, seed)
+            else:
+                fields = synth.cfd(m, seed)
+            base = oracle.OracleView(rec, {"kind": "soa_mb"}, m)
+            for f, col in enumerate(fields):
+                u = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[col.itemsize]
+                base.set_field_values(f, col.view(u).astype(np.uint64))
+            src = oracle.OracleView(rec, src_map, m)
+            base.copy_to(src)
+            dst = oracle.OracleView(rec, dst_map, m)
+            t0 = time.perf_counter()
+            src.copy_to(dst)
+            dt = time.perf_counter() - t0
+            if dt * 4 > per_row or m >= cfg["n"]:
+                break
+            m *= 4
+        nbytes = sum(src.blob_sizes) + sum(dst.blob_sizes)
+        total_bytes += nbytes
+        total_time += dt
+        parts.append(f"{name}: {m} records")
+    return total_bytes / total_time / 1e9, "; ".join(parts), total_time
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(seconds_budget=2.0)
+    vals, times, sample = [], [], ""
+    for _ in range(args.steps):
+        v, sample, t = oracle_sample(seconds_budget=8.0)
+        vals.append(v)
+        times.append(t)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(times) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bytes/int/f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "llama re-layout suite (C1 b=12, C2 E8M23/bytesplit/"
+                                   "changetype, C3 512^3 pairs), bounded sample", "parallelism": "none"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- main --
+
+def run_gpu(args):
+    import torch
+    from paper_2302_08251_gb300 import build, llgb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("gloo")
+    build.build()
+    llgb.lib()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    wl = Workload(device, seed=2302082510 + rank)
+    stream = torch.cuda.current_stream()
+    nrows = len(wl.rows)
+    for _ in range(args.warmup):
+        wl.step(stream)
+    barrier()
+
+    events = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nrows)]
+              for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        wl.step(stream, events[s])
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [[events[s][k][0].elapsed_time(events[s][k][1]) for k in range(nrows)]
+                 for s in range(args.steps)]
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = wl.bytes * world / (ms_per_step * 1e-3) / 1e9
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    kernel_ms = sum(sum(x) for x in launch_ms) / args.steps
+    achieved = wl.bytes / (kernel_ms * 1e-3) / 1e9
+    rows_out = {}
+    for k, r in enumerate(wl.rows):
+        ms = statistics.median(launch_ms[s][k] for s in range(args.steps))
+        gbs = r["bytes"] / (ms * 1e-3) / 1e9
+        rows_out[r["name"]] = {"bytes": r["bytes"], "ms": round(ms, 4), "GB/s": round(gbs, 1),
+                               "frac": round(gbs / hbm, 4)}
+    traffic = profiled_traffic()
+
+    # n-body consumer (65,536 particles through AoS / SoA / AoSoA32 views)
+    nbody = nbody_bench(device, args) if rank == 0 else None
+    # end to end through host buffers
+    e2e = e2e_bench(wl, stream, args) if rank == 0 else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bytes/int/f64->f32", "data": "synthetic (seeded), resident in HBM",
+            "config": {"workload": "llama re-layout suite: C3 512^3 CFD AoS<->SoA, SoA<->AoSoA32, "
+                                   "AoSoA8->AoSoA32 (u32, static inner extents); C1 2^26 INT6 "
+                                   "BitpackInt b=12 pack+unpack; C2 2^25 MIXED_F BitpackFloat "
+                                   "E8M23 pack+unpack, Bytesplit, ChangeType f64->f32",
+                       "bytes_per_step": wl.bytes, "l2": "inputs > L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                         "kernel": "llgb::copy_kernel", "spec_frac_8tbs": round(achieved / 8000.0, 4)},
+            "rows": rows_out,
+            "clocks": clk,
+            "gpu_launches": nrows * args.steps,
+            "e2e": e2e,
+            "nbody": nbody,
+        }
+        if not args.no_cpu_baseline:
+            v, sample, _ = oracle_sample()
+            line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1,
+                                    "kind": "oracle", "sample": sample}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def nbody_bench(device, args):
+    import torch
+    from paper_2302_08251_gb300 import llgb, synth
+    rec = llgb.Record(synth.PARTICLE)
+    n = 65536
+    fields = synth.device_fields("particle", n, 7, device=device)
+    base = llgb.View(rec, {"kind": "soa_mb"}, (n,), blobs=[f.view(torch.uint8) for f in fields])
+    out = {}
+    for name, m in (("AoS", {"kind": "aos"}), ("SoA", {"kind": "soa_mb"}),
+                    ("AoSoA32", {"kind": "aosoa", "lanes": 32})):
+        v = llgb.View(rec, m, (n,))
+        llgb.llgb_copy(base, v)
+        for _ in range(2):
+            llgb.llgb_nbody_step(v, 0.01, 1e-4)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(3, args.steps)
+        a.record()
+        for _ in range(reps):
+            llgb.llgb_nbody_step(v, 0.01, 1e-4)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        flops = 20.0 * n * n
+        out[name] = {"ms_per_step": round(ms, 4), "TFLOP/s": round(flops / (ms * 1e-3) / 1e12, 2)}
+    # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop x clock (2.07 GHz max)
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    best = max(x["TFLOP/s"] for x in out.values())
+    return {"n": n, "flop_per_interaction": 20, "views": out,
+            "roofline": {"bound": "alu", "achieved": best, "peak": round(peak, 1),
+                         "unit": "TFLOP/s", "frac": round(best / peak, 4),
+                         "peak_source": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz (nominal)"}}
+
+
+def e2e_bench(wl, stream, args):
+    """The same step through host buffers: every row's source blobs go
+    host->device from pinned memory, the copy runs, the destination blobs
+    come back device->host, all inside the timed region."""
+    import torch
+    from paper_2302_08251_gb300 import llgb
+    hosts = {}
+    for r in wl.rows:
+        sid = id(r["src"])
+        if sid not in hosts:
+            hosts[sid] = [torch.empty(b.numel(), dtype=torch.uint8, pin_memory=True)
+                          for b in r["src"].blobs]
+            for h, b in zip(hosts[sid], r["src"].blobs):
+                h.copy_(b)
+    out_max = max(max(b.numel() for b in r["dst"].blobs) for r in wl.rows)
+    host_out = torch.empty(out_max, dtype=torch.uint8, pin_memory=True)
+    h2d = sum(sum(b.numel() for b in r["src"].blobs) for r in wl.rows)
+    d2h = sum(sum(b.numel() for b in r["dst"].blobs) for r in wl.rows)
+
+    def step():
+        for r in wl.rows:
+            for h, b in zip(hosts[id(r["src"])], r["src"].blobs):
+                b.copy_(h, non_blocking=True)
+            llgb.llgb_copy(r["src"], r["dst"], stream)
+            for b in r["dst"].blobs:
+                host_out[:b.numel()].copy_(b, non_blocking=True)
+    step()
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"value": round(wl.bytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
+            "steps": reps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,255 @@
+/*
+ * llgb.h -- C ABI of the GB300 library for mapping-driven record layouts.
+ *
+ * The operations follow the problem statement of arXiv 2302.08251 ("Updates on
+ * the Low-Level Abstraction of Memory Access"):
+ *   - a record dimension of nested fields, flattened depth-first into leaves
+ *     (Sec. 1, Fig. 1 concepts);
+ *   - array extents, each static or dynamic, with a chosen index type used for
+ *     index and offset arithmetic (Sec. 2);
+ *   - an exchangeable mapping with its parameters (Sec. 1; new mappings Sec. 3;
+ *     AoS / SoA multi-blob / AoSoA named in Sec. 5);
+ *   - a view = mapping + blobs (Sec. 1, Sec. 2);
+ *   - the layout-aware copy between views (Sec. 1), of which packing into and
+ *     unpacking from the bit-packed mappings are special cases (Sec. 3);
+ *   - a consumer that reads and writes records through a view: one all-pairs
+ *     n-body step (Sec. 5, Fig. 2).
+ *
+ * Conventions for every call:
+ *   - Device pointers are plain CUDA device addresses; host pointers are plain
+ *     process addresses.  No PyTorch or CUDA types appear in the signatures:
+ *     a stream is passed as `void*` holding a cudaStream_t (NULL = legacy
+ *     default stream).
+ *   - The library never allocates or frees blob memory.  The caller owns every
+ *     blob and keeps it alive until the work queued on it has finished.
+ *   - Calls return an llgb_status.  Host-side validation errors are returned
+ *     before anything is queued.  Work is queued asynchronously on the given
+ *     stream; errors raised by kernels (a wait that ran out of time) are
+ *     recorded in a device status word read back by llgb_device_status().
+ *   - llgb_last_error() returns a thread-local, human-readable message for the
+ *     last failing call on the calling thread.
+ *   - No C++ exception crosses this boundary.
+ */
+#ifndef LLGB_H
+#define LLGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status -- */
+
+typedef int32_t llgb_status;
+
+enum {
+    LLGB_OK = 0,
+    LLGB_ERR_INVALID_ARG = 1,    /* null pointer, bad enum, bad parameter           */
+    LLGB_ERR_INDEX_OVERFLOW = 2, /* n or an offset does not fit the index type      */
+    LLGB_ERR_MISMATCH = 3,       /* views differ in record or record count          */
+    LLGB_ERR_UNSUPPORTED = 4,    /* valid request that this library does not run    */
+    LLGB_ERR_CUDA = 5,           /* a CUDA runtime call failed                      */
+    LLGB_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                   */
+    LLGB_ERR_OOM = 7,            /* host or device allocation failed                */
+    LLGB_ERR_UNBOUND = 8         /* view used before llgb_view_bind                 */
+};
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* llgb_last_error(void);
+
+/* Library version string. */
+const char* llgb_version(void);
+
+/* ---------------------------------------------------------- leaf types -- */
+
+enum {
+    LLGB_U8 = 0, LLGB_U16, LLGB_U32, LLGB_U64,
+    LLGB_I8, LLGB_I16, LLGB_I32, LLGB_I64,
+    LLGB_F16, LLGB_BF16, LLGB_F32, LLGB_F64
+};
+
+/* -------------------------------------------------------------- record -- */
+
+/* One leaf of the record dimension.  `path` names the leaf by its tags from
+ * the root, dot separated ("pos.x"); leaves are given in depth-first order
+ * (Sec. 1: records are addressed by tags; nested records flatten to leaves). */
+typedef struct llgb_field_desc {
+    const char* path;
+    int32_t type; /* LLGB_U8 .. LLGB_F64 */
+} llgb_field_desc;
+
+typedef struct llgb_record llgb_record;
+
+/* Create a record dimension from `n` leaves (1 <= n <= 64).  Paths are copied.
+ * Errors: INVALID_ARG for n out of range, a null/empty/duplicate path or an
+ * unknown type.  *out is owned by the caller; release with
+ * llgb_record_destroy. */
+llgb_status llgb_record_create(const llgb_field_desc* leaves, int32_t n,
+                               llgb_record** out);
+void llgb_record_destroy(llgb_record* rec);
+
+/* Number of leaves. */
+int32_t llgb_record_leaf_count(const llgb_record* rec);
+
+/* Bytes of one record: packed = sum of leaf sizes; aligned = C struct rules
+ * (each leaf aligned to its size, the record padded to the largest). */
+llgb_status llgb_record_size(const llgb_record* rec, int32_t packed, uint64_t* out);
+
+/* ------------------------------------------------------------- extents -- */
+
+/* Index types (Sec. 2: the type used for all index and offset arithmetic). */
+enum {
+    LLGB_IDX_I16 = 0, LLGB_IDX_U16, LLGB_IDX_I32, LLGB_IDX_U32,
+    LLGB_IDX_I64, LLGB_IDX_U64
+};
+
+/* Array extents (Sec. 2).  rank 1..4; ext[d] holds every extent, static or
+ * not; bit d of static_mask marks extent d as known at compile time, in which
+ * case kernels specialised for that value are used where they exist.  Records
+ * are linearised row-major (last index fastest).  n = product of extents. */
+typedef struct llgb_extents {
+    int32_t rank;
+    int32_t index_type;   /* LLGB_IDX_* */
+    uint32_t static_mask;
+    uint32_t reserved;    /* must be 0 */
+    uint64_t ext[4];
+} llgb_extents;
+
+/* ------------------------------------------------------------- mapping -- */
+
+enum {
+    LLGB_MAP_AOS = 0,          /* array of structs                             */
+    LLGB_MAP_SOA_SB,           /* struct of arrays, single blob                */
+    LLGB_MAP_SOA_MB,           /* struct of arrays, one blob per leaf          */
+    LLGB_MAP_AOSOA,            /* arrays of structs of arrays, `lanes` lanes    */
+    LLGB_MAP_BITPACK_INT,      /* BitpackIntSoA: b-bit integers (Sec. 3)       */
+    LLGB_MAP_BITPACK_FLOAT,    /* BitpackFloatSoA: (1+E+M)-bit floats (Sec. 3)  */
+    LLGB_MAP_BYTESPLIT,        /* Bytesplit over `inner` (Sec. 3)              */
+    LLGB_MAP_CHANGETYPE        /* ChangeType over `inner` (Sec. 3)             */
+};
+
+#define LLGB_MAX_CT 4
+
+/* Mapping descriptor.  Fields not used by `kind` are ignored.
+ *  AOS:           aos_packed = 0 aligned (C struct rules, default) / 1 packed.
+ *  SOA_SB:        sub-arrays in leaf order in one blob, each starting at a
+ *                 multiple of subarray_align (0 = the leaf's own size).
+ *  SOA_MB:        blob k holds leaf k as a plain array.
+ *  AOSOA:         blocks of `lanes` records; inside a block leaf k's lanes are
+ *                 contiguous, leaves packed in order; the last block is whole
+ *                 and its unused lanes are zero.
+ *  BITPACK_INT:   integral leaves only; leaf k stored with field_bits[k] (or
+ *                 `bits`) bits: the low b bits of the two's complement on
+ *                 store, zero/sign extension on load; one LSB-first stream of
+ *                 little-endian 32-bit words per leaf.
+ *  BITPACK_FLOAT: floating-point leaves only; leaf k stored as sign, E =
+ *                 field_exp[k] (or exp_bits) exponent bits, M = field_man[k]
+ *                 (or man_bits) mantissa bits, IEEE-style, round to nearest
+ *                 even, overflow to INF, NaN kept quiet; one stream per leaf.
+ *                 2 <= E <= 11, 1 <= M <= 52, 1+E+M <= 64.
+ *  BYTESPLIT:     each leaf becomes size-of-leaf u8 leaves (its little-endian
+ *                 bytes) forwarded to `inner`.
+ *  CHANGETYPE:    leaves of type ct_from[k] are stored as ct_to[k] (floating
+ *                 point types) through `inner`; round to nearest even on store,
+ *                 exact or RNE conversion back on load.
+ * `inner` must be an AOS, SOA_* or AOSOA mapping. */
+typedef struct llgb_mapping_desc {
+    int32_t kind;
+    int32_t aos_packed;
+    uint64_t subarray_align;
+    uint64_t lanes;
+    int32_t bits;
+    int32_t exp_bits;
+    int32_t man_bits;
+    int32_t n_ct;
+    int32_t ct_from[LLGB_MAX_CT];
+    int32_t ct_to[LLGB_MAX_CT];
+    const int32_t* field_bits;
+    const int32_t* field_exp;
+    const int32_t* field_man;
+    const struct llgb_mapping_desc* inner;
+} llgb_mapping_desc;
+
+/* ---------------------------------------------------------------- view -- */
+
+typedef struct llgb_view llgb_view;
+
+/* Plan a view of `rec` with extents `ext` and mapping `map` (both copied).
+ * Computes the blob count and sizes; binds no memory.
+ * Errors: INVALID_ARG (bad descriptor), INDEX_OVERFLOW (n or the largest
+ * byte offset does not fit the index type), UNSUPPORTED (a nesting of
+ * wrappers or a leaf count the GPU planner does not handle).
+ * The view keeps a reference to nothing the caller passed. */
+llgb_status llgb_view_create(const llgb_record* rec, const llgb_extents* ext,
+                             const llgb_mapping_desc* map, llgb_view** out);
+void llgb_view_destroy(llgb_view* view);
+
+int32_t llgb_view_blob_count(const llgb_view* view);
+uint64_t llgb_view_blob_size(const llgb_view* view, int32_t k);
+uint64_t llgb_view_record_count(const llgb_view* view);
+
+/* Bind `n` device blobs (n = llgb_view_blob_count, each at least
+ * llgb_view_blob_size bytes, each 16-byte aligned).  The view borrows the
+ * pointers; the caller keeps ownership.  Errors: INVALID_ARG (count, null or
+ * misaligned pointer). */
+llgb_status llgb_view_bind(llgb_view* view, void* const* dev_ptrs, int32_t n);
+
+/* ---------------------------------------------------------------- copy -- */
+
+/* Layout-aware copy (Sec. 1): for every record i < n and leaf f, the logical
+ * value of (i, f) is loaded through src's mapping and stored through dst's;
+ * every byte of every dst blob that no (i, f) owns is written with zero.
+ * Both views must have the same record (leaf types) and the same n; index
+ * types may differ.  src and dst blobs must not overlap.  Queued on `stream`.
+ * Errors: MISMATCH, UNBOUND, UNSUPPORTED, CUDA. */
+llgb_status llgb_copy(const llgb_view* src, llgb_view* dst, void* stream);
+
+/* Pack: copy from a plain (AoS/SoA/AoSoA) view into a BITPACK_* view.
+ * Unpack: the reverse.  Same semantics as llgb_copy; the kinds are checked
+ * (Sec. 3: values are packed on store and unpacked on load). */
+llgb_status llgb_pack(const llgb_view* plain, llgb_view* packed, void* stream);
+llgb_status llgb_unpack(const llgb_view* packed, llgb_view* plain, void* stream);
+
+/* Launch shape of the copy kernel.  All zero = the library's choice. */
+typedef struct llgb_launch_config {
+    int32_t tile_records;   /* records per tile; multiple of 128 and of lanes */
+    int32_t src_stages;     /* source tiles in flight per CTA (1..8)           */
+    int32_t dst_stages;     /* destination tiles in flight per CTA (1..4)      */
+    int32_t threads;        /* threads per CTA: 128, 256, 512 or 1024          */
+    int32_t ctas_per_sm;    /* resident CTAs per SM (1..8)                      */
+    int32_t reserved[3];    /* must be 0                                       */
+} llgb_launch_config;
+
+/* The launch shape llgb_copy uses for this pair (after autotuning, if any). */
+llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst,
+                             llgb_launch_config* out);
+
+/* llgb_copy with an explicit launch shape.  Errors as llgb_copy, plus
+ * INVALID_ARG for a shape that does not fit the pair. */
+llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst,
+                           const llgb_launch_config* cfg, void* stream);
+
+/* -------------------------------------------------------------- n-body -- */
+
+/* One all-pairs n-body step (Sec. 5, Fig. 2) on a view whose record is the
+ * particle {pos.x, pos.y, pos.z, vel.x, vel.y, vel.z, mass} (7 f32 leaves, in
+ * this order) under an AOS, SOA_SB, SOA_MB or AOSOA mapping.  Update: for
+ * every i, v_i += dt * sum_j m_j (p_j - p_i) / (|p_j - p_i|^2 + eps^2)^(3/2),
+ * j over all particles; then move: p_i += dt * v_i.  FP32 arithmetic; the
+ * result bits do not depend on the mapping.  Queued on `stream` (two
+ * kernels).  Errors: INVALID_ARG, UNBOUND, UNSUPPORTED, CUDA. */
+llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream);
+
+/* -------------------------------------------------------------- status -- */
+
+/* Read the device status word that kernels set when a bounded wait gives up
+ * (LLGB_ERR_TIMEOUT); 0 when none did.  Synchronizes the current device.
+ * reset != 0 clears the word. */
+llgb_status llgb_device_status(int32_t* code, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -228,6 +228,17 @@ class OracleView:
         return pos, vel
 
 
+def blob_sizes(record, mapping: dict, n: int) -> list:
+    """Blob sizes of n records under `mapping`, without allocating them."""
+    lib = _load()
+    keep: list = []
+    types = (ctypes.c_int32 * len(record))(*[TYPE_ID[t] for _, t in record])
+    m = _to_c_mapping(mapping, keep)
+    nb = lib.orc_blob_count(types, len(record), ctypes.byref(m))
+    return [int(lib.orc_blob_size(types, len(record), ctypes.byref(m), int(n), k))
+            for k in range(nb)]
+
+
 def copy(src: OracleView, dst: OracleView) -> None:
     src.copy_to(dst)
 

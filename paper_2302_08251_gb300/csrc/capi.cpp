@@ -1,0 +1,369 @@
+// capi.cpp -- the C ABI declared in include/llgb.h.
+//
+// Host-side validation, planning and launch.  No exception leaves this file:
+// every entry point catches and turns failures into an llgb_status with a
+// thread-local message.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "job.h"
+#include "kernels.h"
+#include "llgb.h"
+#include "plan.h"
+
+struct llgb_view {
+    llgb::ViewPlan plan;
+    std::vector<void*> ptrs;
+    bool bound = false;
+};
+
+using namespace llgb;
+
+namespace {
+
+thread_local std::string t_error;
+
+llgb_status fail(llgb_status s, const std::string& msg)
+{
+    t_error = msg;
+    return s;
+}
+
+llgb_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(LLGB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceInfo {
+    int sms = 0;
+    int max_smem = 0;
+};
+
+DeviceInfo device_info()
+{
+    static std::mutex mu;
+    static std::vector<DeviceInfo> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return {};
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1);
+    if (cache[dev].sms == 0) {
+        cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&cache[dev].max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return cache[dev];
+}
+
+bool same_record(const ViewPlan& a, const ViewPlan& b) { return a.types == b.types; }
+
+// Shared memory a launch shape needs for a pair (JobDesc planned at `tile`).
+size_t smem_needed(const JobDesc& J, const llgb_launch_config& c)
+{
+    return copy_shared_header_bytes() + (size_t)c.src_stages * J.src.img_bytes +
+           (size_t)c.dst_stages * J.dst.img_bytes + J.code_bytes;
+}
+
+bool valid_threads(int t) { return t == 128 || t == 256 || t == 512 || t == 1024; }
+
+// The library's default launch shape for a pair.
+llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
+{
+    const DeviceInfo dev = device_info();
+    const int sms = dev.sms > 0 ? dev.sms : 152;
+    const size_t smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
+    llgb_launch_config c{};
+    c.threads = 512;
+    c.ctas_per_sm = 1;
+    c.src_stages = 4;
+    c.dst_stages = 2;
+    const uint32_t q = tile_quantum(src->plan, dst->plan);
+    if (q == 0) return fail(LLGB_ERR_UNSUPPORTED, "AoSoA lane counts give no usable tile size");
+    double sb = 0, db = 0;
+    uint32_t cb = 0;
+    bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
+    const double per_rec = std::max(std::max(sb, db), 1.0);
+    uint64_t tile = (uint64_t)(24576.0 / per_rec) / q * q;
+    if (tile < q) tile = q;
+    // Small views: keep at least two tiles per SM where the records allow.
+    const uint64_t n = src->plan.n;
+    const uint64_t want = (n + 2ull * sms - 1) / (2ull * sms);
+    const uint64_t small = std::max<uint64_t>(q, (want + q - 1) / q * q);
+    tile = std::min(tile, small);
+    std::vector<void*> none_s(src->plan.blob_sizes.size(), nullptr), none_d(dst->plan.blob_sizes.size(), nullptr);
+    static thread_local JobDesc probe;
+    std::string why;
+    for (;;) {
+        if (plan_job(src->plan, none_s, dst->plan, none_d, (uint32_t)tile, &probe, &why) != LLGB_OK)
+            return fail(LLGB_ERR_UNSUPPORTED, why);
+        if (smem_needed(probe, c) <= smem_cap) break;
+        if (c.src_stages > 2) {
+            --c.src_stages;
+            continue;
+        }
+        if (tile <= q) return fail(LLGB_ERR_UNSUPPORTED, "record too large for a shared-memory tile");
+        tile -= q;
+    }
+    c.tile_records = (int32_t)tile;
+    *out = c;
+    return LLGB_OK;
+}
+
+llgb_status check_pair(const llgb_view* src, const llgb_view* dst)
+{
+    if (!src || !dst) return fail(LLGB_ERR_INVALID_ARG, "null view");
+    if (!same_record(src->plan, dst->plan)) return fail(LLGB_ERR_MISMATCH, "views have different records");
+    if (src->plan.n != dst->plan.n) return fail(LLGB_ERR_MISMATCH, "views have different record counts");
+    if (!src->bound || !dst->bound) return fail(LLGB_ERR_UNBOUND, "view used before llgb_view_bind");
+    return LLGB_OK;
+}
+
+llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_config* cfg_in, void* stream)
+{
+    llgb_status st = check_pair(src, dst);
+    if (st != LLGB_OK) return st;
+    if (src->plan.n == 0) return LLGB_OK;
+    llgb_launch_config c{};
+    if (cfg_in && cfg_in->tile_records != 0) {
+        c = *cfg_in;
+    } else {
+        st = default_config(src, dst, &c);
+        if (st != LLGB_OK) return st;
+    }
+    if (!valid_threads(c.threads) || c.src_stages < 1 || c.src_stages > 8 || c.dst_stages < 1 ||
+        c.dst_stages > 4 || c.ctas_per_sm < 1 || c.ctas_per_sm > 8)
+        return fail(LLGB_ERR_INVALID_ARG, "launch config out of range");
+    static thread_local CopyArgs args;
+    memset(&args, 0, sizeof args);
+    std::string why;
+    st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, (uint32_t)c.tile_records, &args.job, &why);
+    if (st != LLGB_OK) return fail(st, why);
+    const DeviceInfo dev = device_info();
+    const size_t smem = smem_needed(args.job, c);
+    if (dev.max_smem > 0 && smem * (size_t)c.ctas_per_sm > (size_t)dev.max_smem + 1024 * (c.ctas_per_sm - 1))
+        return fail(LLGB_ERR_INVALID_ARG, "launch config needs more shared memory than an SM has");
+    args.table = nullptr;
+    args.tile_start = nullptr;
+    args.njobs = 1;
+    args.total_tiles = args.job.ntiles;
+    args.src_stage_bytes = args.job.src.img_bytes;
+    args.dst_stage_bytes = args.job.dst.img_bytes;
+    args.code_bytes = args.job.code_bytes;
+    args.src_stages = (uint16_t)c.src_stages;
+    args.dst_stages = (uint16_t)c.dst_stages;
+    const int sms = dev.sms > 0 ? dev.sms : 152;
+    const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
+    cudaError_t e = launch_copy(args, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+    return LLGB_OK;
+}
+
+bool is_bitpacked(const llgb_view* v) { return v && v->plan.base >= BASE_BITS_INT; }
+
+}  // namespace
+
+extern "C" {
+
+const char* llgb_last_error(void) { return t_error.c_str(); }
+
+const char* llgb_version(void) { return "llgb 0.1 (sm_103a)"; }
+
+llgb_status llgb_record_create(const llgb_field_desc* leaves, int32_t n, llgb_record** out)
+{
+    try {
+        if (!leaves || !out) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+        if (n < 1 || n > 64) return fail(LLGB_ERR_INVALID_ARG, "leaf count must be 1..64");
+        auto* r = new llgb_record;
+        std::set<std::string> seen;
+        for (int k = 0; k < n; ++k) {
+            if (!leaves[k].path || !leaves[k].path[0] || type_size(leaves[k].type) == 0 ||
+                !seen.insert(leaves[k].path).second) {
+                delete r;
+                return fail(LLGB_ERR_INVALID_ARG, "leaf " + std::to_string(k) + ": bad path or type");
+            }
+            r->paths.emplace_back(leaves[k].path);
+            r->types.push_back(leaves[k].type);
+        }
+        *out = r;
+        return LLGB_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+void llgb_record_destroy(llgb_record* rec) { delete rec; }
+
+int32_t llgb_record_leaf_count(const llgb_record* rec) { return rec ? (int32_t)rec->types.size() : 0; }
+
+llgb_status llgb_record_size(const llgb_record* rec, int32_t packed, uint64_t* out)
+{
+    if (!rec || !out) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+    uint64_t off = 0, max_align = 1;
+    for (int32_t t : rec->types) {
+        const uint64_t s = type_size(t);
+        if (!packed) off = (off + s - 1) / s * s;
+        off += s;
+        max_align = std::max(max_align, s);
+    }
+    *out = packed ? off : (off + max_align - 1) / max_align * max_align;
+    return LLGB_OK;
+}
+
+llgb_status llgb_view_create(const llgb_record* rec, const llgb_extents* ext, const llgb_mapping_desc* map,
+                             llgb_view** out)
+{
+    try {
+        if (!rec || !ext || !map || !out) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+        auto* v = new llgb_view;
+        std::string why;
+        const llgb_status st = plan_view(*rec, *ext, *map, &v->plan, &why);
+        if (st != LLGB_OK) {
+            delete v;
+            return fail(st, why);
+        }
+        v->ptrs.assign(v->plan.blob_sizes.size(), nullptr);
+        *out = v;
+        return LLGB_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+void llgb_view_destroy(llgb_view* view) { delete view; }
+
+int32_t llgb_view_blob_count(const llgb_view* view) { return view ? (int32_t)view->plan.blob_sizes.size() : 0; }
+
+uint64_t llgb_view_blob_size(const llgb_view* view, int32_t k)
+{
+    if (!view || k < 0 || k >= (int32_t)view->plan.blob_sizes.size()) return 0;
+    return view->plan.blob_sizes[k];
+}
+
+uint64_t llgb_view_record_count(const llgb_view* view) { return view ? view->plan.n : 0; }
+
+llgb_status llgb_view_bind(llgb_view* view, void* const* dev_ptrs, int32_t n)
+{
+    if (!view) return fail(LLGB_ERR_INVALID_ARG, "null view");
+    if (n != (int32_t)view->plan.blob_sizes.size()) return fail(LLGB_ERR_INVALID_ARG, "wrong blob count");
+    if (n > 0 && !dev_ptrs) return fail(LLGB_ERR_INVALID_ARG, "null pointer array");
+    for (int k = 0; k < n; ++k) {
+        const uintptr_t p = reinterpret_cast<uintptr_t>(dev_ptrs[k]);
+        if (view->plan.blob_sizes[k] > 0 && (p == 0 || (p & 15u)))
+            return fail(LLGB_ERR_INVALID_ARG, "blob " + std::to_string(k) + " is null or not 16-byte aligned");
+    }
+    for (int k = 0; k < n; ++k) view->ptrs[k] = dev_ptrs[k];
+    view->bound = true;
+    return LLGB_OK;
+}
+
+llgb_status llgb_copy(const llgb_view* src, llgb_view* dst, void* stream)
+{
+    try {
+        return run_copy(src, dst, nullptr, stream);
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst, const llgb_launch_config* cfg, void* stream)
+{
+    try {
+        if (!cfg) return fail(LLGB_ERR_INVALID_ARG, "null launch config");
+        for (int k = 0; k < 3; ++k)
+            if (cfg->reserved[k]) return fail(LLGB_ERR_INVALID_ARG, "reserved fields must be 0");
+        if (cfg->tile_records <= 0) return fail(LLGB_ERR_INVALID_ARG, "tile_records must be positive");
+        return run_copy(src, dst, cfg, stream);
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
+{
+    if (!src || !dst || !out) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+    if (!same_record(src->plan, dst->plan) || src->plan.n != dst->plan.n)
+        return fail(LLGB_ERR_MISMATCH, "views differ in record or count");
+    return default_config(src, dst, out);
+}
+
+llgb_status llgb_pack(const llgb_view* plain, llgb_view* packed, void* stream)
+{
+    if (is_bitpacked(plain) || !is_bitpacked(packed))
+        return fail(LLGB_ERR_INVALID_ARG, "pack needs a plain source and a bit-packed destination");
+    return llgb_copy(plain, packed, stream);
+}
+
+llgb_status llgb_unpack(const llgb_view* packed, llgb_view* plain, void* stream)
+{
+    if (!is_bitpacked(packed) || is_bitpacked(plain))
+        return fail(LLGB_ERR_INVALID_ARG, "unpack needs a bit-packed source and a plain destination");
+    return llgb_copy(packed, plain, stream);
+}
+
+llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream)
+{
+    if (!particles) return fail(LLGB_ERR_INVALID_ARG, "null view");
+    const ViewPlan& p = particles->plan;
+    if (p.types != std::vector<int32_t>(7, LLGB_F32))
+        return fail(LLGB_ERR_INVALID_ARG, "n-body needs the 7-leaf f32 particle record");
+    if (p.wrap != WRAP_NONE || p.base >= BASE_BITS_INT)
+        return fail(LLGB_ERR_UNSUPPORTED, "n-body reads AoS, SoA or AoSoA views");
+    if (!particles->bound) return fail(LLGB_ERR_UNBOUND, "view used before llgb_view_bind");
+    if (p.n > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs n < 2^32");
+    ParticleView v{};
+    v.n = (uint32_t)p.n;
+    int kind = PV_GENERIC;
+    switch (p.base) {
+    case BASE_AOS:  // 28-byte record, aligned and packed alike
+        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[0]) + 4 * f;
+        v.bstride = 28;
+        kind = PV_AOS;
+        break;
+    case BASE_SOA_MB:
+        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[f]);
+        v.bstride = 4;
+        kind = PV_SOA;
+        break;
+    case BASE_SOA_SB:
+        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[0]) + p.sb_base[f];
+        v.bstride = 4;
+        kind = PV_SOA;
+        break;
+    default: {  // AoSoA
+        const uint64_t L = p.lanes;
+        if (L & (L - 1)) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs a power-of-two AoSoA lane count");
+        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[0]) + L * 4 * f;
+        v.bstride = (uint32_t)(28 * L);
+        v.lmask = (uint32_t)(L - 1);
+        while ((1ull << v.lshift) < L) ++v.lshift;
+        kind = L == 32 ? PV_AOSOA32 : PV_GENERIC;
+        break;
+    }
+    }
+    const cudaError_t e = launch_nbody(v, kind, eps, dt, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
+    return LLGB_OK;
+}
+
+llgb_status llgb_device_status(int32_t* code, int32_t reset)
+{
+    if (!code) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+    unsigned v = 0;
+    const cudaError_t e = read_device_status(&v, reset != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "device status");
+    *code = (int32_t)v;
+    return LLGB_OK;
+}
+
+}  // extern "C"

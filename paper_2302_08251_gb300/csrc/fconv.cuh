@@ -1,0 +1,112 @@
+// fconv.cuh -- floating-point format conversion on the device.
+//
+// BitpackFloatSoA and ChangeType (Sec. 3 of the paper) store floats with other
+// exponent/mantissa widths.  The rule implemented (the paper only asks that
+// floating-point semantics be kept as well as possible, NaN and INF included,
+// and that overflow on packing give INF): round to nearest, ties to even;
+// gradual underflow; an exponent that rounds up to all ones is INF; NaN keeps
+// its sign and the top bits of its payload and has its top mantissa bit set.
+//
+// Formats are (E exponent bits, M mantissa bits), IEEE layout sign|exp|man,
+// bias 2^(E-1)-1.  Hardware conversions (cvt.rn) are used for the standard
+// pairs whenever the input is not a NaN; they round the same way.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace llgb {
+
+__device__ __forceinline__ uint64_t low_bits64(int w)
+{
+    return w >= 64 ? ~0ull : ((1ull << w) - 1ull);
+}
+
+// General conversion with integer operations only.
+__device__ __noinline__ uint64_t fconv_general(uint64_t x, int se, int sm, int de, int dm)
+{
+    const uint32_t s_all = (1u << se) - 1u;
+    const uint32_t d_all = (1u << de) - 1u;
+    const uint64_t sign = (x >> (se + sm)) & 1ull;
+    const uint32_t ex = (uint32_t)(x >> sm) & s_all;
+    const uint64_t man = x & low_bits64(sm);
+    const uint64_t out_sign = sign << (de + dm);
+    const uint64_t out_inf = (uint64_t)d_all << dm;
+
+    if (ex == s_all) {
+        if (man == 0) return out_sign | out_inf;
+        const uint64_t pay = dm >= sm ? (man << (dm - sm)) : (man >> (sm - dm));
+        return out_sign | out_inf | pay | (1ull << (dm - 1));
+    }
+    if (ex == 0 && man == 0) return out_sign;
+
+    const int s_bias = (1 << (se - 1)) - 1;
+    const int d_bias = (1 << (de - 1)) - 1;
+    uint64_t sig;
+    int lsb_exp;  // value = sig * 2^lsb_exp
+    if (ex) {
+        sig = man | (1ull << sm);
+        lsb_exp = (int)ex - s_bias - sm;
+    } else {
+        sig = man;
+        lsb_exp = 1 - s_bias - sm;
+    }
+    const int top = 63 - __clzll((long long)sig);
+    const int e_val = lsb_exp + top;
+    const int e_min = 1 - d_bias;
+    const bool normal = e_val >= e_min;
+    const int quantum = (normal ? e_val : e_min) - dm;
+    const int shift = quantum - lsb_exp;
+
+    uint64_t r;
+    if (shift <= 0) {
+        r = sig << (-shift);
+    } else if (shift >= 64) {
+        r = 0;
+    } else {
+        const uint64_t kept = sig >> shift;
+        const uint64_t rest = sig & ((1ull << shift) - 1ull);
+        const uint64_t half = 1ull << (shift - 1);
+        r = kept + ((rest > half || (rest == half && (kept & 1ull))) ? 1ull : 0ull);
+    }
+    // r carries the implicit bit for normal results; a rounding carry moves
+    // into the exponent by itself.
+    const uint64_t code = normal ? (((uint64_t)(e_val + d_bias - 1) << dm) + r) : r;
+    if ((code >> dm) >= d_all) return out_sign | out_inf;
+    return out_sign | code;
+}
+
+__device__ __forceinline__ bool is_nan_bits(uint64_t x, int e, int m)
+{
+    const uint64_t all = (1ull << e) - 1ull;
+    return ((x >> m) & all) == all && (x & low_bits64(m)) != 0;
+}
+
+// Conversion with hardware fast paths for non-NaN standard pairs.
+__device__ __forceinline__ uint64_t fconv(uint64_t x, int se, int sm, int de, int dm)
+{
+    if (!is_nan_bits(x, se, sm)) {
+        if (se == 11 && sm == 52) {
+            const double d = __longlong_as_double((long long)x);
+            if (de == 8 && dm == 23) return (uint64_t)__float_as_uint(__double2float_rn(d));
+            if (de == 11 && dm == 52) return x;
+        } else if (se == 8 && sm == 23) {
+            const float f = __uint_as_float((uint32_t)x);
+            if (de == 11 && dm == 52) return (uint64_t)__double_as_longlong((double)f);
+            if (de == 5 && dm == 10) return (uint64_t)__half_as_ushort(__float2half_rn(f));
+            if (de == 8 && dm == 7) return (uint64_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
+            if (de == 8 && dm == 23) return x;
+        } else if (se == 5 && sm == 10) {
+            if (de == 8 && dm == 23) {
+                const float f = __half2float(__ushort_as_half((unsigned short)x));
+                return (uint64_t)__float_as_uint(f);
+            }
+        } else if (se == 8 && sm == 7) {
+            if (de == 8 && dm == 23) return x << 16;
+        }
+    }
+    return fconv_general(x, se, sm, de, dm);
+}
+
+}  // namespace llgb

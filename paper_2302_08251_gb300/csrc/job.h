@@ -1,0 +1,131 @@
+// job.h -- descriptor of one layout-aware copy, as the tile kernel sees it.
+//
+// The host planner (plan.cpp) compiles a (source view, destination view) pair
+// into a JobDesc.  The kernel (copy.cu) moves the records tile by tile: the
+// tile's bytes of each source run are staged into a shared-memory "image",
+// every leaf of every record is moved (or converted) into the destination
+// image, and the destination image's runs are written back.  Inside an image
+// all addressing is 32-bit and tile-local, so no per-element arithmetic ever
+// uses the 64-bit record index (Sec. 2 of the paper: 64-bit integer arithmetic
+// is expensive on GPUs).
+#pragma once
+
+#include <stdint.h>
+
+namespace llgb {
+
+constexpr int kMaxBlobs = 32;   // blobs per side
+constexpr int kMaxSegs = 32;    // contiguous runs per tile per side
+constexpr int kMaxLeaves = 32;  // stored leaves per side
+constexpr int kMaxItems = 64;   // per-tile work items
+constexpr int kMaxPacks = 16;   // bit-stream destination leaves
+constexpr int kImageSlack = 16; // bytes after every run in an image
+
+// One contiguous run of a tile in a blob.  For tile t it covers
+// [gbase + t * tile_bytes, + tile_bytes) (the last tile: tail_bytes) and
+// lands at image offset sbase.
+struct SegDesc {
+    uint64_t gbase;
+    uint32_t tile_bytes;
+    uint32_t tail_bytes;
+    uint32_t sbase;
+    uint32_t blob;
+};
+
+enum LeafKind : uint8_t { LEAF_AFFINE = 0, LEAF_BITS = 1 };
+
+// Where record r's element of a stored leaf lives inside a tile image.
+//   affine: sbase + (r / lanes) * bstride + (r % lanes) * size  (bytes)
+//   bits:   bit r * bits of the LSB-first stream starting at sbase
+struct LeafDesc {
+    uint32_t sbase;
+    uint32_t bstride;
+    uint32_t lanes;
+    uint16_t size;
+    uint8_t kind;
+    uint8_t lshift;  // log2(lanes), or 0xFF when lanes is not a power of two
+    uint8_t bits;
+    uint8_t align;   // power of two dividing every element address (1..8)
+    uint8_t pad[2];
+};
+
+enum ItemOp : uint8_t { ITEM_MOVE = 0, ITEM_VALUE = 1 };
+enum LoadOp : uint8_t { L_DIRECT = 0, L_CT = 1, L_BITS_INT = 2, L_BITS_FLOAT = 3, L_SPLIT = 4 };
+enum StoreOp : uint8_t { S_DIRECT = 0, S_CT = 1, S_BITS_INT = 2, S_BITS_FLOAT = 3, S_SPLIT = 4 };
+
+// A unit of per-record work inside a tile.
+//  MOVE:  copy `size` bytes from (src_leaf, byte src_byte of its element) to
+//         (dst_leaf, byte dst_byte), in pieces of `gran` bytes.
+//  VALUE: load the leaf's logical value (lop), store it (sop).
+struct ItemDesc {
+    uint8_t op;
+    uint8_t size;        // MOVE: bytes; VALUE: logical value bytes
+    uint8_t gran;        // MOVE: piece size (1, 2, 4, 8)
+    uint8_t src_leaf;    // first source leaf (SPLIT: first of `size` byte leaves)
+    uint8_t dst_leaf;
+    uint8_t src_byte;
+    uint8_t dst_byte;
+    uint8_t lop;
+    uint8_t sop;
+    uint8_t is_signed;   // logical type is a signed integer
+    uint8_t l_e, l_m;    // logical float format (0, 0 for integers)
+    uint8_t s_e, s_m;    // source stored format (L_CT, L_BITS_FLOAT)
+    uint8_t d_e, d_m;    // destination stored format (S_CT, S_BITS_FLOAT)
+    uint8_t s_size;      // source stored bytes (L_CT)
+    uint8_t d_size;      // destination stored bytes (S_CT)
+    uint8_t s_bits;      // source bits (L_BITS_*)
+    uint8_t d_bits;      // destination bits (S_BITS_*)
+    uint8_t slot;        // code staging slot (S_BITS_*)
+    uint8_t pad[3];
+};
+
+// Packing of one bit-stream destination leaf from its staged codes.
+struct PackDesc {
+    uint32_t code_off;   // image offset of the slot (relative to code area)
+    uint32_t dst_sbase;  // destination image offset of the stream
+    uint8_t bits;
+    uint8_t wide;        // codes are 64-bit
+    uint8_t pad[6];
+};
+
+struct SideDesc {
+    uint8_t* blobs[kMaxBlobs];
+    SegDesc segs[kMaxSegs];
+    LeafDesc leaves[kMaxLeaves];
+    uint32_t img_bytes;  // image size, multiple of 16
+    uint16_t nsegs;
+    uint16_t nleaves;
+    uint8_t bulk_ok;     // full-tile runs are 16-byte aligned multiples of 16
+    uint8_t pad[7];
+};
+
+struct JobDesc {
+    SideDesc src;
+    SideDesc dst;
+    ItemDesc items[kMaxItems];
+    PackDesc packs[kMaxPacks];
+    uint64_t n;          // records
+    uint32_t tile;       // records per tile
+    uint32_t ntiles;     // tiles covering n
+    uint32_t nfull;      // tiles holding `tile` records
+    uint32_t code_bytes; // code staging bytes
+    uint16_t nitems;
+    uint16_t npacks;
+    uint32_t pad;
+};
+
+// Launch-wide parameters of the copy kernel.
+struct CopyArgs {
+    JobDesc job;                 // used when table == nullptr
+    const JobDesc* table;        // batch: njobs descriptors in device memory
+    const uint32_t* tile_start;  // batch: first global tile of each job (njobs+1)
+    uint32_t njobs;
+    uint32_t total_tiles;
+    uint32_t src_stage_bytes;    // per stage, max over jobs
+    uint32_t dst_stage_bytes;
+    uint32_t code_bytes;
+    uint16_t src_stages;
+    uint16_t dst_stages;
+};
+
+}  // namespace llgb

@@ -1,0 +1,31 @@
+// kernels.h -- host-side entry points of the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "job.h"
+
+namespace llgb {
+
+// copy.cu
+cudaError_t launch_copy(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream);
+size_t copy_shared_header_bytes();
+cudaError_t read_device_status(unsigned* out, bool reset);
+
+// nbody.cu: a particle view, leaf f of record i at
+//   base[f] + (i >> lshift) * bstride + (i & lmask) * 4.
+struct ParticleView {
+    uint8_t* base[7];
+    uint32_t bstride;
+    uint32_t lshift;
+    uint32_t lmask;
+    uint32_t n;
+};
+
+enum { PV_AOS = 0, PV_SOA = 1, PV_AOSOA32 = 2, PV_GENERIC = 3 };
+
+cudaError_t launch_nbody(const ParticleView& v, int kind, float eps, float dt, cudaStream_t stream);
+
+}  // namespace llgb

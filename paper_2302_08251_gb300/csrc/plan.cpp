@@ -1,0 +1,587 @@
+// plan.cpp -- mapping address compiler (host).
+//
+// View plans follow the mappings of arXiv 2302.08251:
+//   AoS / SoA multi-blob / AoSoA (Sec. 5, Fig. 3 text), SoA single blob,
+//   BitpackIntSoA and BitpackFloatSoA (Sec. 3), ChangeType and Bytesplit
+//   (Sec. 3) over an AoS/SoA/AoSoA inner mapping,
+// with the index-type rule of Sec. 2: a view whose record count or largest
+// byte offset does not fit the chosen index type is rejected.
+//
+// Every plain layout is one affine form per leaf,
+//     offset(i, f) = base_f + (i / L) * B + (i % L) * s_f,
+// and every bit-packed leaf is the stream position i * w.  A tile of T
+// records (T a multiple of 128 and of every lane count) therefore covers one
+// contiguous run per blob region, and inside a tile image the same affine
+// form holds with 32-bit tile-local offsets.
+#include "plan.h"
+
+#include <string.h>
+
+#include <algorithm>
+
+namespace llgb {
+
+int type_size(int32_t t)
+{
+    switch (t) {
+    case LLGB_U8: case LLGB_I8: return 1;
+    case LLGB_U16: case LLGB_I16: case LLGB_F16: case LLGB_BF16: return 2;
+    case LLGB_U32: case LLGB_I32: case LLGB_F32: return 4;
+    case LLGB_U64: case LLGB_I64: case LLGB_F64: return 8;
+    default: return 0;
+    }
+}
+
+bool type_is_float(int32_t t, int* e, int* m)
+{
+    int ee = 0, mm = 0;
+    switch (t) {
+    case LLGB_F16: ee = 5; mm = 10; break;
+    case LLGB_BF16: ee = 8; mm = 7; break;
+    case LLGB_F32: ee = 8; mm = 23; break;
+    case LLGB_F64: ee = 11; mm = 52; break;
+    default: return false;
+    }
+    if (e) *e = ee;
+    if (m) *m = mm;
+    return true;
+}
+
+bool type_is_int(int32_t t) { return t >= LLGB_U8 && t <= LLGB_I64; }
+bool type_is_signed(int32_t t) { return t >= LLGB_I8 && t <= LLGB_I64; }
+
+static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+static bool mul_ok(uint64_t a, uint64_t b, uint64_t* out) { return !__builtin_mul_overflow(a, b, out); }
+
+static uint64_t index_max(int itype)
+{
+    switch (itype) {
+    case LLGB_IDX_I16: return 32767ull;
+    case LLGB_IDX_U16: return 65535ull;
+    case LLGB_IDX_I32: return 2147483647ull;
+    case LLGB_IDX_U32: return 4294967295ull;
+    case LLGB_IDX_I64: return 9223372036854775807ull;
+    default: return ~0ull;
+    }
+}
+
+static bool is_affine_kind(int k)
+{
+    return k == LLGB_MAP_AOS || k == LLGB_MAP_SOA_SB || k == LLGB_MAP_SOA_MB || k == LLGB_MAP_AOSOA;
+}
+
+llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llgb_mapping_desc& map,
+                      ViewPlan* out, std::string* why)
+{
+    ViewPlan v;
+    v.types = rec.types;
+    v.ext = ext;
+    const int nf = (int)rec.types.size();
+
+    // --- extents (Sec. 2) ---
+    if (ext.rank < 1 || ext.rank > 4 || ext.reserved != 0) {
+        *why = "extents: rank must be 1..4 and reserved 0";
+        return LLGB_ERR_INVALID_ARG;
+    }
+    if (ext.index_type < LLGB_IDX_I16 || ext.index_type > LLGB_IDX_U64) {
+        *why = "extents: unknown index type";
+        return LLGB_ERR_INVALID_ARG;
+    }
+    const uint64_t imax = index_max(ext.index_type);
+    uint64_t n = 1;
+    for (int d = 0; d < ext.rank; ++d) {
+        if (ext.ext[d] > imax) {
+            *why = "extent " + std::to_string(d) + " does not fit the index type";
+            return LLGB_ERR_INDEX_OVERFLOW;
+        }
+        if (!mul_ok(n, ext.ext[d], &n)) {
+            *why = "record count overflows 64 bits";
+            return LLGB_ERR_INDEX_OVERFLOW;
+        }
+    }
+    if (n > 0 && n - 1 > imax) {
+        *why = "record count " + std::to_string(n) + " does not fit the index type";
+        return LLGB_ERR_INDEX_OVERFLOW;
+    }
+    v.n = n;
+
+    // --- wrappers (Sec. 3: ChangeType, Bytesplit) ---
+    const llgb_mapping_desc* base = &map;
+    std::vector<int32_t> stored_types;
+    if (map.kind == LLGB_MAP_BYTESPLIT || map.kind == LLGB_MAP_CHANGETYPE) {
+        if (!map.inner) {
+            *why = "wrapper mapping without an inner mapping";
+            return LLGB_ERR_INVALID_ARG;
+        }
+        base = map.inner;
+        if (!is_affine_kind(base->kind)) {
+            *why = "the inner mapping of Bytesplit/ChangeType must be AoS, SoA or AoSoA";
+            return LLGB_ERR_UNSUPPORTED;
+        }
+        if (map.kind == LLGB_MAP_BYTESPLIT) {
+            v.wrap = WRAP_BYTESPLIT;
+            for (int f = 0; f < nf; ++f) {
+                const int s = type_size(rec.types[f]);
+                v.recipes.push_back({L_SPLIT, (int)stored_types.size(), s});
+                for (int j = 0; j < s; ++j) stored_types.push_back(LLGB_U8);
+            }
+        } else {
+            v.wrap = WRAP_CHANGETYPE;
+            if (map.n_ct < 0 || map.n_ct > LLGB_MAX_CT) {
+                *why = "ChangeType: n_ct must be 0..4";
+                return LLGB_ERR_INVALID_ARG;
+            }
+            for (int k = 0; k < map.n_ct; ++k) {
+                if (!type_is_float(map.ct_from[k], nullptr, nullptr) ||
+                    !type_is_float(map.ct_to[k], nullptr, nullptr)) {
+                    *why = "ChangeType: only floating-point type pairs are supported";
+                    return LLGB_ERR_INVALID_ARG;
+                }
+            }
+            for (int f = 0; f < nf; ++f) {
+                int32_t t = rec.types[f];
+                for (int k = 0; k < map.n_ct; ++k)
+                    if (map.ct_from[k] == t) {
+                        t = map.ct_to[k];
+                        break;
+                    }
+                v.recipes.push_back({t == rec.types[f] ? (int)L_DIRECT : (int)L_CT, f, 1});
+                stored_types.push_back(t);
+            }
+        }
+    } else if (is_affine_kind(map.kind)) {
+        for (int f = 0; f < nf; ++f) {
+            v.recipes.push_back({L_DIRECT, f, 1});
+            stored_types.push_back(rec.types[f]);
+        }
+    } else if (map.kind == LLGB_MAP_BITPACK_INT || map.kind == LLGB_MAP_BITPACK_FLOAT) {
+        stored_types = rec.types;
+    } else {
+        *why = "unknown mapping kind";
+        return LLGB_ERR_INVALID_ARG;
+    }
+
+    // --- stored leaves ---
+    const int ns = (int)stored_types.size();
+    if (ns > kMaxLeaves) {
+        *why = "more than 32 stored leaves";
+        return LLGB_ERR_UNSUPPORTED;
+    }
+    v.stored.resize(ns);
+    for (int g = 0; g < ns; ++g) {
+        v.stored[g].type = stored_types[g];
+        v.stored[g].size = type_size(stored_types[g]);
+        v.stored[g].bits = 8 * v.stored[g].size;
+    }
+
+    switch (base->kind) {
+    case LLGB_MAP_AOS: v.base = BASE_AOS; break;
+    case LLGB_MAP_SOA_SB: v.base = BASE_SOA_SB; break;
+    case LLGB_MAP_SOA_MB: v.base = BASE_SOA_MB; break;
+    case LLGB_MAP_AOSOA: v.base = BASE_AOSOA; break;
+    case LLGB_MAP_BITPACK_INT: v.base = BASE_BITS_INT; break;
+    default: v.base = BASE_BITS_FLOAT; break;
+    }
+    v.aos_packed = base->aos_packed ? 1 : 0;
+    v.subarray_align = base->subarray_align;
+    v.lanes = v.base == BASE_AOSOA ? base->lanes : 1;
+
+    if (v.base == BASE_BITS_INT) {
+        // Sec. 3 BitpackIntSoA: a bit count for integral leaves.
+        for (int f = 0; f < nf; ++f) {
+            const int b = base->field_bits ? base->field_bits[f] : base->bits;
+            if (!type_is_int(rec.types[f])) {
+                *why = "BitpackInt: leaf " + rec.paths[f] + " is not integral";
+                return LLGB_ERR_INVALID_ARG;
+            }
+            if (b < 1 || b > 8 * type_size(rec.types[f])) {
+                *why = "BitpackInt: bit count out of range for leaf " + rec.paths[f];
+                return LLGB_ERR_INVALID_ARG;
+            }
+            v.stored[f].bits = b;
+            v.recipes.push_back({L_BITS_INT, f, 1});
+        }
+    } else if (v.base == BASE_BITS_FLOAT) {
+        // Sec. 3 BitpackFloatSoA: exponent and mantissa bits per leaf.
+        for (int f = 0; f < nf; ++f) {
+            const int e = base->field_exp ? base->field_exp[f] : base->exp_bits;
+            const int m = base->field_man ? base->field_man[f] : base->man_bits;
+            if (!type_is_float(rec.types[f], nullptr, nullptr)) {
+                *why = "BitpackFloat: leaf " + rec.paths[f] + " is not floating point";
+                return LLGB_ERR_INVALID_ARG;
+            }
+            if (e < 2 || e > 11 || m < 1 || m > 52 || 1 + e + m > 64) {
+                *why = "BitpackFloat: need 2<=E<=11, 1<=M<=52, 1+E+M<=64";
+                return LLGB_ERR_INVALID_ARG;
+            }
+            v.stored[f].e = e;
+            v.stored[f].m = m;
+            v.stored[f].bits = 1 + e + m;
+            v.recipes.push_back({L_BITS_FLOAT, f, 1});
+        }
+    }
+    if (v.base == BASE_SOA_SB && (v.subarray_align & (v.subarray_align - 1))) {
+        *why = "SoA single blob: subarray_align must be 0 or a power of two";
+        return LLGB_ERR_INVALID_ARG;
+    }
+    if (v.base == BASE_AOSOA && v.lanes < 1) {
+        *why = "AoSoA: lanes must be >= 1";
+        return LLGB_ERR_INVALID_ARG;
+    }
+
+    // --- layout and blob sizes ---
+    v.leaf_offset.assign(ns, 0);
+    v.sb_base.assign(ns, 0);
+    v.seg_end.assign(ns, 0);
+    v.leaf_blob.assign(ns, 0);
+    bool ok = true;
+    switch (v.base) {
+    case BASE_AOS:
+    case BASE_AOSOA: {
+        const bool packed = v.base == BASE_AOSOA || v.aos_packed;
+        uint64_t off = 0, max_align = 1;
+        for (int g = 0; g < ns; ++g) {
+            const uint64_t s = v.stored[g].size;
+            if (!packed) off = align_up(off, s);
+            v.leaf_offset[g] = off;
+            off += s;
+            max_align = std::max<uint64_t>(max_align, s);
+        }
+        v.record_bytes = packed ? off : align_up(off, max_align);
+        uint64_t size = 0;
+        if (v.base == BASE_AOS) {
+            ok = mul_ok(n, v.record_bytes, &size);
+        } else {
+            const uint64_t blocks = n / v.lanes + (n % v.lanes ? 1 : 0);
+            uint64_t recs = 0;
+            ok = mul_ok(blocks, v.lanes, &recs) && mul_ok(recs, v.record_bytes, &size);
+        }
+        v.blob_sizes.push_back(size);
+        for (int g = 0; g < ns; ++g) v.seg_end[g] = size;
+        break;
+    }
+    case BASE_SOA_MB:
+        for (int g = 0; g < ns; ++g) {
+            uint64_t size = 0;
+            ok = ok && mul_ok(n, (uint64_t)v.stored[g].size, &size);
+            v.blob_sizes.push_back(size);
+            v.seg_end[g] = size;
+            v.leaf_blob[g] = g;
+        }
+        break;
+    case BASE_SOA_SB: {
+        uint64_t at = 0;
+        for (int g = 0; g < ns; ++g) {
+            const uint64_t s = v.stored[g].size;
+            at = align_up(at, v.subarray_align ? v.subarray_align : s);
+            v.sb_base[g] = at;
+            uint64_t bytes = 0;
+            ok = ok && mul_ok(n, s, &bytes) && !__builtin_add_overflow(at, bytes, &at);
+            v.seg_end[g] = at;
+        }
+        v.blob_sizes.push_back(at);
+        break;
+    }
+    default:  // bit streams: whole 32-bit words per leaf
+        for (int g = 0; g < ns; ++g) {
+            uint64_t bits = 0;
+            ok = ok && mul_ok(n, (uint64_t)v.stored[g].bits, &bits);
+            const uint64_t size = 4 * (bits / 32 + (bits % 32 ? 1 : 0));
+            v.blob_sizes.push_back(size);
+            v.seg_end[g] = size;
+            v.leaf_blob[g] = g;
+        }
+        break;
+    }
+    if (!ok) {
+        *why = "blob size overflows 64 bits";
+        return LLGB_ERR_INDEX_OVERFLOW;
+    }
+    if ((int)v.blob_sizes.size() > kMaxBlobs) {
+        *why = "more than 32 blobs";
+        return LLGB_ERR_UNSUPPORTED;
+    }
+    for (uint64_t s : v.blob_sizes)
+        if (s > 0 && s - 1 > imax) {
+            *why = "largest byte offset " + std::to_string(s - 1) + " does not fit the index type";
+            return LLGB_ERR_INDEX_OVERFLOW;
+        }
+    *out = std::move(v);
+    return LLGB_OK;
+}
+
+static uint64_t gcd64(uint64_t a, uint64_t b)
+{
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+uint32_t tile_quantum(const ViewPlan& src, const ViewPlan& dst)
+{
+    uint64_t q = 128;
+    for (const ViewPlan* v : {&src, &dst})
+        if (v->base == BASE_AOSOA) q = q / gcd64(q, v->lanes) * v->lanes;
+    return q > (1u << 20) ? 0u : (uint32_t)q;
+}
+
+static double image_bpr(const ViewPlan& v)
+{
+    switch (v.base) {
+    case BASE_AOS:
+    case BASE_AOSOA: return (double)v.record_bytes;
+    default: {
+        double s = 0;
+        for (const StoredLeaf& l : v.stored) s += (v.base >= BASE_BITS_INT) ? l.bits / 8.0 : l.size;
+        return s;
+    }
+    }
+}
+
+void bytes_per_record(const ViewPlan& src, const ViewPlan& dst, double* src_bpr, double* dst_bpr,
+                      uint32_t* code_bpr)
+{
+    *src_bpr = image_bpr(src);
+    *dst_bpr = image_bpr(dst);
+    uint32_t c = 0;
+    if (dst.base >= BASE_BITS_INT)
+        for (const StoredLeaf& l : dst.stored) c += l.bits > 32 ? 8 : 4;
+    *code_bpr = c;
+}
+
+// Fill one side's runs and leaf addressing for tiles of `tile` records.
+static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, uint32_t tile, uint32_t ntiles,
+                             SideDesc* S, std::string* why)
+{
+    memset(S, 0, sizeof *S);
+    for (size_t k = 0; k < ptrs.size(); ++k) S->blobs[k] = static_cast<uint8_t*>(ptrs[k]);
+    uint64_t img = 0;
+    bool bulk_ok = true;
+    auto add_seg = [&](uint32_t blob, uint64_t gbase, uint64_t tile_bytes, uint64_t end) -> int64_t {
+        if (S->nsegs >= kMaxSegs || tile_bytes > 0xFFFFFFFFull) return -1;
+        SegDesc& d = S->segs[S->nsegs++];
+        d.blob = blob;
+        d.gbase = gbase;
+        d.tile_bytes = (uint32_t)tile_bytes;
+        d.sbase = (uint32_t)img;
+        // The last tile's run ends exactly where the region ends.
+        const uint64_t last_start = gbase + (uint64_t)(ntiles - 1) * tile_bytes;
+        if (end < last_start || end - last_start > tile_bytes || end > v.blob_sizes[blob]) return -1;
+        d.tail_bytes = (uint32_t)(end - last_start);
+        // Full tiles never run past the region.
+        const uint64_t nfull = v.n / tile;
+        if (gbase + nfull * tile_bytes > end) return -1;
+        if ((gbase & 15u) || (tile_bytes & 15u)) bulk_ok = false;
+        img += align_up(tile_bytes, 16) + kImageSlack;
+        return d.sbase;
+    };
+    const int ns = (int)v.stored.size();
+    S->nleaves = (uint16_t)ns;
+    for (int g = 0; g < ns; ++g) {
+        LeafDesc& L = S->leaves[g];
+        L.size = (uint16_t)v.stored[g].size;
+        L.lanes = 1;
+        L.lshift = 0;
+        L.kind = LEAF_AFFINE;
+    }
+    switch (v.base) {
+    case BASE_AOS: {
+        const int64_t sb = add_seg(0, 0, (uint64_t)tile * v.record_bytes, v.seg_end[0]);
+        if (sb < 0) break;
+        for (int g = 0; g < ns; ++g) {
+            S->leaves[g].sbase = (uint32_t)(sb + v.leaf_offset[g]);
+            S->leaves[g].bstride = (uint32_t)v.record_bytes;
+        }
+        break;
+    }
+    case BASE_AOSOA: {
+        const int64_t sb = add_seg(0, 0, (uint64_t)tile * v.record_bytes, v.seg_end[0]);
+        if (sb < 0) break;
+        const uint32_t L = (uint32_t)v.lanes;
+        uint8_t shift = 0xFF;
+        for (uint8_t p = 0; p < 32; ++p)
+            if ((1u << p) == L) shift = p;
+        for (int g = 0; g < ns; ++g) {
+            S->leaves[g].sbase = (uint32_t)(sb + L * v.leaf_offset[g]);
+            S->leaves[g].bstride = (uint32_t)(L * v.record_bytes);
+            S->leaves[g].lanes = L;
+            S->leaves[g].lshift = shift;
+        }
+        break;
+    }
+    case BASE_SOA_MB:
+    case BASE_SOA_SB:
+        for (int g = 0; g < ns; ++g) {
+            const uint64_t s = v.stored[g].size;
+            const int64_t sb = add_seg(v.leaf_blob[g], v.sb_base[g], (uint64_t)tile * s, v.seg_end[g]);
+            if (sb < 0) break;
+            S->leaves[g].sbase = (uint32_t)sb;
+            S->leaves[g].bstride = (uint32_t)s;
+        }
+        break;
+    default:
+        for (int g = 0; g < ns; ++g) {
+            const uint64_t w = v.stored[g].bits;
+            const int64_t sb = add_seg(v.leaf_blob[g], 0, (uint64_t)tile * w / 8, v.seg_end[g]);
+            if (sb < 0) break;
+            S->leaves[g].sbase = (uint32_t)sb;
+            S->leaves[g].kind = LEAF_BITS;
+            S->leaves[g].bits = (uint8_t)w;
+        }
+        break;
+    }
+    const int expect_segs = (v.base == BASE_AOS || v.base == BASE_AOSOA) ? 1 : ns;
+    if (S->nsegs != expect_segs) {
+        *why = "internal: a tile run does not fit its blob region";
+        return LLGB_ERR_INVALID_ARG;
+    }
+    for (int g = 0; g < ns; ++g) {
+        LeafDesc& L = S->leaves[g];
+        uint32_t p = 8;
+        while (p > 1 && ((L.sbase % p) || (L.bstride % p) || (L.lanes > 1 && (L.size % p)))) p /= 2;
+        L.align = (uint8_t)p;
+    }
+    if (img > 0xFFFFFFFFull) {
+        *why = "tile image too large";
+        return LLGB_ERR_INVALID_ARG;
+    }
+    S->img_bytes = (uint32_t)img;
+    S->bulk_ok = bulk_ok ? 1 : 0;
+    return LLGB_OK;
+}
+
+llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, const ViewPlan& dst,
+                     const std::vector<void*>& dst_ptrs, uint32_t tile, JobDesc* job, std::string* why)
+{
+    memset(job, 0, sizeof *job);
+    const uint32_t q = tile_quantum(src, dst);
+    if (q == 0 || tile == 0 || tile % q) {
+        *why = "tile size must be a positive multiple of " + std::to_string(q);
+        return LLGB_ERR_INVALID_ARG;
+    }
+    const uint64_t n = src.n;
+    const uint64_t ntiles64 = n == 0 ? 0 : (n - 1) / tile + 1;
+    if (ntiles64 > 0xFFFFFFFFull) {
+        *why = "too many tiles";
+        return LLGB_ERR_INVALID_ARG;
+    }
+    job->n = n;
+    job->tile = tile;
+    job->ntiles = (uint32_t)ntiles64;
+    job->nfull = (uint32_t)(n / tile);
+    if (n == 0) return LLGB_OK;
+    llgb_status st = plan_side(src, src_ptrs, tile, job->ntiles, &job->src, why);
+    if (st != LLGB_OK) return st;
+    st = plan_side(dst, dst_ptrs, tile, job->ntiles, &job->dst, why);
+    if (st != LLGB_OK) return st;
+
+    // Code staging slots for bit-stream destination leaves.
+    int slot_of[kMaxLeaves];
+    uint32_t code_at = 0;
+    for (int g = 0; g < (int)dst.stored.size(); ++g) {
+        slot_of[g] = -1;
+        if (dst.base < BASE_BITS_INT) continue;
+        if (job->npacks >= kMaxPacks) {
+            *why = "more than 16 bit-packed leaves";
+            return LLGB_ERR_UNSUPPORTED;
+        }
+        PackDesc& P = job->packs[job->npacks];
+        P.bits = (uint8_t)dst.stored[g].bits;
+        P.wide = dst.stored[g].bits > 32;
+        P.code_off = code_at;
+        P.dst_sbase = job->dst.leaves[g].sbase;
+        code_at += (uint32_t)align_up((uint64_t)tile * (P.wide ? 8 : 4), 16);
+        slot_of[g] = job->npacks++;
+    }
+    job->code_bytes = code_at;
+
+    // Items: one per leaf, or one per byte where a side splits bytes.
+    const int nf = (int)src.types.size();
+    auto add = [&](const ItemDesc& it) -> bool {
+        if (job->nitems >= kMaxItems) return false;
+        job->items[job->nitems++] = it;
+        return true;
+    };
+    for (int f = 0; f < nf; ++f) {
+        const Recipe a = src.recipes[f], b = dst.recipes[f];
+        const int32_t t = src.types[f];
+        const int size = type_size(t);
+        const bool a_bytes = a.op == L_DIRECT || a.op == L_SPLIT;
+        const bool b_bytes = b.op == L_DIRECT || b.op == L_SPLIT;
+        if (a_bytes && b_bytes) {
+            if (a.op == L_DIRECT && b.op == L_DIRECT) {
+                ItemDesc it{};
+                it.op = ITEM_MOVE;
+                it.size = (uint8_t)size;
+                it.src_leaf = (uint8_t)a.first;
+                it.dst_leaf = (uint8_t)b.first;
+                it.gran = (uint8_t)std::min<int>(
+                    size, std::min<int>(job->src.leaves[a.first].align, job->dst.leaves[b.first].align));
+                if (!add(it)) goto too_many;
+            } else {
+                for (int j = 0; j < size; ++j) {
+                    ItemDesc it{};
+                    it.op = ITEM_MOVE;
+                    it.size = 1;
+                    it.gran = 1;
+                    it.src_leaf = (uint8_t)(a.op == L_SPLIT ? a.first + j : a.first);
+                    it.src_byte = (uint8_t)(a.op == L_SPLIT ? 0 : j);
+                    it.dst_leaf = (uint8_t)(b.op == L_SPLIT ? b.first + j : b.first);
+                    it.dst_byte = (uint8_t)(b.op == L_SPLIT ? 0 : j);
+                    if (!add(it)) goto too_many;
+                }
+            }
+            continue;
+        }
+        {
+            ItemDesc it{};
+            it.op = ITEM_VALUE;
+            it.size = (uint8_t)size;
+            it.lop = (uint8_t)a.op;
+            it.sop = (uint8_t)b.op;  // StoreOp numbering matches LoadOp
+            it.src_leaf = (uint8_t)a.first;
+            it.dst_leaf = (uint8_t)b.first;
+            it.is_signed = type_is_signed(t) ? 1 : 0;
+            int le = 0, lm = 0;
+            type_is_float(t, &le, &lm);
+            it.l_e = (uint8_t)le;
+            it.l_m = (uint8_t)lm;
+            if (a.op == L_CT) {
+                int e = 0, m = 0;
+                type_is_float(src.stored[a.first].type, &e, &m);
+                it.s_e = (uint8_t)e;
+                it.s_m = (uint8_t)m;
+                it.s_size = (uint8_t)src.stored[a.first].size;
+            } else if (a.op == L_BITS_FLOAT) {
+                it.s_e = (uint8_t)src.stored[a.first].e;
+                it.s_m = (uint8_t)src.stored[a.first].m;
+            }
+            if (a.op == L_BITS_INT || a.op == L_BITS_FLOAT) it.s_bits = (uint8_t)src.stored[a.first].bits;
+            if (b.op == L_CT) {
+                int e = 0, m = 0;
+                type_is_float(dst.stored[b.first].type, &e, &m);
+                it.d_e = (uint8_t)e;
+                it.d_m = (uint8_t)m;
+                it.d_size = (uint8_t)dst.stored[b.first].size;
+            } else if (b.op == L_BITS_FLOAT) {
+                it.d_e = (uint8_t)dst.stored[b.first].e;
+                it.d_m = (uint8_t)dst.stored[b.first].m;
+            }
+            if (b.op == L_BITS_INT || b.op == L_BITS_FLOAT) {
+                it.d_bits = (uint8_t)dst.stored[b.first].bits;
+                it.slot = (uint8_t)slot_of[b.first];
+            }
+            if (!add(it)) goto too_many;
+        }
+    }
+    return LLGB_OK;
+too_many:
+    *why = "more than 64 work items per tile";
+    return LLGB_ERR_UNSUPPORTED;
+}
+
+}  // namespace llgb

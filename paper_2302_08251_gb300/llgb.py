@@ -1,0 +1,293 @@
+"""Thin ctypes binding of the C ABI in ``include/llgb.h``.
+
+Argument marshalling only: every step of a copy, pack, unpack or n-body step
+runs in the CUDA library ``libllgb.so``.  The library must have been built
+(``paper_2302_08251_gb300.build.build()``); loading raises if it is missing.
+There is no CPU fallback.
+
+The raw entry points keep their C names (``llgb_copy`` ...); ``Record`` and
+``View`` manage handle lifetimes and, for convenience, device blobs allocated
+as torch tensors (PyTorch supplies memory and streams, nothing else).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+TYPES = ["u8", "u16", "u32", "u64", "i8", "i16", "i32", "i64",
+         "f16", "bf16", "f32", "f64"]
+TYPE_ID = {t: k for k, t in enumerate(TYPES)}
+TYPE_SIZE = {"u8": 1, "u16": 2, "u32": 4, "u64": 8, "i8": 1, "i16": 2, "i32": 4,
+             "i64": 8, "f16": 2, "bf16": 2, "f32": 4, "f64": 8}
+INDEX_TYPES = {"i16": 0, "u16": 1, "i32": 2, "u32": 3, "i64": 4, "u64": 5}
+KIND_ID = {"aos": 0, "soa_sb": 1, "soa_mb": 2, "aosoa": 3, "bitpack_int": 4,
+           "bitpack_float": 5, "bytesplit": 6, "changetype": 7}
+MAX_CT = 4
+
+OK = 0
+ERR_INVALID_ARG, ERR_INDEX_OVERFLOW, ERR_MISMATCH, ERR_UNSUPPORTED = 1, 2, 3, 4
+ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_UNBOUND = 5, 6, 7, 8
+
+
+class LlgbError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"llgb status {status}: {message}")
+        self.status = status
+
+
+class FieldDesc(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_char_p), ("type", ctypes.c_int32)]
+
+
+class Extents(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("index_type", ctypes.c_int32),
+                ("static_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("ext", ctypes.c_uint64 * 4)]
+
+
+class MappingDesc(ctypes.Structure):
+    pass
+
+
+MappingDesc._fields_ = [
+    ("kind", ctypes.c_int32), ("aos_packed", ctypes.c_int32),
+    ("subarray_align", ctypes.c_uint64), ("lanes", ctypes.c_uint64),
+    ("bits", ctypes.c_int32), ("exp_bits", ctypes.c_int32), ("man_bits", ctypes.c_int32),
+    ("n_ct", ctypes.c_int32), ("ct_from", ctypes.c_int32 * MAX_CT),
+    ("ct_to", ctypes.c_int32 * MAX_CT),
+    ("field_bits", ctypes.POINTER(ctypes.c_int32)),
+    ("field_exp", ctypes.POINTER(ctypes.c_int32)),
+    ("field_man", ctypes.POINTER(ctypes.c_int32)),
+    ("inner", ctypes.POINTER(MappingDesc)),
+]
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("tile_records", ctypes.c_int32), ("src_stages", ctypes.c_int32),
+                ("dst_stages", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k in
+                ("tile_records", "src_stages", "dst_stages", "threads", "ctas_per_sm")}
+
+
+EXPORTS = [
+    "llgb_last_error", "llgb_version", "llgb_record_create", "llgb_record_destroy",
+    "llgb_record_leaf_count", "llgb_record_size", "llgb_view_create", "llgb_view_destroy",
+    "llgb_view_blob_count", "llgb_view_blob_size", "llgb_view_record_count",
+    "llgb_view_bind", "llgb_copy", "llgb_pack", "llgb_unpack", "llgb_copy_config",
+    "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "paper_2302_08251_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(path)
+        p, i32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+        L.llgb_last_error.restype = ctypes.c_char_p
+        L.llgb_version.restype = ctypes.c_char_p
+        L.llgb_record_create.argtypes = [ctypes.POINTER(FieldDesc), i32, ctypes.POINTER(p)]
+        L.llgb_record_destroy.argtypes = [p]
+        L.llgb_record_leaf_count.argtypes = [p]
+        L.llgb_record_size.argtypes = [p, i32, ctypes.POINTER(u64)]
+        L.llgb_view_create.argtypes = [p, ctypes.POINTER(Extents), ctypes.POINTER(MappingDesc),
+                                       ctypes.POINTER(p)]
+        L.llgb_view_destroy.argtypes = [p]
+        L.llgb_view_blob_count.argtypes = [p]
+        L.llgb_view_blob_size.argtypes = [p, i32]
+        L.llgb_view_blob_size.restype = u64
+        L.llgb_view_record_count.argtypes = [p]
+        L.llgb_view_record_count.restype = u64
+        L.llgb_view_bind.argtypes = [p, ctypes.POINTER(p), i32]
+        for name in ("llgb_copy", "llgb_pack", "llgb_unpack"):
+            getattr(L, name).argtypes = [p, p, p]
+        L.llgb_copy_config.argtypes = [p, p, ctypes.POINTER(LaunchConfig)]
+        L.llgb_copy_with.argtypes = [p, p, ctypes.POINTER(LaunchConfig), p]
+        L.llgb_nbody_step.argtypes = [p, ctypes.c_float, ctypes.c_float, p]
+        L.llgb_device_status.argtypes = [ctypes.POINTER(i32), i32]
+        _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != OK:
+        raise LlgbError(status, lib().llgb_last_error().decode())
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return ctypes.c_void_p(int(stream))
+
+
+def mapping_desc(m: dict, keep: list) -> MappingDesc:
+    """Build an llgb_mapping_desc from the plain-dict mapping description."""
+    c = MappingDesc()
+    c.kind = KIND_ID[m["kind"]]
+    c.aos_packed = int(m.get("packed", 0))
+    c.subarray_align = int(m.get("subarray_align", 0))
+    c.lanes = int(m.get("lanes", 1))
+    c.bits = int(m.get("bits", 0))
+    c.exp_bits = int(m.get("exp", 0))
+    c.man_bits = int(m.get("man", 0))
+    ct = m.get("ct", [])
+    c.n_ct = len(ct)
+    for k, (a, b) in enumerate(ct):
+        c.ct_from[k] = TYPE_ID[a]
+        c.ct_to[k] = TYPE_ID[b]
+    for key in ("field_bits", "field_exp", "field_man"):
+        if m.get(key) is not None:
+            arr = (ctypes.c_int32 * len(m[key]))(*m[key])
+            keep.append(arr)
+            setattr(c, key, ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)))
+    if m.get("inner") is not None:
+        inner = mapping_desc(m["inner"], keep)
+        keep.append(inner)
+        c.inner = ctypes.pointer(inner)
+    return c
+
+
+def extents_desc(extents, index_type: str = "u64", static=None) -> Extents:
+    if isinstance(extents, int):
+        extents = (extents,)
+    e = Extents()
+    e.rank = len(extents)
+    e.index_type = INDEX_TYPES[index_type]
+    mask = 0
+    for d, x in enumerate(extents):
+        e.ext[d] = int(x)
+        if static is not None and static[d]:
+            mask |= 1 << d
+    e.static_mask = mask
+    return e
+
+
+class Record:
+    def __init__(self, leaves):
+        self.leaves = [(str(p), str(t)) for p, t in leaves]
+        arr = (FieldDesc * len(self.leaves))()
+        self._paths = [p.encode() for p, _ in self.leaves]
+        for k, (p, t) in enumerate(self.leaves):
+            arr[k].path = self._paths[k]
+            arr[k].type = TYPE_ID[t]
+        h = ctypes.c_void_p()
+        check(lib().llgb_record_create(arr, len(self.leaves), ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def types(self):
+        return [t for _, t in self.leaves]
+
+    def size(self, packed: bool = False) -> int:
+        out = ctypes.c_uint64()
+        check(lib().llgb_record_size(self.handle, int(packed), ctypes.byref(out)))
+        return out.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.llgb_record_destroy(self.handle)
+            self.handle = None
+
+
+class View:
+    """A view: mapping + blobs.  Blobs are torch uint8 tensors on the device
+    (allocated here unless given) and are bound to the C view."""
+
+    def __init__(self, record: Record, mapping: dict, extents, index_type: str = "u64",
+                 static=None, blobs=None, device=None):
+        self.record = record
+        self.mapping = mapping
+        self._keep: list = []
+        self._ext = extents_desc(extents, index_type, static)
+        self._map = mapping_desc(mapping, self._keep)
+        h = ctypes.c_void_p()
+        check(lib().llgb_view_create(record.handle, ctypes.byref(self._ext),
+                                     ctypes.byref(self._map), ctypes.byref(h)))
+        self.handle = h
+        nb = lib().llgb_view_blob_count(h)
+        self.blob_sizes = [int(lib().llgb_view_blob_size(h, k)) for k in range(nb)]
+        self.n = int(lib().llgb_view_record_count(h))
+        if blobs is None:
+            import torch
+            dev = device if device is not None else torch.device("cuda")
+            blobs = [torch.empty(max(1, s), dtype=torch.uint8, device=dev) for s in self.blob_sizes]
+        self.bind(blobs)
+
+    def bind(self, blobs) -> None:
+        if len(blobs) != len(self.blob_sizes):
+            raise ValueError("wrong number of blobs")
+        for b, s in zip(blobs, self.blob_sizes):
+            if b.numel() * b.element_size() < s:
+                raise ValueError("blob too small")
+        self.blobs = list(blobs)
+        ptrs = (ctypes.c_void_p * max(1, len(blobs)))(*[b.data_ptr() for b in blobs])
+        check(lib().llgb_view_bind(self.handle, ptrs, len(blobs)))
+
+    def blob_bytes(self):
+        """Host copies (numpy uint8) of every blob, trimmed to the blob size."""
+        return [b[:s].cpu().numpy() for b, s in zip(self.blobs, self.blob_sizes)]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.llgb_view_destroy(self.handle)
+            self.handle = None
+
+
+def llgb_copy(src: View, dst: View, stream=None) -> None:
+    check(lib().llgb_copy(src.handle, dst.handle, _stream_ptr(stream)))
+
+
+def llgb_pack(plain: View, packed: View, stream=None) -> None:
+    check(lib().llgb_pack(plain.handle, packed.handle, _stream_ptr(stream)))
+
+
+def llgb_unpack(packed: View, plain: View, stream=None) -> None:
+    check(lib().llgb_unpack(packed.handle, plain.handle, _stream_ptr(stream)))
+
+
+def llgb_copy_config(src: View, dst: View) -> dict:
+    c = LaunchConfig()
+    check(lib().llgb_copy_config(src.handle, dst.handle, ctypes.byref(c)))
+    return c.as_dict()
+
+
+def llgb_copy_with(src: View, dst: View, cfg: dict, stream=None) -> None:
+    c = LaunchConfig()
+    for k, v in cfg.items():
+        setattr(c, k, int(v))
+    check(lib().llgb_copy_with(src.handle, dst.handle, ctypes.byref(c), _stream_ptr(stream)))
+
+
+def llgb_nbody_step(view: View, eps: float, dt: float, stream=None) -> None:
+    check(lib().llgb_nbody_step(view.handle, float(eps), float(dt), _stream_ptr(stream)))
+
+
+def llgb_device_status(reset: bool = False) -> int:
+    code = ctypes.c_int32()
+    check(lib().llgb_device_status(ctypes.byref(code), int(reset)))
+    return code.value
+
+
+copy = llgb_copy
+pack = llgb_pack
+unpack = llgb_unpack
+nbody_step = llgb_nbody_step
+device_status = llgb_device_status

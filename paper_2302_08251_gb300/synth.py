@@ -125,3 +125,57 @@ def special_f32(n: int, seed: int) -> np.ndarray:
     rand_bits = g.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
     out = np.concatenate([fixed.view(np.uint32), nan_bits, rand_bits])
     return out.view(np.float32)
+
+
+# ---------------------------------------------------------------- device --
+# Large inputs are drawn on the device with a seeded torch generator.  They
+# are either one plain array per leaf (the values of each leaf, in record
+# order) or raw random bytes for a whole blob.
+
+def _torch_gen(seed: int, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def device_random_bytes(size: int, seed: int, device="cuda"):
+    """`size` uniformly random bytes (uint8 tensor) on `device`."""
+    import torch
+    g = _torch_gen(seed, device)
+    return torch.randint(0, 256, (max(1, size),), dtype=torch.uint8, generator=g, device=device)
+
+
+def device_fields(kind: str, n: int, seed: int, device="cuda", bits: int = 12):
+    """Leaf arrays of n records on `device`, distributed like the host
+    generators: kind is 'particle', 'int6' (with `bits`), 'mixed_f' or 'cfd'."""
+    import torch
+    g = _torch_gen(seed, device)
+
+    def unif(lo, hi, dtype=torch.float32):
+        return (torch.rand(n, generator=g, device=device, dtype=torch.float64) * (hi - lo) + lo).to(dtype)
+
+    if kind == "particle":
+        return [unif(-1.0, 1.0) for _ in range(6)] + [unif(0.0, 1.0)]
+    if kind == "int6":
+        out = []
+        for _, t in INT6:
+            if t == "u32":
+                v = torch.randint(0, 1 << bits, (n,), generator=g, device=device, dtype=torch.int64)
+            else:
+                v = torch.randint(-(1 << (bits - 1)), 1 << (bits - 1), (n,), generator=g,
+                                  device=device, dtype=torch.int64)
+            out.append(v.to(torch.int32))
+        return out
+    if kind == "mixed_f":
+        cols = [torch.randn(n, generator=g, device=device, dtype=torch.float64) * 1e3 for _ in range(3)]
+        cols.append((torch.randn(n, generator=g, device=device, dtype=torch.float64) * 1e3).float())
+        return cols
+    if kind == "cfd":
+        cols = [unif(-1.0, 1.0) for _ in range(5)]
+        cols.append(torch.randint(-(1 << 15), 1 << 15, (n,), generator=g, device=device,
+                                  dtype=torch.int32).to(torch.int16))
+        cols.append(torch.randint(0, 1 << 16, (n,), generator=g, device=device,
+                                  dtype=torch.int32).to(torch.int16))
+        return cols
+    raise ValueError(kind)

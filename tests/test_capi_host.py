@@ -1,0 +1,204 @@
+"""Host-side checks of the C ABI (no GPU needed, no compute calls).
+
+* the library builds, loads and exports every function declared in include/*.h;
+* view planning (blob count and sizes) agrees with the oracle for every
+  mapping kind, record and size class;
+* descriptor validation and the index-type rule of Sec. 2 (a view whose
+  record count or largest byte offset does not fit its index type is
+  rejected) return the documented status codes.
+"""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+import oracle
+from paper_2302_08251_gb300 import build, llgb, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(llgb_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 19
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (llgb_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = llgb.lib()
+    for n in names:
+        assert hasattr(L, n)
+
+
+def test_binding_covers_the_exports():
+    assert set(llgb.EXPORTS) <= set(declared_functions())
+
+
+def test_version_and_no_error_yet():
+    assert b"sm_103a" in llgb.lib().llgb_version()
+
+
+def host_view(record, mapping, n, index_type="u64", extents=None):
+    """Plan a view (host only) and return its blob sizes."""
+    rec = llgb.Record(record)
+    ext = extents if extents is not None else (n,)
+    keep = []
+    e = llgb.extents_desc(ext, index_type)
+    m = llgb.mapping_desc(mapping, keep)
+    h = ctypes.c_void_p()
+    llgb.check(llgb.lib().llgb_view_create(rec.handle, ctypes.byref(e), ctypes.byref(m),
+                                           ctypes.byref(h)))
+    nb = llgb.lib().llgb_view_blob_count(h)
+    sizes = [int(llgb.lib().llgb_view_blob_size(h, k)) for k in range(nb)]
+    llgb.lib().llgb_view_destroy(h)
+    return rec, sizes
+
+
+MAPPINGS = [
+    {"kind": "aos"}, {"kind": "aos", "packed": 1}, {"kind": "soa_mb"}, {"kind": "soa_sb"},
+    {"kind": "soa_sb", "subarray_align": 128}, {"kind": "aosoa", "lanes": 8},
+    {"kind": "aosoa", "lanes": 32}, {"kind": "aosoa", "lanes": 3},
+    {"kind": "bytesplit", "inner": {"kind": "soa_mb"}},
+    {"kind": "bytesplit", "inner": {"kind": "aos", "packed": 1}},
+    {"kind": "changetype", "ct": [("f64", "f32")], "inner": {"kind": "soa_mb"}},
+    {"kind": "changetype", "ct": [("f64", "f32")], "inner": {"kind": "aos"}},
+]
+
+
+@pytest.mark.parametrize("mapping", MAPPINGS, ids=str)
+@pytest.mark.parametrize("rec", [synth.MIXED_F, synth.CFD, synth.PARTICLE], ids=["mixed", "cfd", "particle"])
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 65537])
+def test_blob_sizes_agree_with_the_oracle(mapping, rec, n):
+    _, sizes = host_view(rec, mapping, n)
+    assert sizes == oracle.OracleView(rec, mapping, n).blob_sizes
+
+
+@pytest.mark.parametrize("b", [1, 3, 7, 12, 17, 31, 32])
+@pytest.mark.parametrize("n", [1, 33, 4096, 100003])
+def test_bitpack_int_blob_sizes(b, n):
+    m = {"kind": "bitpack_int", "bits": b}
+    _, sizes = host_view(synth.INT6, m, n)
+    assert sizes == oracle.OracleView(synth.INT6, m, n).blob_sizes
+
+
+@pytest.mark.parametrize("e,m", [(5, 2), (5, 10), (8, 23), (11, 52), (11, 23), (8, 52)])
+def test_bitpack_float_blob_sizes(e, m):
+    mp = {"kind": "bitpack_float", "exp": e, "man": m}
+    _, sizes = host_view(synth.MIXED_F, mp, 1001)
+    assert sizes == oracle.OracleView(synth.MIXED_F, mp, 1001).blob_sizes
+
+
+def test_full_size_workloads_fit_u32_indexing():
+    _, s = host_view(synth.CFD, {"kind": "aos"}, 0, "u32", extents=(512, 512, 512))
+    assert s == [512 ** 3 * 24]
+    _, s = host_view(synth.INT6, {"kind": "bitpack_int", "bits": 31}, 1 << 26, "u32")
+    assert len(s) == 6
+    _, s = host_view(synth.MIXED_F, {"kind": "bitpack_float", "exp": 11, "man": 52}, 1 << 25, "i32")
+    assert s == [(1 << 25) * 8] * 4
+
+
+def expect_status(record, mapping, ext, itype, status):
+    rec = llgb.Record(record)
+    keep = []
+    e = llgb.extents_desc(ext, itype)
+    m = llgb.mapping_desc(mapping, keep)
+    h = ctypes.c_void_p()
+    got = llgb.lib().llgb_view_create(rec.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(h))
+    if got == 0:
+        llgb.lib().llgb_view_destroy(h)
+    assert got == status, llgb.lib().llgb_last_error()
+    return llgb.lib().llgb_last_error().decode()
+
+
+def test_index_type_overflow_is_rejected():
+    # 2^15 records of 24 bytes: n-1 fits i16? no (32767 is the max index)
+    expect_status(synth.CFD, {"kind": "soa_mb"}, (32768,), "i16", llgb.ERR_INDEX_OVERFLOW)
+    # 1366 records x 24 B = 32784 bytes: the largest byte offset overflows i16
+    expect_status(synth.CFD, {"kind": "aos"}, (1366,), "i16", llgb.ERR_INDEX_OVERFLOW)
+    expect_status(synth.CFD, {"kind": "aos"}, (1365,), "i16", llgb.OK)
+    # 512^3 x 24 B fits u32 but not i32
+    expect_status(synth.CFD, {"kind": "aos"}, (512, 512, 512), "u32", llgb.OK)
+    expect_status(synth.CFD, {"kind": "aos"}, (512, 512, 512), "i32", llgb.ERR_INDEX_OVERFLOW)
+    expect_status(synth.CFD, {"kind": "aos"}, (512, 512, 700), "u32", llgb.ERR_INDEX_OVERFLOW)
+
+
+def test_descriptor_validation():
+    expect_status(synth.MIXED_F, {"kind": "bitpack_int", "bits": 8}, (10,), "u64",
+                  llgb.ERR_INVALID_ARG)
+    expect_status(synth.INT6, {"kind": "bitpack_float", "exp": 8, "man": 23}, (10,), "u64",
+                  llgb.ERR_INVALID_ARG)
+    expect_status(synth.INT6, {"kind": "bitpack_int", "bits": 33}, (10,), "u64",
+                  llgb.ERR_INVALID_ARG)
+    expect_status(synth.MIXED_F, {"kind": "bitpack_float", "exp": 1, "man": 23}, (10,), "u64",
+                  llgb.ERR_INVALID_ARG)
+    expect_status(synth.MIXED_F, {"kind": "bytesplit", "inner": {"kind": "bitpack_int", "bits": 3}},
+                  (10,), "u64", llgb.ERR_UNSUPPORTED)
+    expect_status(synth.MIXED_F, {"kind": "soa_sb", "subarray_align": 24}, (10,), "u64",
+                  llgb.ERR_INVALID_ARG)
+    expect_status(synth.INT6, {"kind": "changetype", "ct": [("i32", "i16")],
+                               "inner": {"kind": "soa_mb"}}, (10,), "u64", llgb.ERR_INVALID_ARG)
+
+
+def test_record_validation():
+    with pytest.raises(llgb.LlgbError):
+        llgb.Record([("a", "f32"), ("a", "f32")])
+    r = llgb.Record(synth.MIXED_F)
+    assert r.size(packed=False) == 32 and r.size(packed=True) == 28
+
+
+def test_copy_rejects_mismatched_and_unbound_views():
+    L = llgb.lib()
+    r1, r2 = llgb.Record(synth.MIXED_F), llgb.Record(synth.CFD)
+    handles = []
+    for rec, n in ((r1, 10), (r1, 11), (r2, 10)):
+        keep = []
+        e = llgb.extents_desc((n,))
+        m = llgb.mapping_desc({"kind": "soa_mb"}, keep)
+        h = ctypes.c_void_p()
+        llgb.check(L.llgb_view_create(rec.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(h)))
+        handles.append(h)
+    assert L.llgb_copy(handles[0], handles[1], None) == llgb.ERR_MISMATCH
+    assert L.llgb_copy(handles[0], handles[2], None) == llgb.ERR_MISMATCH
+    assert L.llgb_copy(handles[0], handles[0], None) == llgb.ERR_UNBOUND
+    bad = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(8)] * 4)
+    assert L.llgb_view_bind(handles[0], bad, 4) == llgb.ERR_INVALID_ARG
+    assert L.llgb_view_bind(handles[0], bad, 3) == llgb.ERR_INVALID_ARG
+    for h in handles:
+        L.llgb_view_destroy(h)
+
+
+def test_default_launch_shape_fits_the_tile_rules():
+    L = llgb.lib()
+    rec = llgb.Record(synth.CFD)
+    hs = []
+    for mp in ({"kind": "aos"}, {"kind": "aosoa", "lanes": 32}):
+        keep = []
+        e = llgb.extents_desc((1 << 20,))
+        m = llgb.mapping_desc(mp, keep)
+        h = ctypes.c_void_p()
+        llgb.check(L.llgb_view_create(rec.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(h)))
+        hs.append(h)
+    c = llgb.LaunchConfig()
+    llgb.check(L.llgb_copy_config(hs[0], hs[1], ctypes.byref(c)))
+    assert c.tile_records % 128 == 0 and c.tile_records >= 128
+    assert c.threads in (128, 256, 512, 1024)
+    for h in hs:
+        L.llgb_view_destroy(h)
