@@ -454,6 +454,13 @@ __global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ Copy
         __syncthreads();
         if (H.abort) break;
 
+        if (t == 0) {
+            for (int q = 0; q < J.nzeros; ++q) {
+                const ZeroRun& Z = J.zeros[q];
+                uint8_t* p = J.dst.blobs[Z.blob] + Z.offset;
+                for (uint32_t b = threadIdx.x; b < Z.bytes; b += blockDim.x) p[b] = 0;
+            }
+        }
         run_items(J, simg, dimg, codes, nvalid);
         if (J.npacks) {
             __syncthreads();

@@ -20,6 +20,7 @@ constexpr int kMaxLeaves = 32;  // stored leaves per side
 constexpr int kMaxItems = 64;   // per-tile work items
 constexpr int kMaxPacks = 16;   // bit-stream destination leaves
 constexpr int kImageSlack = 16; // bytes after every run in an image
+constexpr int kMaxZeros = 32;   // destination byte ranges owned by no leaf
 
 // One contiguous run of a tile in a blob.  For tile t it covers
 // [gbase + t * tile_bytes, + tile_bytes) (the last tile: tail_bytes) and
@@ -99,11 +100,21 @@ struct SideDesc {
     uint8_t pad[7];
 };
 
+// A destination byte range that no tile run covers and no leaf owns (the
+// alignment gaps between SoA single-blob sub-arrays); written as zero by the
+// CTA that handles the job's first tile.
+struct ZeroRun {
+    uint64_t offset;
+    uint32_t bytes;
+    uint32_t blob;
+};
+
 struct JobDesc {
     SideDesc src;
     SideDesc dst;
     ItemDesc items[kMaxItems];
     PackDesc packs[kMaxPacks];
+    ZeroRun zeros[kMaxZeros];
     uint64_t n;          // records
     uint32_t tile;       // records per tile
     uint32_t ntiles;     // tiles covering n
@@ -111,7 +122,8 @@ struct JobDesc {
     uint32_t code_bytes; // code staging bytes
     uint16_t nitems;
     uint16_t npacks;
-    uint32_t pad;
+    uint16_t nzeros;
+    uint16_t pad;
 };
 
 // Launch-wide parameters of the copy kernel.

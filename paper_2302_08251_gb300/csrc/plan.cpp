@@ -479,6 +479,22 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
     st = plan_side(dst, dst_ptrs, tile, job->ntiles, &job->dst, why);
     if (st != LLGB_OK) return st;
 
+    // Gaps between SoA single-blob sub-arrays belong to no leaf: zero them.
+    if (dst.base == BASE_SOA_SB) {
+        for (size_t g = 1; g < dst.stored.size(); ++g) {
+            const uint64_t from = dst.seg_end[g - 1], to = dst.sb_base[g];
+            if (to <= from) continue;
+            if (job->nzeros >= kMaxZeros || to - from > 0xFFFFFFFFull) {
+                *why = "too many or too large sub-array gaps";
+                return LLGB_ERR_UNSUPPORTED;
+            }
+            ZeroRun& z = job->zeros[job->nzeros++];
+            z.offset = from;
+            z.bytes = (uint32_t)(to - from);
+            z.blob = 0;
+        }
+    }
+
     // Code staging slots for bit-stream destination leaves.
     int slot_of[kMaxLeaves];
     uint32_t code_at = 0;

@@ -158,8 +158,9 @@ CONFIGS = [
     {"tile_records": 128, "src_stages": 1, "dst_stages": 1, "threads": 128, "ctas_per_sm": 1},
     {"tile_records": 256, "src_stages": 2, "dst_stages": 1, "threads": 256, "ctas_per_sm": 2},
     {"tile_records": 1024, "src_stages": 4, "dst_stages": 2, "threads": 512, "ctas_per_sm": 1},
-    {"tile_records": 2048, "src_stages": 3, "dst_stages": 3, "threads": 1024, "ctas_per_sm": 1},
-    {"tile_records": 512, "src_stages": 8, "dst_stages": 4, "threads": 256, "ctas_per_sm": 2},
+    {"tile_records": 2048, "src_stages": 2, "dst_stages": 1, "threads": 1024, "ctas_per_sm": 1},
+    {"tile_records": 512, "src_stages": 8, "dst_stages": 4, "threads": 256, "ctas_per_sm": 1},
+    {"tile_records": 384, "src_stages": 3, "dst_stages": 2, "threads": 256, "ctas_per_sm": 3},
 ]
 
 
@@ -176,6 +177,26 @@ def test_launch_shapes(cfg, maps):
     else:
         rec, fields = synth.CFD, synth.cfd(n, 5)
     run_pair(rec, fields, maps[0], maps[1], cfg)
+
+
+def test_single_blob_with_wide_subarray_alignment_zeroes_the_gaps():
+    n = 1001  # 4004-byte sub-arrays, each followed by a 92-byte gap at align 4096
+    rec = synth.CFD
+    fields = synth.cfd(n, 6)
+    run_pair(rec, fields, {"kind": "aos"}, {"kind": "soa_sb", "subarray_align": 4096})
+    run_pair(rec, fields, {"kind": "soa_sb", "subarray_align": 4096}, {"kind": "aosoa", "lanes": 8})
+
+
+def test_too_large_launch_shape_is_rejected():
+    n = 10000
+    src = empty_device_view(synth.CFD, {"kind": "aos"}, n)
+    dst = empty_device_view(synth.CFD, {"kind": "soa_mb"}, n)
+    with pytest.raises(llgb.LlgbError):
+        llgb.llgb_copy_with(src, dst, {"tile_records": 4096, "src_stages": 8, "dst_stages": 4,
+                                       "threads": 256, "ctas_per_sm": 1})
+    with pytest.raises(llgb.LlgbError):
+        llgb.llgb_copy_with(src, dst, {"tile_records": 100, "src_stages": 2, "dst_stages": 1,
+                                       "threads": 256, "ctas_per_sm": 1})
 
 
 def test_unaligned_single_blob_uses_the_plain_path():
