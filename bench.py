@@ -45,14 +45,17 @@ PROFILE = os.path.join(ROOT, "profiles", "copy_kernel_relayout_suite.md")
 
 # ------------------------------------------------------------ workload --
 
-def rows_spec():
+def rows_spec(only=None, scale=1):
+    """(name, config, source mapping, destination mapping) of every row.
+    `only` keeps rows whose name contains it; `scale` divides the record
+    counts (for small profiling captures)."""
     from paper_2302_08251_gb300 import synth
-    c3 = dict(record=synth.CFD, n=512 ** 3, ext=(512, 512, 512), itype="u32",
+    c3 = dict(record=synth.CFD, n=512 ** 3 // scale, ext=(512 // scale, 512, 512), itype="u32",
               static=(False, True, True), fields="cfd")
-    c1 = dict(record=synth.INT6, n=1 << 26, ext=(1 << 26,), itype="u32", static=None,
-              fields="int6")
-    c2 = dict(record=synth.MIXED_F, n=1 << 25, ext=(1 << 25,), itype="u32", static=None,
-              fields="mixed_f")
+    c1 = dict(record=synth.INT6, n=(1 << 26) // scale, ext=((1 << 26) // scale,), itype="u32",
+              static=None, fields="int6")
+    c2 = dict(record=synth.MIXED_F, n=(1 << 25) // scale, ext=((1 << 25) // scale,), itype="u32",
+              static=None, fields="mixed_f")
     soa = {"kind": "soa_mb"}
     aos = {"kind": "aos"}
     a32 = {"kind": "aosoa", "lanes": 32}
@@ -61,7 +64,7 @@ def rows_spec():
     bf = {"kind": "bitpack_float", "exp": 8, "man": 23}
     bs = {"kind": "bytesplit", "inner": soa}
     ct = {"kind": "changetype", "ct": [("f64", "f32")], "inner": soa}
-    return [
+    rows = [
         ("C3 AoS->SoA", c3, aos, soa),
         ("C3 SoA->AoS", c3, soa, aos),
         ("C3 SoA->AoSoA32", c3, soa, a32),
@@ -74,6 +77,7 @@ def rows_spec():
         ("C2 bytesplit", c2, soa, bs),
         ("C2 changetype f64->f32", c2, soa, ct),
     ]
+    return [r for r in rows if only is None or only in r[0]]
 
 
 def key(m):
@@ -83,13 +87,13 @@ def key(m):
 class Workload:
     """Device views for every row; sources are seeded and resident in HBM."""
 
-    def __init__(self, device, seed):
+    def __init__(self, device, seed, only=None, scale=1):
         import torch
         from paper_2302_08251_gb300 import llgb, synth
         self.rows = []
         self.records = {}
         cache = {}  # (config name, mapping) -> source view
-        for name, cfg, src_map, dst_map in rows_spec():
+        for name, cfg, src_map, dst_map in rows_spec(only, scale):
             cname = name.split()[0]
             rec = self.records.setdefault(cname, llgb.Record(cfg["record"]))
             kw = dict(index_type=cfg["itype"], static=cfg["static"])
@@ -306,7 +310,7 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
 
-    wl = Workload(device, seed=2302082510 + rank)
+    wl = Workload(device, seed=2302082510 + rank, only=args.only, scale=args.scale)
     stream = torch.cuda.current_stream()
     nrows = len(wl.rows)
     for _ in range(args.warmup):
@@ -350,9 +354,9 @@ def run_gpu(args):
     traffic = profiled_traffic()
 
     # n-body consumer (65,536 particles through AoS / SoA / AoSoA32 views)
-    nbody = nbody_bench(device, args) if rank == 0 else None
+    nbody = nbody_bench(device, args) if rank == 0 and not args.no_extras else None
     # end to end through host buffers
-    e2e = e2e_bench(wl, stream, args) if rank == 0 else None
+    e2e = e2e_bench(wl, stream, args) if rank == 0 and not args.no_extras else None
 
     if rank == 0:
         line = {
@@ -376,7 +380,7 @@ def run_gpu(args):
             "e2e": e2e,
             "nbody": nbody,
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and not args.no_extras:
             v, sample, _ = oracle_sample()
             line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1,
                                     "kind": "oracle", "sample": sample}
@@ -468,6 +472,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the n-body, e2e and CPU-baseline legs (profiling runs)")
+    ap.add_argument("--only", default=None, help="run only rows whose name contains this")
+    ap.add_argument("--scale", type=int, default=1, help="divide record counts (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -67,11 +67,11 @@ bool same_record(const ViewPlan& a, const ViewPlan& b) { return a.types == b.typ
 // Shared memory a launch shape needs for a pair (JobDesc planned at `tile`).
 size_t smem_needed(const JobDesc& J, const llgb_launch_config& c)
 {
-    return copy_shared_header_bytes() + (size_t)c.src_stages * J.src.img_bytes +
+    return copy_shared_header_bytes() + (size_t)c.src_stages * (J.src.img_bytes + kStageZeroBytes) +
            (size_t)c.dst_stages * J.dst.img_bytes + J.code_bytes;
 }
 
-bool valid_threads(int t) { return t == 128 || t == 256 || t == 512 || t == 1024; }
+bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
 
 // The library's default launch shape for a pair.
 llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
@@ -153,14 +153,19 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     args.tile_start = nullptr;
     args.njobs = 1;
     args.total_tiles = args.job.ntiles;
-    args.src_stage_bytes = args.job.src.img_bytes;
+    args.src_stage_bytes = args.job.src.img_bytes + kStageZeroBytes;
     args.dst_stage_bytes = args.job.dst.img_bytes;
     args.code_bytes = args.job.code_bytes;
     args.src_stages = (uint16_t)c.src_stages;
     args.dst_stages = (uint16_t)c.dst_stages;
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
-    cudaError_t e = launch_copy(args, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
+    int mode = args.job.gather;
+    if (mode != 0) {
+        const uint64_t words = (args.job.dst.img_bytes - kImageSlack) / 4u;
+        if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)c.threads) mode = 0;
+    }
+    cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
     return LLGB_OK;
 }

@@ -125,14 +125,6 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // ------------------------------------------------------- image access --
 
-__device__ __forceinline__ uint32_t elem_off(const LeafDesc& L, uint32_t r)
-{
-    if (L.lanes == 1) return L.sbase + r * L.bstride;
-    if (L.lshift != 0xFF)
-        return L.sbase + (r >> L.lshift) * L.bstride + (r & (L.lanes - 1u)) * L.size;
-    return L.sbase + (r / L.lanes) * L.bstride + (r % L.lanes) * L.size;
-}
-
 __device__ __forceinline__ uint64_t ld_elem(const uint8_t* p, int size, int align)
 {
     if (align >= size) {
@@ -172,6 +164,23 @@ __device__ __forceinline__ uint64_t ld_bits(const uint8_t* base, uint32_t pos, i
     return v & low_bits64(w);
 }
 
+// Leaf addressing held in registers for a whole loop.
+struct LeafRegs {
+    uint32_t sbase, bstride, lanes, size, lshift, align, bits;
+};
+
+__device__ __forceinline__ LeafRegs leaf_regs(const LeafDesc& L)
+{
+    return LeafRegs{L.sbase, L.bstride, L.lanes, L.size, L.lshift, L.align, L.bits};
+}
+
+__device__ __forceinline__ uint32_t eoff(const LeafRegs& L, uint32_t r)
+{
+    if (L.lanes == 1) return L.sbase + r * L.bstride;
+    if (L.lshift != 0xFF) return L.sbase + (r >> L.lshift) * L.bstride + (r & (L.lanes - 1u)) * L.size;
+    return L.sbase + (r / L.lanes) * L.bstride + (r % L.lanes) * L.size;
+}
+
 template <int G>
 struct UInt;
 template <>
@@ -184,94 +193,87 @@ template <>
 struct UInt<8> { using T = uint64_t; };
 
 template <int G>
-__device__ __forceinline__ void move_loop(const LeafDesc A, const LeafDesc B, uint32_t sb, uint32_t db,
-                                          uint32_t size, const uint8_t* simg, uint8_t* dimg,
-                                          uint32_t tile, uint32_t nvalid)
+__device__ __forceinline__ void move_loop(const LeafRegs A, const LeafRegs B, uint32_t sb, uint32_t db,
+                                          uint32_t size, const uint8_t* __restrict__ simg,
+                                          uint8_t* __restrict__ dimg, uint32_t tile, uint32_t nvalid)
 {
     using W = typename UInt<G>::T;
     for (uint32_t r = threadIdx.x; r < tile; r += blockDim.x) {
-        const uint32_t so = elem_off(A, r) + sb;
-        const uint32_t dof = elem_off(B, r) + db;
-        if (r < nvalid) {
-            for (uint32_t p = 0; p < size; p += G)
-                *reinterpret_cast<W*>(dimg + dof + p) = *reinterpret_cast<const W*>(simg + so + p);
-        } else {
-            for (uint32_t p = 0; p < size; p += G) *reinterpret_cast<W*>(dimg + dof + p) = W(0);
-        }
+        const uint32_t so = eoff(A, r) + sb;
+        const uint32_t dof = eoff(B, r) + db;
+        const bool live = r < nvalid;
+        for (uint32_t p = 0; p < size; p += G)
+            *reinterpret_cast<W*>(dimg + dof + p) = live ? *reinterpret_cast<const W*>(simg + so + p) : W(0);
     }
 }
 
-__device__ __forceinline__ uint64_t load_value(const ItemDesc& I, const SideDesc& S, const uint8_t* simg,
-                                               uint32_t r)
+// One VALUE item: load the logical value through LOP, store it through SOP.
+template <int LOP, int SOP>
+__device__ __noinline__ void value_loop(const ItemDesc I, const JobDesc& J, const uint8_t* __restrict__ simg,
+                                        uint8_t* __restrict__ dimg, uint8_t* __restrict__ codes,
+                                        uint32_t tile, uint32_t nvalid)
 {
-    switch (I.lop) {
-    case L_DIRECT: {
-        const LeafDesc& L = S.leaves[I.src_leaf];
-        return ld_elem(simg + elem_off(L, r), I.size, L.align);
+    const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
+    const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
+    const int size = I.size;
+    const uint64_t lmask = low_bits64(8 * size);
+    uint32_t code_off = 0;
+    bool wide = false;
+    if (SOP == S_BITS_INT || SOP == S_BITS_FLOAT) {
+        code_off = J.packs[I.slot].code_off;
+        wide = J.packs[I.slot].wide;
     }
-    case L_CT: {
-        const LeafDesc& L = S.leaves[I.src_leaf];
-        const uint64_t u = ld_elem(simg + elem_off(L, r), I.s_size, L.align);
-        return fconv(u, I.s_e, I.s_m, I.l_e, I.l_m);
-    }
-    case L_BITS_INT: {
-        const LeafDesc& L = S.leaves[I.src_leaf];
-        uint64_t c = ld_bits(simg + L.sbase, r * L.bits, L.bits);
-        if (I.is_signed && ((c >> (L.bits - 1)) & 1ull)) c |= ~low_bits64(L.bits);
-        return c & low_bits64(8 * I.size);
-    }
-    case L_BITS_FLOAT: {
-        const LeafDesc& L = S.leaves[I.src_leaf];
-        const uint64_t c = ld_bits(simg + L.sbase, r * L.bits, L.bits);
-        return fconv(c, I.s_e, I.s_m, I.l_e, I.l_m);
-    }
-    default: {  // L_SPLIT
+    const uint64_t dmask = low_bits64(I.d_bits);
+    const uint64_t smask = low_bits64(A.bits);
+    for (uint32_t r = threadIdx.x; r < tile; r += blockDim.x) {
         uint64_t v = 0;
-        for (int j = 0; j < I.size; ++j) {
-            const LeafDesc& L = S.leaves[I.src_leaf + j];
-            v |= (uint64_t)simg[elem_off(L, r)] << (8 * j);
+        if (r < nvalid) {
+            if (LOP == L_DIRECT) {
+                v = ld_elem(simg + eoff(A, r), size, A.align);
+            } else if (LOP == L_CT) {
+                v = fconv(ld_elem(simg + eoff(A, r), I.s_size, A.align), I.s_e, I.s_m, I.l_e, I.l_m);
+            } else if (LOP == L_BITS_INT) {
+                uint64_t c = ld_bits(simg + A.sbase, r * A.bits, A.bits);
+                if (I.is_signed && ((c >> (A.bits - 1)) & 1ull)) c |= ~smask;
+                v = c & lmask;
+            } else if (LOP == L_BITS_FLOAT) {
+                v = fconv(ld_bits(simg + A.sbase, r * A.bits, A.bits), I.s_e, I.s_m, I.l_e, I.l_m);
+            } else {  // L_SPLIT
+                for (int j = 0; j < size; ++j) {
+                    const LeafRegs S = leaf_regs(J.src.leaves[I.src_leaf + j]);
+                    v |= (uint64_t)simg[eoff(S, r)] << (8 * j);
+                }
+            }
         }
-        return v;
-    }
+        if (SOP == S_DIRECT) {
+            st_elem(dimg + eoff(B, r), size, B.align, v);
+        } else if (SOP == S_CT) {
+            st_elem(dimg + eoff(B, r), I.d_size, B.align, fconv(v, I.l_e, I.l_m, I.d_e, I.d_m));
+        } else if (SOP == S_BITS_INT || SOP == S_BITS_FLOAT) {
+            const uint64_t c = SOP == S_BITS_INT ? (v & dmask) : fconv(v, I.l_e, I.l_m, I.d_e, I.d_m);
+            if (wide)
+                reinterpret_cast<uint64_t*>(codes + code_off)[r] = c;
+            else
+                reinterpret_cast<uint32_t*>(codes + code_off)[r] = (uint32_t)c;
+        } else {  // S_SPLIT
+            for (int j = 0; j < size; ++j) {
+                const LeafRegs D = leaf_regs(J.dst.leaves[I.dst_leaf + j]);
+                dimg[eoff(D, r)] = (uint8_t)(v >> (8 * j));
+            }
+        }
     }
 }
 
-__device__ __forceinline__ void store_code(const PackDesc& P, uint8_t* codes, uint32_t r, uint64_t c)
+template <int LOP>
+__device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc& J, const uint8_t* simg,
+                                               uint8_t* dimg, uint8_t* codes, uint32_t tile, uint32_t nvalid)
 {
-    if (P.wide)
-        reinterpret_cast<uint64_t*>(codes + P.code_off)[r] = c;
-    else
-        reinterpret_cast<uint32_t*>(codes + P.code_off)[r] = (uint32_t)c;
-}
-
-__device__ __forceinline__ void store_value(const ItemDesc& I, const JobDesc& J, uint8_t* dimg, uint8_t* codes,
-                                            uint32_t r, uint64_t v)
-{
-    const SideDesc& D = J.dst;
     switch (I.sop) {
-    case S_DIRECT: {
-        const LeafDesc& L = D.leaves[I.dst_leaf];
-        st_elem(dimg + elem_off(L, r), I.size, L.align, v);
-        return;
-    }
-    case S_CT: {
-        const LeafDesc& L = D.leaves[I.dst_leaf];
-        st_elem(dimg + elem_off(L, r), I.d_size, L.align, fconv(v, I.l_e, I.l_m, I.d_e, I.d_m));
-        return;
-    }
-    case S_BITS_INT:
-        store_code(J.packs[I.slot], codes, r, v & low_bits64(I.d_bits));
-        return;
-    case S_BITS_FLOAT:
-        store_code(J.packs[I.slot], codes, r, fconv(v, I.l_e, I.l_m, I.d_e, I.d_m));
-        return;
-    default: {  // S_SPLIT
-        for (int j = 0; j < I.size; ++j) {
-            const LeafDesc& L = D.leaves[I.dst_leaf + j];
-            dimg[elem_off(L, r)] = (uint8_t)(v >> (8 * j));
-        }
-        return;
-    }
+    case S_DIRECT: value_loop<LOP, S_DIRECT>(I, J, simg, dimg, codes, tile, nvalid); break;
+    case S_CT: value_loop<LOP, S_CT>(I, J, simg, dimg, codes, tile, nvalid); break;
+    case S_BITS_INT: value_loop<LOP, S_BITS_INT>(I, J, simg, dimg, codes, tile, nvalid); break;
+    case S_BITS_FLOAT: value_loop<LOP, S_BITS_FLOAT>(I, J, simg, dimg, codes, tile, nvalid); break;
+    default: value_loop<LOP, S_SPLIT>(I, J, simg, dimg, codes, tile, nvalid); break;
     }
 }
 
@@ -282,8 +284,8 @@ __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, 
     for (int it = 0; it < J.nitems; ++it) {
         const ItemDesc I = J.items[it];
         if (I.op == ITEM_MOVE) {
-            const LeafDesc A = J.src.leaves[I.src_leaf];
-            const LeafDesc B = J.dst.leaves[I.dst_leaf];
+            const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
+            const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
             switch (I.gran) {
             case 8: move_loop<8>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
             case 4: move_loop<4>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
@@ -291,37 +293,222 @@ __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, 
             default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
             }
         } else {
-            for (uint32_t r = threadIdx.x; r < tile; r += blockDim.x) {
-                const uint64_t v = r < nvalid ? load_value(I, J.src, simg, r) : 0ull;
-                store_value(I, J, dimg, codes, r, v);
+            switch (I.lop) {
+            case L_DIRECT: value_dispatch<L_DIRECT>(I, J, simg, dimg, codes, tile, nvalid); break;
+            case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, codes, tile, nvalid); break;
+            case L_BITS_INT: value_dispatch<L_BITS_INT>(I, J, simg, dimg, codes, tile, nvalid); break;
+            case L_BITS_FLOAT: value_dispatch<L_BITS_FLOAT>(I, J, simg, dimg, codes, tile, nvalid); break;
+            default: value_dispatch<L_SPLIT>(I, J, simg, dimg, codes, tile, nvalid); break;
             }
         }
     }
 }
 
-// One thread per 32-bit word of each bit-stream destination: OR together the
-// staged codes that overlap the word.
-__device__ void run_packs(const JobDesc& J, uint8_t* dimg, const uint8_t* codes)
+// Byte moves only (the items of a gather job, for its last tile).
+__device__ __forceinline__ void run_moves(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid)
 {
-    const uint32_t tile = J.tile;
+    for (int it = 0; it < J.nitems; ++it) {
+        const ItemDesc I = J.items[it];
+        const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
+        const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
+        switch (I.gran) {
+        case 8: move_loop<8>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
+        case 4: move_loop<4>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
+        case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
+        default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
+        }
+    }
+}
+
+// One thread per 32-bit word of a bit-stream destination: OR together the
+// codes that overlap the word.
+template <bool DIRECT, bool WIDE>
+__device__ __noinline__ void pack_loop(const PackDesc P, const JobDesc& J, const uint8_t* __restrict__ simg,
+                                       uint8_t* __restrict__ dimg, const uint8_t* __restrict__ codes,
+                                       uint32_t tile, uint32_t nvalid)
+{
+    const uint32_t w = P.bits;
+    const uint32_t nwords = tile * w / 32u;
+    uint32_t* out = reinterpret_cast<uint32_t*>(dimg + P.dst_sbase);
+    LeafRegs A{};
+    if (DIRECT) A = leaf_regs(J.src.leaves[P.src_leaf]);
+    const uint64_t mask = low_bits64(w);
+    const int ssize = P.src_size;
+    for (uint32_t q = threadIdx.x; q < nwords; q += blockDim.x) {
+        const uint32_t bit0 = q * 32u;
+        const uint32_t jlo = __umulhi(bit0, P.magic);
+        uint32_t jhi = __umulhi(bit0 + 31u, P.magic);
+        if (jhi > tile - 1u) jhi = tile - 1u;
+        uint32_t word = 0;
+        for (uint32_t j = jlo; j <= jhi; ++j) {
+            uint64_t c;
+            if (DIRECT)
+                c = j < nvalid ? (ld_elem(simg + eoff(A, j), ssize, A.align) & mask) : 0ull;
+            else if (WIDE)
+                c = reinterpret_cast<const uint64_t*>(codes + P.code_off)[j];
+            else
+                c = reinterpret_cast<const uint32_t*>(codes + P.code_off)[j];
+            const int pos = (int)(j * w) - (int)bit0;
+            word |= pos >= 0 ? (uint32_t)(c << pos) : (uint32_t)(c >> (-pos));
+        }
+        out[q] = word;
+    }
+}
+
+__device__ void run_packs(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, const uint8_t* codes,
+                          uint32_t nvalid)
+{
     for (int k = 0; k < J.npacks; ++k) {
         const PackDesc P = J.packs[k];
-        const uint32_t w = P.bits;
-        const uint32_t nwords = tile * w / 32u;
-        uint32_t* out = reinterpret_cast<uint32_t*>(dimg + P.dst_sbase);
-        for (uint32_t q = threadIdx.x; q < nwords; q += blockDim.x) {
-            const uint32_t bit0 = q * 32u;
-            const uint32_t jlo = bit0 / w;
-            uint32_t jhi = (bit0 + 31u) / w;
-            if (jhi > tile - 1u) jhi = tile - 1u;
-            uint32_t word = 0;
-            for (uint32_t j = jlo; j <= jhi; ++j) {
-                const uint64_t c = P.wide ? reinterpret_cast<const uint64_t*>(codes + P.code_off)[j]
-                                          : (uint64_t) reinterpret_cast<const uint32_t*>(codes + P.code_off)[j];
-                const int pos = (int)(j * w) - (int)bit0;
-                word |= pos >= 0 ? (uint32_t)(c << pos) : (uint32_t)(c >> (-pos));
+        if (P.direct)
+            pack_loop<true, false>(P, J, simg, dimg, codes, J.tile, nvalid);
+        else if (P.wide)
+            pack_loop<false, true>(P, J, simg, dimg, codes, J.tile, nvalid);
+        else
+            pack_loop<false, false>(P, J, simg, dimg, codes, J.tile, nvalid);
+    }
+}
+
+// ------------------------------------------------------ gather programs --
+//
+// A job made only of byte moves permutes bytes: destination image byte o of
+// every full tile comes from the same source image byte (or is zero).  Each
+// thread derives, once per job, a program for each of its destination words
+// w = tid + k * blockDim.x: up to four source words and the byte selectors
+// that assemble the word with PRMT.  A full tile then costs a few loads, one
+// or three PRMTs and one store per destination word.
+
+// Destination words per thread: 16 for the 2-word form, 12 for the 4-word
+// form (registers: 2 resp. 4 per word).
+template <int FORM>
+struct GatherMax {
+    static constexpr int value = FORM == 2 ? 16 : (FORM == 4 ? 12 : 1);
+};
+
+// Source image byte feeding destination image byte o, or -1 (no leaf: zero).
+__device__ __forceinline__ int32_t gather_source(const JobDesc& J, uint32_t o)
+{
+    const SideDesc& D = J.dst;
+    for (int g = 0; g < D.nleaves; ++g) {
+        const LeafDesc& L = D.leaves[g];
+        if (o < L.sbase) continue;
+        const uint32_t d = o - L.sbase;
+        uint32_t r, e;
+        if (L.lanes == 1) {
+            r = d / L.bstride;
+            e = d - r * L.bstride;
+            if (e >= L.size || r >= J.tile) continue;
+        } else {
+            const uint32_t blk = d / L.bstride;
+            const uint32_t rem = d - blk * L.bstride;
+            const uint32_t lane = rem / L.size;
+            e = rem - lane * L.size;
+            if (lane >= L.lanes) continue;
+            r = blk * L.lanes + lane;
+            if (r >= J.tile) continue;
+        }
+        for (int it = 0; it < J.nitems; ++it) {
+            const ItemDesc& I = J.items[it];
+            if (I.dst_leaf != g || e < I.dst_byte || e >= (uint32_t)I.dst_byte + I.size) continue;
+            return (int32_t)(eoff(leaf_regs(J.src.leaves[I.src_leaf]), r) + I.src_byte + (e - I.dst_byte));
+        }
+        return -1;
+    }
+    return -1;
+}
+
+template <int FORM>
+struct GatherProgram {
+    static constexpr int K = GatherMax<FORM>::value;
+    uint32_t idx01[K];                 // source word indices i0 | i1 << 16
+    uint32_t sel01[K];                 // q0 | q1 << 16
+    uint32_t idx23[FORM == 4 ? K : 1]; // i2 | i3 << 16
+    uint32_t sel2[FORM == 4 ? K : 1];  // q2
+};
+
+template <int FORM>
+__device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_word, uint32_t nwords,
+                                             GatherProgram<FORM>& G)
+{
+    // Rolled over k so that gather_source is expanded once; each result is
+    // steered into its register slot by an unrolled select.
+#pragma unroll 1
+    for (int k = 0; k < GatherProgram<FORM>::K; ++k) {
+        const uint32_t w = threadIdx.x + k * blockDim.x;
+        uint32_t word[4], byte[4];
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+            const int32_t src = w < nwords ? gather_source(J, 4u * w + b) : -1;
+            word[b] = src < 0 ? zero_word : (uint32_t)src >> 2;
+            byte[b] = src < 0 ? 0u : (uint32_t)src & 3u;
+        }
+        uint32_t u[4] = {word[0], word[0], word[0], word[0]};
+        int nu = 1;
+#pragma unroll
+        for (int b = 1; b < 4; ++b) {
+            bool seen = false;
+            for (int x = 0; x < 4; ++x) seen |= (x < nu && u[x] == word[b]);
+            if (!seen) {
+                if (nu == 1) u[1] = word[b];
+                else if (nu == 2) u[2] = word[b];
+                else u[3] = word[b];
+                ++nu;
             }
-            out[q] = word;
+        }
+        uint32_t q0 = 0, q1 = 0, q2 = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t sh = 4u * b;
+            if (word[b] == u[0]) {
+                q0 |= byte[b] << sh;
+                q2 |= (uint32_t)b << sh;
+            } else if (word[b] == u[1]) {
+                q0 |= (4u + byte[b]) << sh;
+                q2 |= (uint32_t)b << sh;
+            } else if (word[b] == u[2]) {
+                q1 |= byte[b] << sh;
+                q2 |= (4u + b) << sh;
+            } else {
+                q1 |= (4u + byte[b]) << sh;
+                q2 |= (4u + b) << sh;
+            }
+        }
+        if (FORM == 2 && nu > 2) atomicOr(&g_device_status, 0x100u);  // planner broke its promise
+        const uint32_t i01 = u[0] | (u[1] << 16), s01 = q0 | (q1 << 16);
+        const uint32_t i23 = u[2] | (u[3] << 16);
+#pragma unroll
+        for (int kk = 0; kk < GatherProgram<FORM>::K; ++kk) {
+            if (kk == k) {
+                G.idx01[kk] = i01;
+                G.sel01[kk] = s01;
+                if (FORM == 4) {
+                    G.idx23[kk] = i23;
+                    G.sel2[kk] = q2;
+                }
+            }
+        }
+    }
+}
+
+template <int FORM>
+__device__ __forceinline__ void run_gather(const GatherProgram<FORM>& G, const uint8_t* simg, uint8_t* dimg,
+                                           uint32_t nwords)
+{
+    const uint32_t* __restrict__ s = reinterpret_cast<const uint32_t*>(simg);
+    uint32_t* __restrict__ d = reinterpret_cast<uint32_t*>(dimg);
+#pragma unroll
+    for (int k = 0; k < GatherProgram<FORM>::K; ++k) {
+        const uint32_t w = threadIdx.x + k * blockDim.x;
+        if (w < nwords) {
+            const uint32_t a = s[G.idx01[k] & 0xFFFFu], b = s[G.idx01[k] >> 16];
+            if (FORM == 2) {
+                d[w] = __byte_perm(a, b, G.sel01[k] & 0xFFFFu);
+            } else {
+                const uint32_t c = s[G.idx23[k] & 0xFFFFu], e = s[G.idx23[k] >> 16];
+                const uint32_t t0 = __byte_perm(a, b, G.sel01[k] & 0xFFFFu);
+                const uint32_t t1 = __byte_perm(c, e, G.sel01[k] >> 16);
+                d[w] = __byte_perm(t0, t1, G.sel2[k]);
+            }
         }
     }
 }
@@ -367,7 +554,10 @@ struct __align__(16) CopyShared {
 
 __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ CopyArgs a)
+// MODE 0: general items and packs.  MODE 2 / 4: every job is made of byte
+// moves; full tiles run gather programs of that form.
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ CopyArgs a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     CopyShared& H = *reinterpret_cast<CopyShared*>(smem);
@@ -380,6 +570,11 @@ __global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ Copy
     if (first >= a.total_tiles) return;
     const uint32_t count = (a.total_tiles - first + G - 1u) / G;
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
+    // The last 16 bytes of every source stage hold zeros: gather programs
+    // read destination padding from there.
+    const uint32_t zero_word = (a.src_stage_bytes - kStageZeroBytes) / 4u;
+    if (threadIdx.x < NS * 4u)
+        reinterpret_cast<uint32_t*>(src_stage + (threadIdx.x / 4u) * a.src_stage_bytes)[zero_word + threadIdx.x % 4u] = 0u;
 
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < NS; ++s) mbar_init(&H.full[s], 1);
@@ -388,6 +583,8 @@ __global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ Copy
         H.cur_job = -1;
     }
     __syncthreads();
+    GatherProgram<MODE> gp;
+    uint32_t gather_words = 0;
 
     // Producer side (thread 0): issue the TMA loads of this CTA's k-th tile.
     auto issue = [&](uint32_t k) {
@@ -429,6 +626,10 @@ __global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ Copy
             for (uint32_t w = threadIdx.x; w < zwords; w += blockDim.x) z[w] = make_uint4(0, 0, 0, 0);
             __syncthreads();
             if (threadIdx.x == 0) H.cur_job = (int)j;
+            if (MODE != 0) {
+                gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
+                build_gather<MODE>(H.job, zero_word, gather_words, gp);
+            }
         }
         const JobDesc& J = H.job;
         const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
@@ -461,10 +662,17 @@ __global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ Copy
                 for (uint32_t b = threadIdx.x; b < Z.bytes; b += blockDim.x) p[b] = 0;
             }
         }
-        run_items(J, simg, dimg, codes, nvalid);
-        if (J.npacks) {
-            __syncthreads();
-            run_packs(J, dimg, codes);
+        if (MODE != 0) {
+            if (t < J.nfull)
+                run_gather<MODE>(gp, simg, dimg, gather_words);
+            else
+                run_moves(J, simg, dimg, nvalid);
+        } else {
+            run_items(J, simg, dimg, codes, nvalid);
+            if (J.npacks) {
+                __syncthreads();
+                run_packs(J, simg, dimg, codes, nvalid);
+            }
         }
         fence_proxy_async();
         __syncthreads();
@@ -506,7 +714,10 @@ __global__ void __launch_bounds__(1024) copy_kernel(const __grid_constant__ Copy
 
 size_t copy_shared_header_bytes() { return (sizeof(CopyShared) + 15u) & ~size_t(15); }
 
-cudaError_t launch_copy(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream)
+int gather_words_per_thread(int mode) { return mode == 2 ? GatherMax<2>::value : (mode == 4 ? GatherMax<4>::value : 0); }
+
+template <int MODE>
+static cudaError_t launch_mode(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream)
 {
     static thread_local int configured_dev = -1;
     static thread_local size_t configured_bytes = 0;
@@ -514,13 +725,23 @@ cudaError_t launch_copy(const CopyArgs& args, int grid, int threads, size_t smem
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev != configured_dev || smem_bytes > configured_bytes) {
-        e = cudaFuncSetAttribute(copy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        e = cudaFuncSetAttribute(copy_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
         if (e != cudaSuccess) return e;
         configured_dev = dev;
         configured_bytes = smem_bytes;
     }
-    copy_kernel<<<grid, threads, smem_bytes, stream>>>(args);
+    copy_kernel<MODE><<<grid, threads, smem_bytes, stream>>>(args);
     return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, size_t smem_bytes,
+                        cudaStream_t stream)
+{
+    switch (mode) {
+    case 2: return launch_mode<2>(args, grid, threads, smem_bytes, stream);
+    case 4: return launch_mode<4>(args, grid, threads, smem_bytes, stream);
+    default: return launch_mode<0>(args, grid, threads, smem_bytes, stream);
+    }
 }
 
 cudaError_t read_device_status(unsigned* out, bool reset)

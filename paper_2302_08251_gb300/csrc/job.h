@@ -21,6 +21,7 @@ constexpr int kMaxItems = 64;   // per-tile work items
 constexpr int kMaxPacks = 16;   // bit-stream destination leaves
 constexpr int kImageSlack = 16; // bytes after every run in an image
 constexpr int kMaxZeros = 32;   // destination byte ranges owned by no leaf
+constexpr int kStageZeroBytes = 16;  // zero block at the end of every source stage
 
 // One contiguous run of a tile in a blob.  For tile t it covers
 // [gbase + t * tile_bytes, + tile_bytes) (the last tile: tail_bytes) and
@@ -80,13 +81,19 @@ struct ItemDesc {
     uint8_t pad[3];
 };
 
-// Packing of one bit-stream destination leaf from its staged codes.
+// Packing of one bit-stream destination leaf, one thread per output word.
+// Codes come from the staging slot, or -- for an integer leaf stored plainly
+// in the source image -- straight from the source leaf, masked to `bits`.
 struct PackDesc {
     uint32_t code_off;   // image offset of the slot (relative to code area)
     uint32_t dst_sbase;  // destination image offset of the stream
+    uint32_t magic;      // ceil(2^32 / bits): x / bits == umulhi(x, magic) for x < 2^26
     uint8_t bits;
     uint8_t wide;        // codes are 64-bit
-    uint8_t pad[6];
+    uint8_t direct;      // read codes from source leaf `src_leaf`
+    uint8_t src_leaf;
+    uint8_t src_size;    // bytes of that source element
+    uint8_t pad[3];
 };
 
 struct SideDesc {
@@ -123,7 +130,8 @@ struct JobDesc {
     uint16_t nitems;
     uint16_t npacks;
     uint16_t nzeros;
-    uint16_t pad;
+    uint8_t gather;      // full tiles use gather programs: 0 no, 2 or 4 source words
+    uint8_t pad;
 };
 
 // Launch-wide parameters of the copy kernel.
@@ -133,7 +141,7 @@ struct CopyArgs {
     const uint32_t* tile_start;  // batch: first global tile of each job (njobs+1)
     uint32_t njobs;
     uint32_t total_tiles;
-    uint32_t src_stage_bytes;    // per stage, max over jobs
+    uint32_t src_stage_bytes;    // per stage: max image over jobs + kStageZeroBytes
     uint32_t dst_stage_bytes;
     uint32_t code_bytes;
     uint16_t src_stages;

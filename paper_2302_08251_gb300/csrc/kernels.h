@@ -10,7 +10,11 @@
 namespace llgb {
 
 // copy.cu
-cudaError_t launch_copy(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream);
+// mode 0: general kernel; 2 / 4: gather kernel of that form (every job of the
+// launch must have JobDesc::gather == mode and fit its words per thread).
+cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, size_t smem_bytes,
+                        cudaStream_t stream);
+int gather_words_per_thread(int mode);
 size_t copy_shared_header_bytes();
 cudaError_t read_device_status(unsigned* out, bool reset);
 

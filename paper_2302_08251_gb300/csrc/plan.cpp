@@ -510,6 +510,7 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         P.wide = dst.stored[g].bits > 32;
         P.code_off = code_at;
         P.dst_sbase = job->dst.leaves[g].sbase;
+        P.magic = (uint32_t)(((1ull << 32) + P.bits - 1) / P.bits);
         code_at += (uint32_t)align_up((uint64_t)tile * (P.wide ? 8 : 4), 16);
         slot_of[g] = job->npacks++;
     }
@@ -517,6 +518,10 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
 
     // Items: one per leaf, or one per byte where a side splits bytes.
     const int nf = (int)src.types.size();
+    auto too_many = [&]() -> llgb_status {
+        *why = "more than 64 work items per tile";
+        return LLGB_ERR_UNSUPPORTED;
+    };
     auto add = [&](const ItemDesc& it) -> bool {
         if (job->nitems >= kMaxItems) return false;
         job->items[job->nitems++] = it;
@@ -537,7 +542,7 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
                 it.dst_leaf = (uint8_t)b.first;
                 it.gran = (uint8_t)std::min<int>(
                     size, std::min<int>(job->src.leaves[a.first].align, job->dst.leaves[b.first].align));
-                if (!add(it)) goto too_many;
+                if (!add(it)) return too_many();
             } else {
                 for (int j = 0; j < size; ++j) {
                     ItemDesc it{};
@@ -548,9 +553,17 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
                     it.src_byte = (uint8_t)(a.op == L_SPLIT ? 0 : j);
                     it.dst_leaf = (uint8_t)(b.op == L_SPLIT ? b.first + j : b.first);
                     it.dst_byte = (uint8_t)(b.op == L_SPLIT ? 0 : j);
-                    if (!add(it)) goto too_many;
+                    if (!add(it)) return too_many();
                 }
             }
+            continue;
+        }
+        if (a.op == L_DIRECT && b.op == L_BITS_INT) {
+            // Integers stored plainly pack straight from the source image.
+            PackDesc& P = job->packs[slot_of[b.first]];
+            P.direct = 1;
+            P.src_leaf = (uint8_t)a.first;
+            P.src_size = (uint8_t)size;
             continue;
         }
         {
@@ -591,13 +604,20 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
                 it.d_bits = (uint8_t)dst.stored[b.first].bits;
                 it.slot = (uint8_t)slot_of[b.first];
             }
-            if (!add(it)) goto too_many;
+            if (!add(it)) return too_many();
         }
     }
+    // Jobs made only of byte moves run full tiles through gather programs:
+    // 2 source words per destination word when every move is at least
+    // 2-byte grained and aligned, else up to 4.
+    bool all_moves = job->npacks == 0;
+    int min_gran = 8;
+    for (int k = 0; k < job->nitems; ++k) {
+        if (job->items[k].op != ITEM_MOVE) all_moves = false;
+        min_gran = std::min<int>(min_gran, job->items[k].gran);
+    }
+    job->gather = all_moves ? (min_gran >= 2 ? 2 : 4) : 0;
     return LLGB_OK;
-too_many:
-    *why = "more than 64 work items per tile";
-    return LLGB_ERR_UNSUPPORTED;
 }
 
 }  // namespace llgb

@@ -158,7 +158,7 @@ CONFIGS = [
     {"tile_records": 128, "src_stages": 1, "dst_stages": 1, "threads": 128, "ctas_per_sm": 1},
     {"tile_records": 256, "src_stages": 2, "dst_stages": 1, "threads": 256, "ctas_per_sm": 2},
     {"tile_records": 1024, "src_stages": 4, "dst_stages": 2, "threads": 512, "ctas_per_sm": 1},
-    {"tile_records": 2048, "src_stages": 2, "dst_stages": 1, "threads": 1024, "ctas_per_sm": 1},
+    {"tile_records": 2048, "src_stages": 2, "dst_stages": 1, "threads": 512, "ctas_per_sm": 1},
     {"tile_records": 512, "src_stages": 8, "dst_stages": 4, "threads": 256, "ctas_per_sm": 1},
     {"tile_records": 384, "src_stages": 3, "dst_stages": 2, "threads": 256, "ctas_per_sm": 3},
 ]
