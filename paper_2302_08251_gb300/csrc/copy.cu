@@ -336,8 +336,8 @@ __device__ __noinline__ void pack_loop(const PackDesc P, const JobDesc& J, const
     const int ssize = P.src_size;
     for (uint32_t q = threadIdx.x; q < nwords; q += blockDim.x) {
         const uint32_t bit0 = q * 32u;
-        const uint32_t jlo = __umulhi(bit0, P.magic);
-        uint32_t jhi = __umulhi(bit0 + 31u, P.magic);
+        const uint32_t jlo = w == 1 ? bit0 : __umulhi(bit0, P.magic);
+        uint32_t jhi = w == 1 ? bit0 + 31u : __umulhi(bit0 + 31u, P.magic);
         if (jhi > tile - 1u) jhi = tile - 1u;
         uint32_t word = 0;
         for (uint32_t j = jlo; j <= jhi; ++j) {

@@ -87,7 +87,7 @@ struct ItemDesc {
 struct PackDesc {
     uint32_t code_off;   // image offset of the slot (relative to code area)
     uint32_t dst_sbase;  // destination image offset of the stream
-    uint32_t magic;      // ceil(2^32 / bits): x / bits == umulhi(x, magic) for x < 2^26
+    uint32_t magic;      // ceil(2^32 / bits): x / bits == umulhi(x, magic) for x < 2^26 (0 if bits == 1)
     uint8_t bits;
     uint8_t wide;        // codes are 64-bit
     uint8_t direct;      // read codes from source leaf `src_leaf`

@@ -510,7 +510,7 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         P.wide = dst.stored[g].bits > 32;
         P.code_off = code_at;
         P.dst_sbase = job->dst.leaves[g].sbase;
-        P.magic = (uint32_t)(((1ull << 32) + P.bits - 1) / P.bits);
+        P.magic = P.bits > 1 ? (uint32_t)(((1ull << 32) + P.bits - 1) / P.bits) : 0u;  // w = 1: no division
         code_at += (uint32_t)align_up((uint64_t)tile * (P.wide ? 8 : 4), 16);
         slot_of[g] = job->npacks++;
     }
