@@ -80,17 +80,17 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const size_t smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
     llgb_launch_config c{};
-    c.threads = 512;
-    c.ctas_per_sm = 1;
+    c.threads = 256;
+    c.ctas_per_sm = 2;
     c.src_stages = 4;
-    c.dst_stages = 2;
+    c.dst_stages = 3;
     const uint32_t q = tile_quantum(src->plan, dst->plan);
     if (q == 0) return fail(LLGB_ERR_UNSUPPORTED, "AoSoA lane counts give no usable tile size");
     double sb = 0, db = 0;
     uint32_t cb = 0;
     bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
     const double per_rec = std::max(std::max(sb, db), 1.0);
-    uint64_t tile = (uint64_t)(24576.0 / per_rec) / q * q;
+    uint64_t tile = (uint64_t)(12288.0 / per_rec) / q * q;
     if (tile < q) tile = q;
     // Small views: keep at least two tiles per SM where the records allow.
     const uint64_t n = src->plan.n;
@@ -103,7 +103,7 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
     for (;;) {
         if (plan_job(src->plan, none_s, dst->plan, none_d, (uint32_t)tile, &probe, &why) != LLGB_OK)
             return fail(LLGB_ERR_UNSUPPORTED, why);
-        if (smem_needed(probe, c) <= smem_cap) break;
+        if (smem_needed(probe, c) * c.ctas_per_sm <= smem_cap) break;
         if (c.src_stages > 2) {
             --c.src_stages;
             continue;
@@ -162,8 +162,15 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
     int mode = args.job.gather;
     if (mode != 0) {
-        const uint64_t words = (args.job.dst.img_bytes - kImageSlack) / 4u;
-        if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)c.threads) mode = 0;
+        // words the gather programs cover: every run (interleaved), or the
+        // whole image up to its last slack (linear)
+        uint64_t words = (args.job.dst.img_bytes - kImageSlack) / 4u;
+        if (args.job.interleave) {
+            words = 0;
+            for (int q = 0; q < args.job.dst.nsegs; ++q) words += ((args.job.dst.segs[q].tile_bytes + 15u) & ~15u) / 4u;
+        }
+        // warp 0 of every CTA is the TMA producer; the rest run the programs
+        if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)(c.threads - 32)) mode = 0;
     }
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");

@@ -3,18 +3,19 @@
 // unpack on load, ChangeType, Bytesplit).
 //
 // One persistent kernel serves every mapping pair and, through a descriptor
-// table, many views per launch.  Each CTA walks its share of tiles:
+// table, many views per launch.  Each CTA walks its share of tiles with one
+// producer warp and several consumer warps, synchronised by mbarriers:
 //
-//   1. the source runs of the tile are brought into a shared-memory image,
-//      with 1-D TMA bulk copies (cp.async.bulk + mbarrier) for full tiles,
-//      `src_stages` tiles ahead of the one being converted;
-//   2. every item (a leaf moved byte for byte, or a value loaded, converted
-//      and stored) runs over the tile's records, one record per thread, from
-//      the source image into the destination image; bit-stream destinations
-//      first stage their codes, then one thread per 32-bit output word gathers
-//      the codes that overlap it;
-//   3. the destination runs go back to global memory with bulk stores
-//      (cp.async.bulk ... bulk_group), `dst_stages` tiles in flight.
+//   1. the producer brings the source runs of a tile into a shared-memory
+//      image with 1-D TMA bulk copies (cp.async.bulk + mbarrier transaction
+//      counts), `src_stages` tiles ahead of the consumers;
+//   2. the consumers convert the tile into a destination image: jobs made of
+//      byte moves run per-thread gather programs (PRMT); other jobs run their
+//      items (a leaf moved byte for byte, or a value loaded, converted and
+//      stored) one record per thread, and bit-stream destinations gather the
+//      codes that overlap each 32-bit output word;
+//   3. the producer writes the destination runs back with bulk stores
+//      (cp.async.bulk ... bulk_group) as soon as the consumers release them.
 //
 // The last tile of a view, and views whose runs are not 16-byte aligned, use
 // plain coalesced loads and stores instead of TMA.  Every wait on an mbarrier
@@ -79,14 +80,32 @@ __device__ __forceinline__ uint64_t global_timer_ns()
     return t;
 }
 
+// try_wait that may suspend the thread for up to `hint_ns` until the phase
+// completes, instead of returning at once: waiting warps then leave the issue
+// slots to the warps that have work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for phase `parity` of `bar` to complete, for at most ~2 s.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t spin = 0; spin < (1u << 30); ++spin) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((spin & 63u) == 0 && global_timer_ns() - t0 > 2000000000ull) break;
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (global_timer_ns() - t0 > 2000000000ull) break;
     }
     return false;
 }
@@ -124,6 +143,16 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ------------------------------------------------------- image access --
+
+// Warp 0 of a CTA is the TMA producer; the other warps are consumers, and
+// every per-tile loop below is strided over the consumer threads only.
+__device__ __forceinline__ uint32_t ctid() { return threadIdx.x - 32u; }
+__device__ __forceinline__ uint32_t cnum() { return blockDim.x - 32u; }
+
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(blockDim.x - 32u) : "memory");
+}
 
 __device__ __forceinline__ uint64_t ld_elem(const uint8_t* p, int size, int align)
 {
@@ -198,7 +227,7 @@ __device__ __forceinline__ void move_loop(const LeafRegs A, const LeafRegs B, ui
                                           uint8_t* __restrict__ dimg, uint32_t tile, uint32_t nvalid)
 {
     using W = typename UInt<G>::T;
-    for (uint32_t r = threadIdx.x; r < tile; r += blockDim.x) {
+    for (uint32_t r = ctid(); r < tile; r += cnum()) {
         const uint32_t so = eoff(A, r) + sb;
         const uint32_t dof = eoff(B, r) + db;
         const bool live = r < nvalid;
@@ -207,7 +236,27 @@ __device__ __forceinline__ void move_loop(const LeafRegs A, const LeafRegs B, ui
     }
 }
 
+__device__ __forceinline__ bool byte_aligned_width(uint32_t w) { return w == 8 || w == 16 || w == 32 || w == 64; }
+
+__device__ __forceinline__ void red_or_shared(uint32_t* p, uint32_t v)
+{
+    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+// OR the w-bit code c into the zeroed LSB-first stream at `base`, at bit pos.
+__device__ __forceinline__ void or_bits(uint8_t* base, uint32_t pos, uint32_t w, uint64_t c)
+{
+    if (c == 0) return;
+    uint32_t* words = reinterpret_cast<uint32_t*>(base) + (pos >> 5);
+    const uint32_t sh = pos & 31u;
+    const uint32_t lo = (uint32_t)c, hi = (uint32_t)(c >> 32);
+    red_or_shared(words, lo << sh);
+    if (sh + w > 32u) red_or_shared(words + 1, sh ? __funnelshift_l(lo, hi, sh) : hi);
+    if (sh + w > 64u) red_or_shared(words + 2, hi >> (32u - sh));
+}
+
 // One VALUE item: load the logical value through LOP, store it through SOP.
+// Two records per iteration keep two independent chains in flight.
 template <int LOP, int SOP>
 __device__ __noinline__ void value_loop(const ItemDesc I, const JobDesc& J, const uint8_t* __restrict__ simg,
                                         uint8_t* __restrict__ dimg, uint8_t* __restrict__ codes,
@@ -217,50 +266,67 @@ __device__ __noinline__ void value_loop(const ItemDesc I, const JobDesc& J, cons
     const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
     const int size = I.size;
     const uint64_t lmask = low_bits64(8 * size);
-    uint32_t code_off = 0;
-    bool wide = false;
-    if (SOP == S_BITS_INT || SOP == S_BITS_FLOAT) {
-        code_off = J.packs[I.slot].code_off;
-        wide = J.packs[I.slot].wide;
-    }
-    const uint64_t dmask = low_bits64(I.d_bits);
+    const bool is_bits_src = LOP == L_BITS_INT || LOP == L_BITS_FLOAT;
+    const bool a_aligned = is_bits_src && byte_aligned_width(A.bits);
+    const uint32_t abytes = A.bits / 8u;
     const uint64_t smask = low_bits64(A.bits);
-    for (uint32_t r = threadIdx.x; r < tile; r += blockDim.x) {
-        uint64_t v = 0;
-        if (r < nvalid) {
-            if (LOP == L_DIRECT) {
-                v = ld_elem(simg + eoff(A, r), size, A.align);
-            } else if (LOP == L_CT) {
-                v = fconv(ld_elem(simg + eoff(A, r), I.s_size, A.align), I.s_e, I.s_m, I.l_e, I.l_m);
-            } else if (LOP == L_BITS_INT) {
-                uint64_t c = ld_bits(simg + A.sbase, r * A.bits, A.bits);
-                if (I.is_signed && ((c >> (A.bits - 1)) & 1ull)) c |= ~smask;
-                v = c & lmask;
-            } else if (LOP == L_BITS_FLOAT) {
-                v = fconv(ld_bits(simg + A.sbase, r * A.bits, A.bits), I.s_e, I.s_m, I.l_e, I.l_m);
-            } else {  // L_SPLIT
-                for (int j = 0; j < size; ++j) {
-                    const LeafRegs S = leaf_regs(J.src.leaves[I.src_leaf + j]);
-                    v |= (uint64_t)simg[eoff(S, r)] << (8 * j);
-                }
+    const bool d_aligned = (SOP == S_BITS_INT || SOP == S_BITS_FLOAT) && byte_aligned_width(I.d_bits);
+    const uint32_t dbytes = I.d_bits / 8u;
+    const uint64_t dmask = low_bits64(I.d_bits);
+
+    auto load = [&](uint32_t r) -> uint64_t {
+        if (r >= nvalid) return 0ull;
+        if (LOP == L_DIRECT) return ld_elem(simg + eoff(A, r), size, A.align);
+        if (LOP == L_CT) return fconv(ld_elem(simg + eoff(A, r), I.s_size, A.align), I.s_e, I.s_m, I.l_e, I.l_m);
+        if (is_bits_src) {
+            uint64_t c;
+            if (a_aligned) {
+                c = ld_elem(simg + A.sbase + r * abytes, (int)abytes, (int)abytes);
+            } else if (A.bits <= 32) {
+                const uint32_t* wd = reinterpret_cast<const uint32_t*>(simg + A.sbase);
+                const uint32_t pos = r * A.bits;
+                c = __funnelshift_r(wd[pos >> 5], wd[(pos >> 5) + 1], pos & 31u) & (uint32_t)smask;
+            } else {
+                c = ld_bits(simg + A.sbase, r * A.bits, A.bits);
             }
+            if (LOP == L_BITS_INT) {
+                if (I.is_signed && ((c >> (A.bits - 1)) & 1ull)) c |= ~smask;
+                return c & lmask;
+            }
+            return fconv(c, I.s_e, I.s_m, I.l_e, I.l_m);
         }
+        uint64_t v = 0;  // L_SPLIT
+        for (int j = 0; j < size; ++j) {
+            const LeafRegs S = leaf_regs(J.src.leaves[I.src_leaf + j]);
+            v |= (uint64_t)simg[eoff(S, r)] << (8 * j);
+        }
+        return v;
+    };
+    auto store = [&](uint32_t r, uint64_t v) {
         if (SOP == S_DIRECT) {
             st_elem(dimg + eoff(B, r), size, B.align, v);
         } else if (SOP == S_CT) {
             st_elem(dimg + eoff(B, r), I.d_size, B.align, fconv(v, I.l_e, I.l_m, I.d_e, I.d_m));
         } else if (SOP == S_BITS_INT || SOP == S_BITS_FLOAT) {
             const uint64_t c = SOP == S_BITS_INT ? (v & dmask) : fconv(v, I.l_e, I.l_m, I.d_e, I.d_m);
-            if (wide)
-                reinterpret_cast<uint64_t*>(codes + code_off)[r] = c;
+            if (d_aligned)
+                st_elem(dimg + B.sbase + r * dbytes, (int)dbytes, (int)dbytes, c);
             else
-                reinterpret_cast<uint32_t*>(codes + code_off)[r] = (uint32_t)c;
+                or_bits(dimg + B.sbase, r * I.d_bits, I.d_bits, c);
         } else {  // S_SPLIT
             for (int j = 0; j < size; ++j) {
                 const LeafRegs D = leaf_regs(J.dst.leaves[I.dst_leaf + j]);
                 dimg[eoff(D, r)] = (uint8_t)(v >> (8 * j));
             }
         }
+    };
+    const uint32_t n = cnum();
+    for (uint32_t r = ctid(); r < tile; r += 2u * n) {
+        const uint32_t r2 = r + n;
+        const uint64_t v1 = load(r);
+        const uint64_t v2 = r2 < tile ? load(r2) : 0ull;
+        store(r, v1);
+        if (r2 < tile) store(r2, v2);
     }
 }
 
@@ -275,6 +341,153 @@ __device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc&
     case S_BITS_FLOAT: value_loop<LOP, S_BITS_FLOAT>(I, J, simg, dimg, codes, tile, nvalid); break;
     default: value_loop<LOP, S_SPLIT>(I, J, simg, dimg, codes, tile, nvalid); break;
     }
+}
+
+// ------------------------------------------------------ fast value loops --
+//
+// A VALUE item whose element sizes and conversion are among the common cases
+// runs here: the recipe is fixed at compile time and every thread keeps
+// kFastBatch records in flight (all loads issued before any store).
+
+constexpr int kFastBatch = 4;
+
+enum FastLoad { FL_AFF = 0, FL_AL = 1, FL_BITS = 2 };
+enum FastStore { FS_AFF = 0, FS_AL = 1, FS_BITS = 2 };
+enum FastConv { FC_INT = 0, FC_D2F = 1, FC_F2D = 2, FC_RT = 3 };
+
+template <int SZ>
+__device__ __forceinline__ uint64_t ld_sz(const uint8_t* p)
+{
+    if (SZ == 1) return *p;
+    if (SZ == 2) return *reinterpret_cast<const uint16_t*>(p);
+    if (SZ == 4) return *reinterpret_cast<const uint32_t*>(p);
+    return *reinterpret_cast<const uint64_t*>(p);
+}
+
+template <int SZ>
+__device__ __forceinline__ void st_sz(uint8_t* p, uint64_t v)
+{
+    if (SZ == 1) *p = (uint8_t)v;
+    else if (SZ == 2) *reinterpret_cast<uint16_t*>(p) = (uint16_t)v;
+    else if (SZ == 4) *reinterpret_cast<uint32_t*>(p) = (uint32_t)v;
+    else *reinterpret_cast<uint64_t*>(p) = v;
+}
+
+// LK/SK: how the source / destination element is reached; SZL/SZS: element
+// bytes (affine or whole-byte streams); CV: the conversion, applied on the
+// load side (stream -> leaf) when CONV_ON_LOAD, else on the store side.
+template <int LK, int SK, int SZL, int SZS, int CV, bool CONV_ON_LOAD>
+__device__ __noinline__ void fast_loop(const ItemDesc I, const JobDesc& J, const uint8_t* __restrict__ simg,
+                                       uint8_t* __restrict__ dimg, uint32_t tile, uint32_t nvalid)
+{
+    const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
+    const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
+    const uint32_t wa = A.bits, wb = I.d_bits;
+    const uint32_t amask = wa >= 32u ? 0xFFFFFFFFu : ((1u << wa) - 1u);
+    const bool sgn = I.is_signed;
+    const int se = CONV_ON_LOAD ? I.s_e : I.l_e, sm = CONV_ON_LOAD ? I.s_m : I.l_m;
+    const int de = CONV_ON_LOAD ? I.l_e : I.d_e, dm = CONV_ON_LOAD ? I.l_m : I.d_m;
+    const uint64_t bmask = low_bits64(wb);
+    const uint32_t n = cnum();
+    for (uint32_t r0 = ctid(); r0 < tile; r0 += kFastBatch * n) {
+        uint64_t v[kFastBatch];
+#pragma unroll
+        for (int u = 0; u < kFastBatch; ++u) {
+            const uint32_t r = r0 + u * n;
+            uint64_t c = 0;
+            if (r < nvalid) {
+                if (LK == FL_AFF) {
+                    c = ld_sz<SZL>(simg + eoff(A, r));
+                } else if (LK == FL_AL) {
+                    c = ld_sz<SZL>(simg + A.sbase + r * SZL);
+                } else {
+                    const uint32_t pos = r * wa;
+                    const uint32_t* wd = reinterpret_cast<const uint32_t*>(simg + A.sbase) + (pos >> 5);
+                    if (wa <= 32u)
+                        c = __funnelshift_r(wd[0], wd[1], pos & 31u) & amask;
+                    else
+                        c = ld_bits(simg + A.sbase, pos, wa);
+                }
+            }
+            v[u] = c;
+        }
+#pragma unroll
+        for (int u = 0; u < kFastBatch; ++u) {
+            const uint32_t r = r0 + u * n;
+            if (r >= tile) break;
+            uint64_t x = v[u];
+            if (CV == FC_INT) {
+                if (CONV_ON_LOAD && sgn && wa < 32u && ((x >> (wa - 1u)) & 1u)) x |= ~(uint64_t)amask;
+                if (CONV_ON_LOAD) x &= 0xFFFFFFFFull;
+                else x &= bmask;
+            } else if (r < nvalid) {
+                if (CV == FC_D2F) {
+                    const double d = __longlong_as_double((long long)x);
+                    x = (d == d) ? (uint64_t)__float_as_uint(__double2float_rn(d)) : fconv_general(x, 11, 52, 8, 23);
+                } else if (CV == FC_F2D) {
+                    const float f = __uint_as_float((uint32_t)x);
+                    x = (f == f) ? (uint64_t)__double_as_longlong((double)f) : fconv_general(x, 8, 23, 11, 52);
+                } else {
+                    x = fconv(x, se, sm, de, dm);
+                }
+            }
+            if (SK == FS_AFF)
+                st_sz<SZS>(dimg + eoff(B, r), x);
+            else if (SK == FS_AL)
+                st_sz<SZS>(dimg + B.sbase + r * SZS, x);
+            else
+                or_bits(dimg + B.sbase, r * wb, wb, x);
+        }
+    }
+}
+
+// Runs a VALUE item in its specialised loop; false when it has none.
+__device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                         uint32_t tile, uint32_t nvalid)
+{
+    switch (I.fast) {
+    case FK_PACK_INT32: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_INT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_INT32: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_INT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_D_F32: fast_loop<FL_AFF, FS_AL, 8, 4, FC_D2F, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL32_FROM8: fast_loop<FL_AFF, FS_AL, 8, 4, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL32_FROM4: fast_loop<FL_AFF, FS_AL, 4, 4, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL64_FROM8: fast_loop<FL_AFF, FS_AL, 8, 8, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL64_FROM4: fast_loop<FL_AFF, FS_AL, 4, 8, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL16_FROM8: fast_loop<FL_AFF, FS_AL, 8, 2, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL16_FROM4: fast_loop<FL_AFF, FS_AL, 4, 2, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_BITS_FROM8: fast_loop<FL_AFF, FS_BITS, 8, 8, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_BITS_FROM4: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_F32_D: fast_loop<FL_AL, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL32_TO8: fast_loop<FL_AL, FS_AFF, 4, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL32_TO4: fast_loop<FL_AL, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL64_TO8: fast_loop<FL_AL, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL64_TO4: fast_loop<FL_AL, FS_AFF, 8, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL16_TO8: fast_loop<FL_AL, FS_AFF, 2, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL16_TO4: fast_loop<FL_AL, FS_AFF, 2, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_BITS_TO8: fast_loop<FL_BITS, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_BITS_TO4: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_CT_D_F32: fast_loop<FL_AFF, FS_AFF, 8, 4, FC_D2F, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_CT_F32_D: fast_loop<FL_AFF, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL8_FROM8: fast_loop<FL_AFF, FS_AL, 8, 1, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_AL8_FROM4: fast_loop<FL_AFF, FS_AL, 4, 1, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL8_TO8: fast_loop<FL_AL, FS_AFF, 1, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_UNPACK_AL8_TO4: fast_loop<FL_AL, FS_AFF, 1, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    default: return false;
+    }
+}
+
+// Zero the bit streams that values are ORed into (all but whole-byte widths).
+__device__ __forceinline__ bool zero_streams(const JobDesc& J, uint8_t* dimg)
+{
+    bool any = false;
+    for (int k = 0; k < J.npacks; ++k) {
+        const PackDesc& P = J.packs[k];
+        if (P.aligned) continue;
+        uint4* z = reinterpret_cast<uint4*>(dimg + P.dst_sbase);
+        for (uint32_t q = ctid(); q < (P.bytes + 15u) / 16u; q += cnum()) z[q] = make_uint4(0, 0, 0, 0);
+        any = true;
+    }
+    return any;
 }
 
 __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint8_t* codes,
@@ -292,7 +505,7 @@ __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, 
             case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
             default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
             }
-        } else {
+        } else if (!run_fast(I, J, simg, dimg, tile, nvalid)) {
             switch (I.lop) {
             case L_DIRECT: value_dispatch<L_DIRECT>(I, J, simg, dimg, codes, tile, nvalid); break;
             case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, codes, tile, nvalid); break;
@@ -320,61 +533,12 @@ __device__ __forceinline__ void run_moves(const JobDesc& J, const uint8_t* simg,
     }
 }
 
-// One thread per 32-bit word of a bit-stream destination: OR together the
-// codes that overlap the word.
-template <bool DIRECT, bool WIDE>
-__device__ __noinline__ void pack_loop(const PackDesc P, const JobDesc& J, const uint8_t* __restrict__ simg,
-                                       uint8_t* __restrict__ dimg, const uint8_t* __restrict__ codes,
-                                       uint32_t tile, uint32_t nvalid)
-{
-    const uint32_t w = P.bits;
-    const uint32_t nwords = tile * w / 32u;
-    uint32_t* out = reinterpret_cast<uint32_t*>(dimg + P.dst_sbase);
-    LeafRegs A{};
-    if (DIRECT) A = leaf_regs(J.src.leaves[P.src_leaf]);
-    const uint64_t mask = low_bits64(w);
-    const int ssize = P.src_size;
-    for (uint32_t q = threadIdx.x; q < nwords; q += blockDim.x) {
-        const uint32_t bit0 = q * 32u;
-        const uint32_t jlo = w == 1 ? bit0 : __umulhi(bit0, P.magic);
-        uint32_t jhi = w == 1 ? bit0 + 31u : __umulhi(bit0 + 31u, P.magic);
-        if (jhi > tile - 1u) jhi = tile - 1u;
-        uint32_t word = 0;
-        for (uint32_t j = jlo; j <= jhi; ++j) {
-            uint64_t c;
-            if (DIRECT)
-                c = j < nvalid ? (ld_elem(simg + eoff(A, j), ssize, A.align) & mask) : 0ull;
-            else if (WIDE)
-                c = reinterpret_cast<const uint64_t*>(codes + P.code_off)[j];
-            else
-                c = reinterpret_cast<const uint32_t*>(codes + P.code_off)[j];
-            const int pos = (int)(j * w) - (int)bit0;
-            word |= pos >= 0 ? (uint32_t)(c << pos) : (uint32_t)(c >> (-pos));
-        }
-        out[q] = word;
-    }
-}
-
-__device__ void run_packs(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, const uint8_t* codes,
-                          uint32_t nvalid)
-{
-    for (int k = 0; k < J.npacks; ++k) {
-        const PackDesc P = J.packs[k];
-        if (P.direct)
-            pack_loop<true, false>(P, J, simg, dimg, codes, J.tile, nvalid);
-        else if (P.wide)
-            pack_loop<false, true>(P, J, simg, dimg, codes, J.tile, nvalid);
-        else
-            pack_loop<false, false>(P, J, simg, dimg, codes, J.tile, nvalid);
-    }
-}
-
 // ------------------------------------------------------ gather programs --
 //
 // A job made only of byte moves permutes bytes: destination image byte o of
 // every full tile comes from the same source image byte (or is zero).  Each
 // thread derives, once per job, a program for each of its destination words
-// w = tid + k * blockDim.x: up to four source words and the byte selectors
+// w = ctid + k * cnum: up to four source words and the byte selectors
 // that assemble the word with PRMT.  A full tile then costs a few loads, one
 // or three PRMTs and one store per destination word.
 
@@ -420,11 +584,23 @@ __device__ __forceinline__ int32_t gather_source(const JobDesc& J, uint32_t o)
 template <int FORM>
 struct GatherProgram {
     static constexpr int K = GatherMax<FORM>::value;
-    uint32_t idx01[K];                 // source word indices i0 | i1 << 16
-    uint32_t sel01[K];                 // q0 | q1 << 16
-    uint32_t idx23[FORM == 4 ? K : 1]; // i2 | i3 << 16
-    uint32_t sel2[FORM == 4 ? K : 1];  // q2
+    uint32_t idx01[K];                         // source word indices i0 | i1 << 16
+    uint32_t sel01[K];                         // q0 | q1 << 16
+    uint32_t idx23[FORM == 4 ? K : 1];         // i2 | i3 << 16
+    uint32_t sel2[FORM == 4 ? K : 1];          // q2
+    uint32_t dstw[FORM == 4 ? (K + 1) / 2 : 1]; // destination word of slot k (16 bits each; 0xFFFF: none)
 };
+
+// Destination word of consumer slot x: x itself, or -- interleaved -- word
+// x / nsegs of run x % nsegs (all runs of equal size).  0xFFFFFFFF: none.
+__device__ __forceinline__ uint32_t gather_slot_word(const JobDesc& J, uint32_t x, uint32_t nwords)
+{
+    if (!J.interleave) return x < nwords ? x : 0xFFFFFFFFu;
+    const uint32_t nseg = J.dst.nsegs;
+    const uint32_t seg = x % nseg, p = x / nseg;
+    const uint32_t seg_words = ((J.dst.segs[seg].tile_bytes + 15u) & ~15u) / 4u;
+    return p < seg_words ? J.dst.segs[seg].sbase / 4u + p : 0xFFFFFFFFu;
+}
 
 template <int FORM>
 __device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_word, uint32_t nwords,
@@ -434,11 +610,12 @@ __device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_wor
     // steered into its register slot by an unrolled select.
 #pragma unroll 1
     for (int k = 0; k < GatherProgram<FORM>::K; ++k) {
-        const uint32_t w = threadIdx.x + k * blockDim.x;
+        const uint32_t w = FORM == 4 ? gather_slot_word(J, ctid() + k * cnum(), nwords)
+                                     : (ctid() + k * cnum() < nwords ? ctid() + k * cnum() : 0xFFFFFFFFu);
         uint32_t word[4], byte[4];
 #pragma unroll 1
         for (int b = 0; b < 4; ++b) {
-            const int32_t src = w < nwords ? gather_source(J, 4u * w + b) : -1;
+            const int32_t src = w != 0xFFFFFFFFu ? gather_source(J, 4u * w + b) : -1;
             word[b] = src < 0 ? zero_word : (uint32_t)src >> 2;
             byte[b] = src < 0 ? 0u : (uint32_t)src & 3u;
         }
@@ -484,6 +661,8 @@ __device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_wor
                 if (FORM == 4) {
                     G.idx23[kk] = i23;
                     G.sel2[kk] = q2;
+                    const uint32_t half = (w == 0xFFFFFFFFu ? 0xFFFFu : (w & 0xFFFFu)) << (16 * (kk & 1));
+                    G.dstw[kk / 2] = (G.dstw[kk / 2] & ~(0xFFFFu << (16 * (kk & 1)))) | half;
                 }
             }
         }
@@ -496,40 +675,50 @@ __device__ __forceinline__ void run_gather(const GatherProgram<FORM>& G, const u
 {
     const uint32_t* __restrict__ s = reinterpret_cast<const uint32_t*>(simg);
     uint32_t* __restrict__ d = reinterpret_cast<uint32_t*>(dimg);
+    constexpr int K = GatherProgram<FORM>::K;
+    // every source word first, then the stores: K loads in flight per thread
+    uint32_t a[K], b[K], c[FORM == 4 ? K : 1], e[FORM == 4 ? K : 1];
 #pragma unroll
-    for (int k = 0; k < GatherProgram<FORM>::K; ++k) {
-        const uint32_t w = threadIdx.x + k * blockDim.x;
-        if (w < nwords) {
-            const uint32_t a = s[G.idx01[k] & 0xFFFFu], b = s[G.idx01[k] >> 16];
+    for (int k = 0; k < K; ++k) {
+        a[k] = s[G.idx01[k] & 0xFFFFu];
+        b[k] = s[G.idx01[k] >> 16];
+        if (FORM == 4) {
+            c[k] = s[G.idx23[k] & 0xFFFFu];
+            e[k] = s[G.idx23[k] >> 16];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t w = FORM == 4 ? (G.dstw[k / 2] >> (16 * (k & 1))) & 0xFFFFu : ctid() + k * cnum();
+        if (FORM == 4 ? w != 0xFFFFu : w < nwords) {
             if (FORM == 2) {
-                d[w] = __byte_perm(a, b, G.sel01[k] & 0xFFFFu);
+                d[w] = __byte_perm(a[k], b[k], G.sel01[k] & 0xFFFFu);
             } else {
-                const uint32_t c = s[G.idx23[k] & 0xFFFFu], e = s[G.idx23[k] >> 16];
-                const uint32_t t0 = __byte_perm(a, b, G.sel01[k] & 0xFFFFu);
-                const uint32_t t1 = __byte_perm(c, e, G.sel01[k] >> 16);
+                const uint32_t t0 = __byte_perm(a[k], b[k], G.sel01[k] & 0xFFFFu);
+                const uint32_t t1 = __byte_perm(c[k], e[k], G.sel01[k] >> 16);
                 d[w] = __byte_perm(t0, t1, G.sel2[k]);
             }
         }
     }
 }
 
-// Plain copy of `bytes` between global and shared memory by all threads.
+// Plain copy of `bytes` between global and shared memory by the consumers.
 __device__ void plain_copy(uint8_t* dst, const uint8_t* src, uint32_t bytes)
 {
     const uintptr_t both = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src);
     uint32_t done = 0;
     if ((both & 15u) == 0) {
         const uint32_t n16 = bytes / 16u;
-        for (uint32_t k = threadIdx.x; k < n16; k += blockDim.x)
+        for (uint32_t k = ctid(); k < n16; k += cnum())
             reinterpret_cast<uint4*>(dst)[k] = reinterpret_cast<const uint4*>(src)[k];
         done = n16 * 16u;
     } else if ((both & 3u) == 0) {
         const uint32_t n4 = bytes / 4u;
-        for (uint32_t k = threadIdx.x; k < n4; k += blockDim.x)
+        for (uint32_t k = ctid(); k < n4; k += cnum())
             reinterpret_cast<uint32_t*>(dst)[k] = reinterpret_cast<const uint32_t*>(src)[k];
         done = n4 * 4u;
     }
-    for (uint32_t k = done + threadIdx.x; k < bytes; k += blockDim.x) dst[k] = src[k];
+    for (uint32_t k = done + ctid(); k < bytes; k += cnum()) dst[k] = src[k];
 }
 
 __device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g)
@@ -545,14 +734,200 @@ __device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g)
 }
 
 struct __align__(16) CopyShared {
-    uint64_t full[8];
+    uint64_t full[8];    // source stage s holds its tile (TMA transaction count)
+    uint64_t empty[8];   // consumers are done reading source stage s
+    uint64_t dfull[4];   // consumers have written destination stage d
+    uint64_t dempty[4];  // the store of destination stage d has read it
     int abort;
-    int cur_job;
-    int pad[2];
-    JobDesc job;
+    int pad[3];
+    JobDesc job;         // the consumers' copy of the current job
 };
 
 __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+struct TileRef {
+    const JobDesc* job;  // descriptor in param or global memory
+    uint32_t j;          // job index
+    uint32_t t;          // tile index within the job
+};
+
+__device__ __forceinline__ TileRef tile_ref(const CopyArgs& a, uint32_t g)
+{
+    const uint32_t j = job_of(a, g);
+    return TileRef{a.table ? a.table + j : &a.job, j, g - (a.table ? a.tile_start[j] : 0u)};
+}
+
+__device__ __forceinline__ bool tile_bulk_in(const JobDesc* J, uint32_t t) { return t < J->nfull && J->src.bulk_ok; }
+__device__ __forceinline__ bool tile_bulk_out(const JobDesc* J, uint32_t t) { return t < J->nfull && J->dst.bulk_ok; }
+
+// Producer warp: TMA loads `src_stages` tiles ahead, bulk stores as the
+// consumers finish each destination stage.
+__device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint8_t* dst_stage, uint32_t first,
+                         uint32_t count)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t G = gridDim.x, NS = a.src_stages, ND = a.dst_stages;
+
+    auto issue_load = [&](uint32_t k) {
+        const TileRef R = tile_ref(a, first + k * G);
+        const JobDesc* J = R.job;
+        if (!tile_bulk_in(J, R.t)) return;
+        const uint32_t s = k % NS;
+        uint8_t* img = src_stage + s * a.src_stage_bytes;
+        const int nsegs = J->src.nsegs;
+        if (lane == 0) {
+            uint32_t total = 0;
+            for (int q = 0; q < nsegs; ++q) total += J->src.segs[q].tile_bytes;
+            mbar_arrive_expect_tx(&H.full[s], total);
+        }
+        for (int q = (int)lane; q < nsegs; q += 32) {
+            const SegDesc S = J->src.segs[q];
+            bulk_load(img + S.sbase, J->src.blobs[S.blob] + S.gbase + (uint64_t)R.t * S.tile_bytes, S.tile_bytes,
+                      &H.full[s]);
+        }
+    };
+
+    for (uint32_t k = 0; k < NS && k < count; ++k) issue_load(k);
+    for (uint32_t k = 0; k < count; ++k) {
+        const uint32_t d = k % ND;
+        if (!mbar_wait_bounded(&H.dfull[d], (k / ND) & 1u)) {
+            H.abort = 1;
+            break;
+        }
+        const TileRef R = tile_ref(a, first + k * G);
+        if (tile_bulk_out(R.job, R.t)) {
+            const JobDesc* J = R.job;
+            uint8_t* img = dst_stage + d * a.dst_stage_bytes;
+            for (int q = (int)lane; q < J->dst.nsegs; q += 32) {
+                const SegDesc S = J->dst.segs[q];
+                bulk_store(J->dst.blobs[S.blob] + S.gbase + (uint64_t)R.t * S.tile_bytes, img + S.sbase,
+                           S.tile_bytes);
+            }
+        }
+        // One group per tile (empty for tiles the consumers stored): keeping
+        // ND-1 groups in flight, the group of tile k-ND+1 has read its stage,
+        // which tile k+1 reuses.
+        bulk_commit();
+        bulk_wait_read((int)ND - 1);
+        __syncwarp();
+        if (lane == 0 && k + 1 >= ND) mbar_arrive(&H.dempty[(k + 1) % ND]);
+        if (k + NS < count) {
+            if (!mbar_wait_bounded(&H.empty[k % NS], (k / NS) & 1u)) {
+                H.abort = 1;
+                break;
+            }
+            issue_load(k + NS);
+        }
+        if (H.abort) break;
+    }
+    bulk_wait_all();
+}
+
+// Consumer warps: convert each tile from its source stage into a destination
+// stage, or load / store it themselves where TMA does not apply.
+template <int MODE>
+__device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint8_t* dst_stage, uint8_t* codes,
+                         uint32_t first, uint32_t count)
+{
+    const uint32_t G = gridDim.x, NS = a.src_stages, ND = a.dst_stages;
+    const uint32_t zero_word = (a.src_stage_bytes - kStageZeroBytes) / 4u;
+    const bool warp_leader = (threadIdx.x & 31u) == 0;
+    GatherProgram<MODE> gp;
+    uint32_t gather_words = 0;
+    uint32_t phase = 0;        // per source stage: parity of the next full phase
+    uint32_t zeroed = 0;       // destination stages whose padding bytes are zero (current job)
+    int cur_job = -1;
+
+    for (uint32_t k = 0; k < count; ++k) {
+        const uint32_t g = first + k * G;
+        const uint32_t j = job_of(a, g);
+        if ((int)j != cur_job) {
+            consumer_sync();
+            const uint2* from = reinterpret_cast<const uint2*>(a.table ? a.table + j : &a.job);
+            uint2* to = reinterpret_cast<uint2*>(&H.job);
+            for (uint32_t w = ctid(); w < sizeof(JobDesc) / 8u; w += cnum()) to[w] = from[w];
+            consumer_sync();
+            cur_job = (int)j;
+            zeroed = 0;
+            if (MODE != 0) {
+                gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
+                build_gather<MODE>(H.job, zero_word, gather_words, gp);
+            }
+        }
+        const JobDesc& J = H.job;
+        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t nvalid = (t + 1u < J.ntiles) ? J.tile : (uint32_t)(J.n - (uint64_t)t * J.tile);
+        const uint32_t s = k % NS, d = k % ND;
+        uint8_t* simg = src_stage + s * a.src_stage_bytes;
+        uint8_t* dimg = dst_stage + d * a.dst_stage_bytes;
+        const bool bulk_in = t < J.nfull && J.src.bulk_ok;
+        const bool bulk_out = t < J.nfull && J.dst.bulk_ok;
+
+        bool ok = true;
+        if (bulk_in) {
+            ok = mbar_wait_bounded(&H.full[s], (phase >> s) & 1u);
+            phase ^= 1u << s;
+        } else {
+            const bool last = (t + 1u == J.ntiles);
+            for (int q = 0; q < J.src.nsegs; ++q) {
+                const SegDesc& S = J.src.segs[q];
+                plain_copy(simg + S.sbase, J.src.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes,
+                           last ? S.tail_bytes : S.tile_bytes);
+            }
+        }
+        ok = mbar_wait_bounded(&H.dempty[d], ((k / ND) + 1u) & 1u) && ok;
+        if (!ok) H.abort = 1;
+        consumer_sync();
+        if (H.abort) break;
+
+        // Items write leaf bytes only: their stage must start with zero padding.
+        // (A gather program writes every word, zeros included.)
+        const bool items_here = MODE == 0 || t >= J.nfull;
+        if (items_here && !(zeroed & (1u << d))) {
+            uint4* z = reinterpret_cast<uint4*>(dimg);
+            for (uint32_t w = ctid(); w < a.dst_stage_bytes / 16u; w += cnum()) z[w] = make_uint4(0, 0, 0, 0);
+            zeroed |= 1u << d;
+            consumer_sync();
+        }
+        if (t == 0) {
+            for (int q = 0; q < J.nzeros; ++q) {
+                const ZeroRun& Z = J.zeros[q];
+                uint8_t* p = J.dst.blobs[Z.blob] + Z.offset;
+                for (uint32_t b = ctid(); b < Z.bytes; b += cnum()) p[b] = 0;
+            }
+        }
+        if (MODE != 0) {
+            if (t < J.nfull) {
+                run_gather<MODE>(gp, simg, dimg, gather_words);
+                zeroed |= 1u << d;
+            } else {
+                run_moves(J, simg, dimg, nvalid);
+            }
+        } else {
+            if (zero_streams(J, dimg)) consumer_sync();
+            run_items(J, simg, dimg, codes, nvalid);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (warp_leader) mbar_arrive(&H.empty[s]);
+        if (!bulk_out) {
+            consumer_sync();
+            const bool last = (t + 1u == J.ntiles);
+            for (int q = 0; q < J.dst.nsegs; ++q) {
+                const SegDesc& S = J.dst.segs[q];
+                plain_copy(J.dst.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes, dimg + S.sbase,
+                           last ? S.tail_bytes : S.tile_bytes);
+            }
+            __syncwarp();
+        }
+        if (warp_leader) mbar_arrive(&H.dfull[d]);
+    }
+}
 
 // MODE 0: general items and packs.  MODE 2 / 4: every job is made of byte
 // moves; full tiles run gather programs of that form.
@@ -570,144 +945,35 @@ __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ Co
     if (first >= a.total_tiles) return;
     const uint32_t count = (a.total_tiles - first + G - 1u) / G;
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
+    const uint32_t consumer_warps = blockDim.x / 32u - 1u;
+
     // The last 16 bytes of every source stage hold zeros: gather programs
     // read destination padding from there.
     const uint32_t zero_word = (a.src_stage_bytes - kStageZeroBytes) / 4u;
     if (threadIdx.x < NS * 4u)
         reinterpret_cast<uint32_t*>(src_stage + (threadIdx.x / 4u) * a.src_stage_bytes)[zero_word + threadIdx.x % 4u] = 0u;
-
     if (threadIdx.x == 0) {
-        for (uint32_t s = 0; s < NS; ++s) mbar_init(&H.full[s], 1);
+        for (uint32_t s = 0; s < NS; ++s) {
+            mbar_init(&H.full[s], 1);
+            mbar_init(&H.empty[s], consumer_warps);
+        }
+        for (uint32_t d = 0; d < ND; ++d) {
+            mbar_init(&H.dfull[d], consumer_warps);
+            mbar_init(&H.dempty[d], 1);
+        }
         fence_barrier_init();
         H.abort = 0;
-        H.cur_job = -1;
     }
     __syncthreads();
-    GatherProgram<MODE> gp;
-    uint32_t gather_words = 0;
 
-    // Producer side (thread 0): issue the TMA loads of this CTA's k-th tile.
-    auto issue = [&](uint32_t k) {
-        const uint32_t g = first + k * G;
-        const uint32_t j = job_of(a, g);
-        const JobDesc* J = a.table ? a.table + j : &a.job;
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
-        if (t >= J->nfull || !J->src.bulk_ok) return;
-        const uint32_t s = k % NS;
-        uint8_t* img = src_stage + s * a.src_stage_bytes;
-        uint32_t total = 0;
-        for (int q = 0; q < J->src.nsegs; ++q) total += J->src.segs[q].tile_bytes;
-        mbar_arrive_expect_tx(&H.full[s], total);
-        for (int q = 0; q < J->src.nsegs; ++q) {
-            const SegDesc& S = J->src.segs[q];
-            bulk_load(img + S.sbase, J->src.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes,
-                      S.tile_bytes, &H.full[s]);
-        }
-    };
+    if (threadIdx.x < 32u)
+        producer(a, H, src_stage, dst_stage, first, count);
+    else
+        consumer<MODE>(a, H, src_stage, dst_stage, codes, first, count);
 
-    if (threadIdx.x == 0)
-        for (uint32_t k = 0; k < NS && k < count; ++k) issue(k);
-
-    uint32_t phase = 0;
-    uint32_t k = 0;
-    for (; k < count; ++k) {
-        const uint32_t g = first + k * G;
-        const uint32_t j = job_of(a, g);
-        if ((int)j != H.cur_job) {
-            __syncthreads();
-            if (threadIdx.x == 0) bulk_wait_read(0);
-            __syncthreads();
-            const JobDesc* src_desc = a.table ? a.table + j : &a.job;
-            const uint2* from = reinterpret_cast<const uint2*>(src_desc);
-            uint2* to = reinterpret_cast<uint2*>(&H.job);
-            for (uint32_t w = threadIdx.x; w < sizeof(JobDesc) / 8u; w += blockDim.x) to[w] = from[w];
-            uint4* z = reinterpret_cast<uint4*>(dst_stage);
-            const uint32_t zwords = (ND * a.dst_stage_bytes + a.code_bytes) / 16u;
-            for (uint32_t w = threadIdx.x; w < zwords; w += blockDim.x) z[w] = make_uint4(0, 0, 0, 0);
-            __syncthreads();
-            if (threadIdx.x == 0) H.cur_job = (int)j;
-            if (MODE != 0) {
-                gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
-                build_gather<MODE>(H.job, zero_word, gather_words, gp);
-            }
-        }
-        const JobDesc& J = H.job;
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
-        const uint32_t nvalid = (t + 1u < J.ntiles) ? J.tile : (uint32_t)(J.n - (uint64_t)t * J.tile);
-        const uint32_t s = k % NS, d = k % ND;
-        uint8_t* simg = src_stage + s * a.src_stage_bytes;
-        uint8_t* dimg = dst_stage + d * a.dst_stage_bytes;
-        const bool bulk_in = t < J.nfull && J.src.bulk_ok;
-        const bool bulk_out = t < J.nfull && J.dst.bulk_ok;
-
-        if (bulk_in) {
-            if (!mbar_wait_bounded(&H.full[s], (phase >> s) & 1u)) H.abort = 1;
-            phase ^= 1u << s;
-        } else {
-            const bool last = (t + 1u == J.ntiles);
-            for (int q = 0; q < J.src.nsegs; ++q) {
-                const SegDesc& S = J.src.segs[q];
-                plain_copy(simg + S.sbase, J.src.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes,
-                           last ? S.tail_bytes : S.tile_bytes);
-            }
-        }
-        if (threadIdx.x == 0) bulk_wait_read((int)ND - 1);
-        __syncthreads();
-        if (H.abort) break;
-
-        if (t == 0) {
-            for (int q = 0; q < J.nzeros; ++q) {
-                const ZeroRun& Z = J.zeros[q];
-                uint8_t* p = J.dst.blobs[Z.blob] + Z.offset;
-                for (uint32_t b = threadIdx.x; b < Z.bytes; b += blockDim.x) p[b] = 0;
-            }
-        }
-        if (MODE != 0) {
-            if (t < J.nfull)
-                run_gather<MODE>(gp, simg, dimg, gather_words);
-            else
-                run_moves(J, simg, dimg, nvalid);
-        } else {
-            run_items(J, simg, dimg, codes, nvalid);
-            if (J.npacks) {
-                __syncthreads();
-                run_packs(J, simg, dimg, codes, nvalid);
-            }
-        }
-        fence_proxy_async();
-        __syncthreads();
-
-        if (bulk_out) {
-            if (threadIdx.x == 0) {
-                for (int q = 0; q < J.dst.nsegs; ++q) {
-                    const SegDesc& S = J.dst.segs[q];
-                    bulk_store(J.dst.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes, dimg + S.sbase,
-                               S.tile_bytes);
-                }
-                bulk_commit();
-            }
-        } else {
-            const bool last = (t + 1u == J.ntiles);
-            for (int q = 0; q < J.dst.nsegs; ++q) {
-                const SegDesc& S = J.dst.segs[q];
-                plain_copy(J.dst.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes, dimg + S.sbase,
-                           last ? S.tail_bytes : S.tile_bytes);
-            }
-        }
-        if (threadIdx.x == 0 && k + NS < count) issue(k + NS);
-    }
-
-    if (threadIdx.x == 0) {
-        if (H.abort) {
-            atomicOr(&g_device_status, (unsigned)LLGB_ERR_TIMEOUT);
-            // let the loads already issued land before the CTA goes away
-            for (uint32_t q = k + 1; q < k + NS && q < count; ++q) {
-                const uint32_t s = q % NS;
-                mbar_wait_bounded(&H.full[s], (phase >> s) & 1u);
-            }
-        }
-        bulk_wait_all();
-    }
+    // Both roles return after bounded waits, so every thread gets here.
+    __syncthreads();
+    if (H.abort && threadIdx.x == 0) atomicOr(&g_device_status, (unsigned)LLGB_ERR_TIMEOUT);
 }
 
 // ------------------------------------------------------------ launcher --

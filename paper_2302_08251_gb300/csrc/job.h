@@ -77,23 +77,50 @@ struct ItemDesc {
     uint8_t d_size;      // destination stored bytes (S_CT)
     uint8_t s_bits;      // source bits (L_BITS_*)
     uint8_t d_bits;      // destination bits (S_BITS_*)
-    uint8_t slot;        // code staging slot (S_BITS_*)
+    uint8_t fast;        // FastKind of the specialised loop, FK_GENERIC if none
     uint8_t pad[3];
 };
 
-// Packing of one bit-stream destination leaf, one thread per output word.
-// Codes come from the staging slot, or -- for an integer leaf stored plainly
-// in the source image -- straight from the source leaf, masked to `bits`.
+// Specialised VALUE loops (element sizes and conversion fixed at compile time).
+enum FastKind : uint8_t {
+    FK_GENERIC = 0,
+    FK_PACK_INT32,        // 4-byte integer leaf -> stream of <= 32 bits
+    FK_UNPACK_INT32,      // stream of <= 32 bits -> 4-byte integer leaf
+    FK_PACK_D_F32,        // f64 leaf -> (8,23) stream, hardware conversion
+    FK_PACK_AL32_FROM8,   // float leaf -> 32-bit stream (any format)
+    FK_PACK_AL32_FROM4,
+    FK_PACK_AL64_FROM8,   // -> 64-bit stream
+    FK_PACK_AL64_FROM4,
+    FK_PACK_AL16_FROM8,   // -> 16-bit stream
+    FK_PACK_AL16_FROM4,
+    FK_PACK_BITS_FROM8,   // -> stream of any other width
+    FK_PACK_BITS_FROM4,
+    FK_UNPACK_F32_D,      // (8,23) stream -> f64 leaf, hardware conversion
+    FK_UNPACK_AL32_TO8,
+    FK_UNPACK_AL32_TO4,
+    FK_UNPACK_AL64_TO8,
+    FK_UNPACK_AL64_TO4,
+    FK_UNPACK_AL16_TO8,
+    FK_UNPACK_AL16_TO4,
+    FK_UNPACK_BITS_TO8,
+    FK_UNPACK_BITS_TO4,
+    FK_CT_D_F32,          // ChangeType store f64 -> f32
+    FK_CT_F32_D,          // ChangeType load f32 -> f64
+    FK_PACK_AL8_FROM8,    // -> 8-bit stream
+    FK_PACK_AL8_FROM4,
+    FK_UNPACK_AL8_TO8,
+    FK_UNPACK_AL8_TO4
+};
+
+// A bit-stream destination leaf.  Values are ORed into the stream, so the
+// consumers zero its `bytes` at `dst_sbase` before every tile -- unless the
+// width is 8, 16, 32 or 64 bits, where codes are stored whole.
 struct PackDesc {
-    uint32_t code_off;   // image offset of the slot (relative to code area)
     uint32_t dst_sbase;  // destination image offset of the stream
-    uint32_t magic;      // ceil(2^32 / bits): x / bits == umulhi(x, magic) for x < 2^26 (0 if bits == 1)
+    uint32_t bytes;      // stream bytes per tile
     uint8_t bits;
-    uint8_t wide;        // codes are 64-bit
-    uint8_t direct;      // read codes from source leaf `src_leaf`
-    uint8_t src_leaf;
-    uint8_t src_size;    // bytes of that source element
-    uint8_t pad[3];
+    uint8_t aligned;
+    uint8_t pad[6];
 };
 
 struct SideDesc {
@@ -131,7 +158,7 @@ struct JobDesc {
     uint16_t npacks;
     uint16_t nzeros;
     uint8_t gather;      // full tiles use gather programs: 0 no, 2 or 4 source words
-    uint8_t pad;
+    uint8_t interleave;  // 4-word gathers: deal destination words round-robin over the runs
 };
 
 // Launch-wide parameters of the copy kernel.

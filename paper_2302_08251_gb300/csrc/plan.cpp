@@ -454,6 +454,48 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
     return LLGB_OK;
 }
 
+static bool fmt_is(int e, int m, int fe, int fm) { return e == fe && m == fm; }
+
+// The specialised loop a VALUE item can run in (FastKind), or FK_GENERIC.
+static int fast_kind(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
+{
+    const bool a_aff = A.kind == LEAF_AFFINE, b_aff = B.kind == LEAF_AFFINE;
+    const bool a_al = A.kind == LEAF_BITS && (A.bits == 8 || A.bits == 16 || A.bits == 32 || A.bits == 64);
+    const bool b_al = B.kind == LEAF_BITS && (B.bits == 8 || B.bits == 16 || B.bits == 32 || B.bits == 64);
+    const int size = it.size;
+    // integers: plain leaf <-> bit stream of at most 32 bits, 4-byte leaves
+    // (whole-byte widths are stored whole by the generic loop, not ORed)
+    if (it.lop == L_DIRECT && it.sop == S_BITS_INT && a_aff && size == 4 && A.align >= 4 && it.d_bits <= 32 && !b_al)
+        return FK_PACK_INT32;
+    if (it.lop == L_BITS_INT && it.sop == S_DIRECT && b_aff && size == 4 && B.align >= 4 && A.bits <= 32)
+        return FK_UNPACK_INT32;
+    // floats into / out of bit streams
+    if (it.lop == L_DIRECT && it.sop == S_BITS_FLOAT && a_aff && A.align >= size && (size == 4 || size == 8)) {
+        if (b_al && it.d_bits == 32 && size == 8 && fmt_is(it.d_e, it.d_m, 8, 23)) return FK_PACK_D_F32;
+        if (b_al && it.d_bits == 32) return size == 8 ? FK_PACK_AL32_FROM8 : FK_PACK_AL32_FROM4;
+        if (b_al && it.d_bits == 64) return size == 8 ? FK_PACK_AL64_FROM8 : FK_PACK_AL64_FROM4;
+        if (b_al && it.d_bits == 16) return size == 8 ? FK_PACK_AL16_FROM8 : FK_PACK_AL16_FROM4;
+        if (b_al && it.d_bits == 8) return size == 8 ? FK_PACK_AL8_FROM8 : FK_PACK_AL8_FROM4;
+        return size == 8 ? FK_PACK_BITS_FROM8 : FK_PACK_BITS_FROM4;
+    }
+    if (it.lop == L_BITS_FLOAT && it.sop == S_DIRECT && b_aff && B.align >= size && (size == 4 || size == 8)) {
+        if (a_al && A.bits == 32 && size == 8 && fmt_is(it.s_e, it.s_m, 8, 23)) return FK_UNPACK_F32_D;
+        if (a_al && A.bits == 32) return size == 8 ? FK_UNPACK_AL32_TO8 : FK_UNPACK_AL32_TO4;
+        if (a_al && A.bits == 64) return size == 8 ? FK_UNPACK_AL64_TO8 : FK_UNPACK_AL64_TO4;
+        if (a_al && A.bits == 16) return size == 8 ? FK_UNPACK_AL16_TO8 : FK_UNPACK_AL16_TO4;
+        if (a_al && A.bits == 8) return size == 8 ? FK_UNPACK_AL8_TO8 : FK_UNPACK_AL8_TO4;
+        return size == 8 ? FK_UNPACK_BITS_TO8 : FK_UNPACK_BITS_TO4;
+    }
+    // ChangeType f64 <-> f32
+    if (it.lop == L_DIRECT && it.sop == S_CT && a_aff && b_aff && size == 8 && it.d_size == 4 && A.align >= 8 &&
+        B.align >= 4 && fmt_is(it.d_e, it.d_m, 8, 23))
+        return FK_CT_D_F32;
+    if (it.lop == L_CT && it.sop == S_DIRECT && a_aff && b_aff && size == 8 && it.s_size == 4 && A.align >= 4 &&
+        B.align >= 8 && fmt_is(it.s_e, it.s_m, 8, 23))
+        return FK_CT_F32_D;
+    return FK_GENERIC;
+}
+
 llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, const ViewPlan& dst,
                      const std::vector<void*>& dst_ptrs, uint32_t tile, JobDesc* job, std::string* why)
 {
@@ -495,26 +537,21 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         }
     }
 
-    // Code staging slots for bit-stream destination leaves.
-    int slot_of[kMaxLeaves];
-    uint32_t code_at = 0;
+    // Bit-stream destination leaves: values are ORed into their streams, which
+    // the consumers zero first unless the width is a whole number of bytes.
     for (int g = 0; g < (int)dst.stored.size(); ++g) {
-        slot_of[g] = -1;
-        if (dst.base < BASE_BITS_INT) continue;
+        if (dst.base < BASE_BITS_INT) break;
         if (job->npacks >= kMaxPacks) {
             *why = "more than 16 bit-packed leaves";
             return LLGB_ERR_UNSUPPORTED;
         }
-        PackDesc& P = job->packs[job->npacks];
+        PackDesc& P = job->packs[job->npacks++];
         P.bits = (uint8_t)dst.stored[g].bits;
-        P.wide = dst.stored[g].bits > 32;
-        P.code_off = code_at;
         P.dst_sbase = job->dst.leaves[g].sbase;
-        P.magic = P.bits > 1 ? (uint32_t)(((1ull << 32) + P.bits - 1) / P.bits) : 0u;  // w = 1: no division
-        code_at += (uint32_t)align_up((uint64_t)tile * (P.wide ? 8 : 4), 16);
-        slot_of[g] = job->npacks++;
+        P.aligned = (P.bits == 8 || P.bits == 16 || P.bits == 32 || P.bits == 64) ? 1 : 0;
+        P.bytes = (uint32_t)((uint64_t)tile * P.bits / 8);
     }
-    job->code_bytes = code_at;
+    job->code_bytes = 0;
 
     // Items: one per leaf, or one per byte where a side splits bytes.
     const int nf = (int)src.types.size();
@@ -558,14 +595,6 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
             }
             continue;
         }
-        if (a.op == L_DIRECT && b.op == L_BITS_INT) {
-            // Integers stored plainly pack straight from the source image.
-            PackDesc& P = job->packs[slot_of[b.first]];
-            P.direct = 1;
-            P.src_leaf = (uint8_t)a.first;
-            P.src_size = (uint8_t)size;
-            continue;
-        }
         {
             ItemDesc it{};
             it.op = ITEM_VALUE;
@@ -600,10 +629,8 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
                 it.d_e = (uint8_t)dst.stored[b.first].e;
                 it.d_m = (uint8_t)dst.stored[b.first].m;
             }
-            if (b.op == L_BITS_INT || b.op == L_BITS_FLOAT) {
-                it.d_bits = (uint8_t)dst.stored[b.first].bits;
-                it.slot = (uint8_t)slot_of[b.first];
-            }
+            if (b.op == L_BITS_INT || b.op == L_BITS_FLOAT) it.d_bits = (uint8_t)dst.stored[b.first].bits;
+            it.fast = (uint8_t)fast_kind(it, job->src.leaves[a.first], job->dst.leaves[b.first]);
             if (!add(it)) return too_many();
         }
     }
@@ -617,6 +644,14 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         min_gran = std::min<int>(min_gran, job->items[k].gran);
     }
     job->gather = all_moves ? (min_gran >= 2 ? 2 : 4) : 0;
+    // Byte-plane destinations (equal runs, e.g. Bytesplit over SoA): neighbouring
+    // consumer threads take words of different runs, which spreads the 4-word
+    // gathers over the shared-memory banks.
+    if (job->gather == 4 && job->dst.nsegs >= 4) {
+        bool equal = true;
+        for (int q = 1; q < job->dst.nsegs; ++q) equal &= job->dst.segs[q].tile_bytes == job->dst.segs[0].tile_bytes;
+        job->interleave = equal ? 1 : 0;
+    }
     return LLGB_OK;
 }
 

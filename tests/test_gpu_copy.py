@@ -262,3 +262,26 @@ def test_stream_argument_is_honoured():
     llgb.llgb_copy(src_g, dst_g, stream=s)
     s.synchronize()
     assert_same_bytes(dst_g, dst_o)
+
+
+@pytest.mark.parametrize("em", [(5, 2), (2, 5), (5, 10), (8, 23), (11, 52), (3, 4)],
+                         ids=lambda x: f"E{x[0]}M{x[1]}")
+def test_bitpack_float_many_tiles_per_cta(em):
+    # more tiles than CTAs, so every stage is reused: stale stage bytes must
+    # never leak into a stream (whole-byte widths included)
+    e, m = em
+    n = 400000 + 3
+    fields = synth.mixed_f(n, seed=e + 7 * m)
+    packed = {"kind": "bitpack_float", "exp": e, "man": m}
+    cfg = {"tile_records": 128, "src_stages": 2, "dst_stages": 2, "threads": 128, "ctas_per_sm": 1}
+    run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, packed, cfg)
+    run_pair(synth.MIXED_F, fields, packed, {"kind": "aos"}, cfg)
+
+
+@pytest.mark.parametrize("b", [1, 7, 8, 16, 31])
+def test_bitpack_int_many_tiles_per_cta(b):
+    n = 300000 + 5
+    fields = synth.int6(n, b, seed=b)
+    cfg = {"tile_records": 128, "src_stages": 2, "dst_stages": 2, "threads": 128, "ctas_per_sm": 1}
+    run_pair(synth.INT6, fields, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": b}, cfg)
+    run_pair(synth.INT6, fields, {"kind": "bitpack_int", "bits": b}, {"kind": "aos"}, cfg)
