@@ -73,33 +73,39 @@ size_t smem_needed(const JobDesc& J, const llgb_launch_config& c)
 
 bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
 
-// The library's default launch shape for a pair.
+// The library's default launch shape for a pair: 2 CTAs of 256 threads per
+// SM; byte-move jobs (gather programs) take ~12 KB images and 4 source
+// stages, value jobs ~24 KB images and 2 source stages (from launch-shape
+// sweeps on GB300).
 llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const size_t smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
+    const uint32_t q = tile_quantum(src->plan, dst->plan);
+    if (q == 0) return fail(LLGB_ERR_UNSUPPORTED, "AoSoA lane counts give no usable tile size");
+    std::vector<void*> none_s(src->plan.blob_sizes.size(), nullptr), none_d(dst->plan.blob_sizes.size(), nullptr);
+    static thread_local JobDesc probe;
+    std::string why;
+    if (plan_job(src->plan, none_s, dst->plan, none_d, q, &probe, &why) != LLGB_OK)
+        return fail(LLGB_ERR_UNSUPPORTED, why);
+    const bool gather = probe.gather != 0;
     llgb_launch_config c{};
     c.threads = 256;
     c.ctas_per_sm = 2;
-    c.src_stages = 4;
+    c.src_stages = gather ? 4 : 2;
     c.dst_stages = 3;
-    const uint32_t q = tile_quantum(src->plan, dst->plan);
-    if (q == 0) return fail(LLGB_ERR_UNSUPPORTED, "AoSoA lane counts give no usable tile size");
     double sb = 0, db = 0;
     uint32_t cb = 0;
     bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
     const double per_rec = std::max(std::max(sb, db), 1.0);
-    uint64_t tile = (uint64_t)(12288.0 / per_rec) / q * q;
+    uint64_t tile = (uint64_t)((gather ? 12288.0 : 24576.0) / per_rec) / q * q;
     if (tile < q) tile = q;
     // Small views: keep at least two tiles per SM where the records allow.
     const uint64_t n = src->plan.n;
     const uint64_t want = (n + 2ull * sms - 1) / (2ull * sms);
     const uint64_t small = std::max<uint64_t>(q, (want + q - 1) / q * q);
     tile = std::min(tile, small);
-    std::vector<void*> none_s(src->plan.blob_sizes.size(), nullptr), none_d(dst->plan.blob_sizes.size(), nullptr);
-    static thread_local JobDesc probe;
-    std::string why;
     for (;;) {
         if (plan_job(src->plan, none_s, dst->plan, none_d, (uint32_t)tile, &probe, &why) != LLGB_OK)
             return fail(LLGB_ERR_UNSUPPORTED, why);
@@ -108,7 +114,17 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
             --c.src_stages;
             continue;
         }
-        if (tile <= q) return fail(LLGB_ERR_UNSUPPORTED, "record too large for a shared-memory tile");
+        if (c.dst_stages > 2) {
+            --c.dst_stages;
+            continue;
+        }
+        if (tile <= q) {
+            if (c.ctas_per_sm > 1) {
+                c.ctas_per_sm = 1;
+                continue;
+            }
+            return fail(LLGB_ERR_UNSUPPORTED, "record too large for a shared-memory tile");
+        }
         tile -= q;
     }
     c.tile_records = (int32_t)tile;

@@ -210,6 +210,11 @@ __device__ __forceinline__ uint32_t eoff(const LeafRegs& L, uint32_t r)
     return L.sbase + (r / L.lanes) * L.bstride + (r % L.lanes) * L.size;
 }
 
+// The records a loop visits: r0, r0 + step, ... below r1.
+struct Span {
+    uint32_t r0, r1, step;
+};
+
 template <int G>
 struct UInt;
 template <>
@@ -224,10 +229,10 @@ struct UInt<8> { using T = uint64_t; };
 template <int G>
 __device__ __forceinline__ void move_loop(const LeafRegs A, const LeafRegs B, uint32_t sb, uint32_t db,
                                           uint32_t size, const uint8_t* __restrict__ simg,
-                                          uint8_t* __restrict__ dimg, uint32_t tile, uint32_t nvalid)
+                                          uint8_t* __restrict__ dimg, Span sp, uint32_t nvalid)
 {
     using W = typename UInt<G>::T;
-    for (uint32_t r = ctid(); r < tile; r += cnum()) {
+    for (uint32_t r = sp.r0; r < sp.r1; r += sp.step) {
         const uint32_t so = eoff(A, r) + sb;
         const uint32_t dof = eoff(B, r) + db;
         const bool live = r < nvalid;
@@ -258,9 +263,8 @@ __device__ __forceinline__ void or_bits(uint8_t* base, uint32_t pos, uint32_t w,
 // One VALUE item: load the logical value through LOP, store it through SOP.
 // Two records per iteration keep two independent chains in flight.
 template <int LOP, int SOP>
-__device__ __noinline__ void value_loop(const ItemDesc I, const JobDesc& J, const uint8_t* __restrict__ simg,
-                                        uint8_t* __restrict__ dimg, uint8_t* __restrict__ codes,
-                                        uint32_t tile, uint32_t nvalid)
+__device__ __noinline__ void value_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* __restrict__ simg,
+                                        uint8_t* __restrict__ dimg, Span sp, uint32_t nvalid)
 {
     const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
     const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
@@ -320,26 +324,25 @@ __device__ __noinline__ void value_loop(const ItemDesc I, const JobDesc& J, cons
             }
         }
     };
-    const uint32_t n = cnum();
-    for (uint32_t r = ctid(); r < tile; r += 2u * n) {
-        const uint32_t r2 = r + n;
+    for (uint32_t r = sp.r0; r < sp.r1; r += 2u * sp.step) {
+        const uint32_t r2 = r + sp.step;
         const uint64_t v1 = load(r);
-        const uint64_t v2 = r2 < tile ? load(r2) : 0ull;
+        const uint64_t v2 = r2 < sp.r1 ? load(r2) : 0ull;
         store(r, v1);
-        if (r2 < tile) store(r2, v2);
+        if (r2 < sp.r1) store(r2, v2);
     }
 }
 
 template <int LOP>
 __device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc& J, const uint8_t* simg,
-                                               uint8_t* dimg, uint8_t* codes, uint32_t tile, uint32_t nvalid)
+                                               uint8_t* dimg, Span sp, uint32_t nvalid)
 {
     switch (I.sop) {
-    case S_DIRECT: value_loop<LOP, S_DIRECT>(I, J, simg, dimg, codes, tile, nvalid); break;
-    case S_CT: value_loop<LOP, S_CT>(I, J, simg, dimg, codes, tile, nvalid); break;
-    case S_BITS_INT: value_loop<LOP, S_BITS_INT>(I, J, simg, dimg, codes, tile, nvalid); break;
-    case S_BITS_FLOAT: value_loop<LOP, S_BITS_FLOAT>(I, J, simg, dimg, codes, tile, nvalid); break;
-    default: value_loop<LOP, S_SPLIT>(I, J, simg, dimg, codes, tile, nvalid); break;
+    case S_DIRECT: value_loop<LOP, S_DIRECT>(I, J, simg, dimg, sp, nvalid); break;
+    case S_CT: value_loop<LOP, S_CT>(I, J, simg, dimg, sp, nvalid); break;
+    case S_BITS_INT: value_loop<LOP, S_BITS_INT>(I, J, simg, dimg, sp, nvalid); break;
+    case S_BITS_FLOAT: value_loop<LOP, S_BITS_FLOAT>(I, J, simg, dimg, sp, nvalid); break;
+    default: value_loop<LOP, S_SPLIT>(I, J, simg, dimg, sp, nvalid); break;
     }
 }
 
@@ -377,8 +380,8 @@ __device__ __forceinline__ void st_sz(uint8_t* p, uint64_t v)
 // bytes (affine or whole-byte streams); CV: the conversion, applied on the
 // load side (stream -> leaf) when CONV_ON_LOAD, else on the store side.
 template <int LK, int SK, int SZL, int SZS, int CV, bool CONV_ON_LOAD>
-__device__ __noinline__ void fast_loop(const ItemDesc I, const JobDesc& J, const uint8_t* __restrict__ simg,
-                                       uint8_t* __restrict__ dimg, uint32_t tile, uint32_t nvalid)
+__device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* __restrict__ simg,
+                                       uint8_t* __restrict__ dimg, Span sp, uint32_t nvalid)
 {
     const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
     const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
@@ -388,12 +391,11 @@ __device__ __noinline__ void fast_loop(const ItemDesc I, const JobDesc& J, const
     const int se = CONV_ON_LOAD ? I.s_e : I.l_e, sm = CONV_ON_LOAD ? I.s_m : I.l_m;
     const int de = CONV_ON_LOAD ? I.l_e : I.d_e, dm = CONV_ON_LOAD ? I.l_m : I.d_m;
     const uint64_t bmask = low_bits64(wb);
-    const uint32_t n = cnum();
-    for (uint32_t r0 = ctid(); r0 < tile; r0 += kFastBatch * n) {
+    for (uint32_t r0 = sp.r0; r0 < sp.r1; r0 += kFastBatch * sp.step) {
         uint64_t v[kFastBatch];
 #pragma unroll
         for (int u = 0; u < kFastBatch; ++u) {
-            const uint32_t r = r0 + u * n;
+            const uint32_t r = r0 + u * sp.step;
             uint64_t c = 0;
             if (r < nvalid) {
                 if (LK == FL_AFF) {
@@ -413,8 +415,8 @@ __device__ __noinline__ void fast_loop(const ItemDesc I, const JobDesc& J, const
         }
 #pragma unroll
         for (int u = 0; u < kFastBatch; ++u) {
-            const uint32_t r = r0 + u * n;
-            if (r >= tile) break;
+            const uint32_t r = r0 + u * sp.step;
+            if (r >= sp.r1) break;
             uint64_t x = v[u];
             if (CV == FC_INT) {
                 if (CONV_ON_LOAD && sgn && wa < 32u && ((x >> (wa - 1u)) & 1u)) x |= ~(uint64_t)amask;
@@ -443,35 +445,35 @@ __device__ __noinline__ void fast_loop(const ItemDesc I, const JobDesc& J, const
 
 // Runs a VALUE item in its specialised loop; false when it has none.
 __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
-                                         uint32_t tile, uint32_t nvalid)
+                                         Span sp, uint32_t nvalid)
 {
     switch (I.fast) {
-    case FK_PACK_INT32: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_INT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_INT32: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_INT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_D_F32: fast_loop<FL_AFF, FS_AL, 8, 4, FC_D2F, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL32_FROM8: fast_loop<FL_AFF, FS_AL, 8, 4, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL32_FROM4: fast_loop<FL_AFF, FS_AL, 4, 4, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL64_FROM8: fast_loop<FL_AFF, FS_AL, 8, 8, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL64_FROM4: fast_loop<FL_AFF, FS_AL, 4, 8, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL16_FROM8: fast_loop<FL_AFF, FS_AL, 8, 2, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL16_FROM4: fast_loop<FL_AFF, FS_AL, 4, 2, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_BITS_FROM8: fast_loop<FL_AFF, FS_BITS, 8, 8, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_BITS_FROM4: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_F32_D: fast_loop<FL_AL, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL32_TO8: fast_loop<FL_AL, FS_AFF, 4, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL32_TO4: fast_loop<FL_AL, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL64_TO8: fast_loop<FL_AL, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL64_TO4: fast_loop<FL_AL, FS_AFF, 8, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL16_TO8: fast_loop<FL_AL, FS_AFF, 2, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL16_TO4: fast_loop<FL_AL, FS_AFF, 2, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_BITS_TO8: fast_loop<FL_BITS, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_BITS_TO4: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_CT_D_F32: fast_loop<FL_AFF, FS_AFF, 8, 4, FC_D2F, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_CT_F32_D: fast_loop<FL_AFF, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL8_FROM8: fast_loop<FL_AFF, FS_AL, 8, 1, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_PACK_AL8_FROM4: fast_loop<FL_AFF, FS_AL, 4, 1, FC_RT, false>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL8_TO8: fast_loop<FL_AL, FS_AFF, 1, 8, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
-    case FK_UNPACK_AL8_TO4: fast_loop<FL_AL, FS_AFF, 1, 4, FC_RT, true>(I, J, simg, dimg, tile, nvalid); return true;
+    case FK_PACK_INT32: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_INT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_INT32: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_INT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_D_F32: fast_loop<FL_AFF, FS_AL, 8, 4, FC_D2F, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL32_FROM8: fast_loop<FL_AFF, FS_AL, 8, 4, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL32_FROM4: fast_loop<FL_AFF, FS_AL, 4, 4, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL64_FROM8: fast_loop<FL_AFF, FS_AL, 8, 8, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL64_FROM4: fast_loop<FL_AFF, FS_AL, 4, 8, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL16_FROM8: fast_loop<FL_AFF, FS_AL, 8, 2, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL16_FROM4: fast_loop<FL_AFF, FS_AL, 4, 2, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_BITS_FROM8: fast_loop<FL_AFF, FS_BITS, 8, 8, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_BITS_FROM4: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_F32_D: fast_loop<FL_AL, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL32_TO8: fast_loop<FL_AL, FS_AFF, 4, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL32_TO4: fast_loop<FL_AL, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL64_TO8: fast_loop<FL_AL, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL64_TO4: fast_loop<FL_AL, FS_AFF, 8, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL16_TO8: fast_loop<FL_AL, FS_AFF, 2, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL16_TO4: fast_loop<FL_AL, FS_AFF, 2, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_BITS_TO8: fast_loop<FL_BITS, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_BITS_TO4: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_CT_D_F32: fast_loop<FL_AFF, FS_AFF, 8, 4, FC_D2F, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_CT_F32_D: fast_loop<FL_AFF, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL8_FROM8: fast_loop<FL_AFF, FS_AL, 8, 1, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_PACK_AL8_FROM4: fast_loop<FL_AFF, FS_AL, 4, 1, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL8_TO8: fast_loop<FL_AL, FS_AFF, 1, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+    case FK_UNPACK_AL8_TO4: fast_loop<FL_AL, FS_AFF, 1, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
     default: return false;
     }
 }
@@ -490,30 +492,42 @@ __device__ __forceinline__ bool zero_streams(const JobDesc& J, uint8_t* dimg)
     return any;
 }
 
-__device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint8_t* codes,
-                          uint32_t nvalid)
+// Every item runs over the tile in units of 128 records handed to warps
+// round-robin: a unit loads its descriptors once for 4 records per lane,
+// and jobs with few items still keep every warp busy.
+constexpr uint32_t kUnitRecords = 128;
+
+__device__ __forceinline__ void run_item_span(const JobDesc& J, const ItemDesc& I, const uint8_t* simg, uint8_t* dimg,
+                                              Span sp, uint32_t nvalid)
 {
-    const uint32_t tile = J.tile;
-    for (int it = 0; it < J.nitems; ++it) {
-        const ItemDesc I = J.items[it];
-        if (I.op == ITEM_MOVE) {
-            const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
-            const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
-            switch (I.gran) {
-            case 8: move_loop<8>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
-            case 4: move_loop<4>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
-            case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
-            default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, tile, nvalid); break;
-            }
-        } else if (!run_fast(I, J, simg, dimg, tile, nvalid)) {
-            switch (I.lop) {
-            case L_DIRECT: value_dispatch<L_DIRECT>(I, J, simg, dimg, codes, tile, nvalid); break;
-            case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, codes, tile, nvalid); break;
-            case L_BITS_INT: value_dispatch<L_BITS_INT>(I, J, simg, dimg, codes, tile, nvalid); break;
-            case L_BITS_FLOAT: value_dispatch<L_BITS_FLOAT>(I, J, simg, dimg, codes, tile, nvalid); break;
-            default: value_dispatch<L_SPLIT>(I, J, simg, dimg, codes, tile, nvalid); break;
-            }
+    if (I.op == ITEM_MOVE) {
+        const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
+        const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
+        switch (I.gran) {
+        case 8: move_loop<8>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
+        case 4: move_loop<4>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
+        case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
+        default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
         }
+    } else if (!run_fast(I, J, simg, dimg, sp, nvalid)) {
+        switch (I.lop) {
+        case L_DIRECT: value_dispatch<L_DIRECT>(I, J, simg, dimg, sp, nvalid); break;
+        case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, sp, nvalid); break;
+        case L_BITS_INT: value_dispatch<L_BITS_INT>(I, J, simg, dimg, sp, nvalid); break;
+        case L_BITS_FLOAT: value_dispatch<L_BITS_FLOAT>(I, J, simg, dimg, sp, nvalid); break;
+        default: value_dispatch<L_SPLIT>(I, J, simg, dimg, sp, nvalid); break;
+        }
+    }
+}
+
+__device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid)
+{
+    const uint32_t lane = threadIdx.x & 31u, wid = ctid() >> 5, nw = cnum() >> 5;
+    const uint32_t chunks = J.tile / kUnitRecords;
+    const uint32_t units = J.nitems * chunks;
+    for (uint32_t u = wid; u < units; u += nw) {
+        const uint32_t it = u / chunks, c = u - it * chunks;
+        run_item_span(J, J.items[it], simg, dimg, Span{c * kUnitRecords + lane, (c + 1) * kUnitRecords, 32u}, nvalid);
     }
 }
 
@@ -524,11 +538,12 @@ __device__ __forceinline__ void run_moves(const JobDesc& J, const uint8_t* simg,
         const ItemDesc I = J.items[it];
         const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
         const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
+        const Span sp{ctid(), J.tile, cnum()};
         switch (I.gran) {
-        case 8: move_loop<8>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
-        case 4: move_loop<4>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
-        case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
-        default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, J.tile, nvalid); break;
+        case 8: move_loop<8>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
+        case 4: move_loop<4>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
+        case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
+        default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
         }
     }
 }
@@ -750,20 +765,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-struct TileRef {
-    const JobDesc* job;  // descriptor in param or global memory
-    uint32_t j;          // job index
-    uint32_t t;          // tile index within the job
+// Run addressing of one side of a job, held in the producer warp's
+// registers: lane q keeps run q (base address, bytes per tile, image offset).
+struct LaneRuns {
+    int job = -1;
+    const uint8_t* gptr = nullptr;
+    uint32_t bytes = 0, sbase = 0, total = 0, nfull = 0;
+    int nsegs = 0;
+    bool bulk = false;
 };
 
-__device__ __forceinline__ TileRef tile_ref(const CopyArgs& a, uint32_t g)
+__device__ __forceinline__ void lane_runs_load(LaneRuns& L, const SideDesc& S, const JobDesc* J, int j, uint32_t lane)
 {
-    const uint32_t j = job_of(a, g);
-    return TileRef{a.table ? a.table + j : &a.job, j, g - (a.table ? a.tile_start[j] : 0u)};
+    L.job = j;
+    L.nsegs = S.nsegs;
+    L.nfull = J->nfull;
+    L.bulk = S.bulk_ok;
+    if ((int)lane < L.nsegs) {
+        const SegDesc seg = S.segs[lane];
+        L.gptr = S.blobs[seg.blob] + seg.gbase;
+        L.bytes = seg.tile_bytes;
+        L.sbase = seg.sbase;
+    } else {
+        L.gptr = nullptr;
+        L.bytes = 0;
+        L.sbase = 0;
+    }
+    L.total = __reduce_add_sync(0xFFFFFFFFu, L.bytes);
 }
-
-__device__ __forceinline__ bool tile_bulk_in(const JobDesc* J, uint32_t t) { return t < J->nfull && J->src.bulk_ok; }
-__device__ __forceinline__ bool tile_bulk_out(const JobDesc* J, uint32_t t) { return t < J->nfull && J->dst.bulk_ok; }
 
 // Producer warp: TMA loads `src_stages` tiles ahead, bulk stores as the
 // consumers finish each destination stage.
@@ -772,24 +801,22 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t G = gridDim.x, NS = a.src_stages, ND = a.dst_stages;
+    LaneRuns in, out;
 
     auto issue_load = [&](uint32_t k) {
-        const TileRef R = tile_ref(a, first + k * G);
-        const JobDesc* J = R.job;
-        if (!tile_bulk_in(J, R.t)) return;
+        const uint32_t g = first + k * G;
+        const uint32_t j = job_of(a, g);
+        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        if ((int)j != in.job) {
+            const JobDesc* J = a.table ? a.table + j : &a.job;
+            lane_runs_load(in, J->src, J, (int)j, lane);
+        }
+        if (!(t < in.nfull && in.bulk)) return;
         const uint32_t s = k % NS;
-        uint8_t* img = src_stage + s * a.src_stage_bytes;
-        const int nsegs = J->src.nsegs;
-        if (lane == 0) {
-            uint32_t total = 0;
-            for (int q = 0; q < nsegs; ++q) total += J->src.segs[q].tile_bytes;
-            mbar_arrive_expect_tx(&H.full[s], total);
-        }
-        for (int q = (int)lane; q < nsegs; q += 32) {
-            const SegDesc S = J->src.segs[q];
-            bulk_load(img + S.sbase, J->src.blobs[S.blob] + S.gbase + (uint64_t)R.t * S.tile_bytes, S.tile_bytes,
+        if (lane == 0) mbar_arrive_expect_tx(&H.full[s], in.total);
+        if ((int)lane < in.nsegs)
+            bulk_load(src_stage + s * a.src_stage_bytes + in.sbase, in.gptr + (uint64_t)t * in.bytes, in.bytes,
                       &H.full[s]);
-        }
     };
 
     for (uint32_t k = 0; k < NS && k < count; ++k) issue_load(k);
@@ -799,16 +826,16 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             H.abort = 1;
             break;
         }
-        const TileRef R = tile_ref(a, first + k * G);
-        if (tile_bulk_out(R.job, R.t)) {
-            const JobDesc* J = R.job;
-            uint8_t* img = dst_stage + d * a.dst_stage_bytes;
-            for (int q = (int)lane; q < J->dst.nsegs; q += 32) {
-                const SegDesc S = J->dst.segs[q];
-                bulk_store(J->dst.blobs[S.blob] + S.gbase + (uint64_t)R.t * S.tile_bytes, img + S.sbase,
-                           S.tile_bytes);
-            }
+        const uint32_t g = first + k * G;
+        const uint32_t j = job_of(a, g);
+        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        if ((int)j != out.job) {
+            const JobDesc* J = a.table ? a.table + j : &a.job;
+            lane_runs_load(out, J->dst, J, (int)j, lane);
         }
+        if (t < out.nfull && out.bulk && (int)lane < out.nsegs)
+            bulk_store(const_cast<uint8_t*>(out.gptr) + (uint64_t)t * out.bytes,
+                       dst_stage + d * a.dst_stage_bytes + out.sbase, out.bytes);
         // One group per tile (empty for tiles the consumers stored): keeping
         // ND-1 groups in flight, the group of tile k-ND+1 has read its stage,
         // which tile k+1 reuses.
@@ -910,7 +937,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             }
         } else {
             if (zero_streams(J, dimg)) consumer_sync();
-            run_items(J, simg, dimg, codes, nvalid);
+            run_items(J, simg, dimg, nvalid);
         }
         fence_proxy_async();
         __syncwarp();
