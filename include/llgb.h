@@ -230,6 +230,43 @@ llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst,
 llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst,
                            const llgb_launch_config* cfg, void* stream);
 
+/* --------------------------------------------------------------- batch -- */
+
+/* Many layout-aware copies (Sec. 1) in one or a few launches: a batch plans
+ * every (src[k], dst[k]) pair once, groups the jobs by kernel mode and builds
+ * a device descriptor table per group (allocated with cudaMalloc on the
+ * current device, released by llgb_batch_destroy).  Each launch moves every
+ * pair exactly as llgb_copy would, same bytes.  Views keep their bound blobs
+ * for the life of the batch (rebinding a view requires a new batch).  Pairs
+ * with n = 0 are skipped.  Errors: as llgb_copy, plus OOM. */
+typedef struct llgb_batch llgb_batch;
+
+llgb_status llgb_batch_create(int32_t n, const llgb_view* const* src, llgb_view* const* dst,
+                              llgb_batch** out);
+
+/* Queue every copy of the batch on `stream`.  use_graph != 0: the launches
+ * are captured once into a CUDA graph (on a private stream) and the graph is
+ * replayed on `stream`. */
+llgb_status llgb_batch_launch(llgb_batch* b, void* stream, int32_t use_graph);
+
+/* Kernel launches per llgb_batch_launch, total tiles and algorithmic bytes
+ * (every source and destination blob byte).  Any pointer may be NULL. */
+llgb_status llgb_batch_info(const llgb_batch* b, int32_t* launches, uint64_t* tiles, uint64_t* bytes);
+
+/* Waits for the batch's last queued launch, then frees it. */
+void llgb_batch_destroy(llgb_batch* b);
+
+/* Autotuner: time candidate launch shapes (tile records, stages, threads,
+ * CTAs per SM) of llgb_copy(src, dst) on `stream` (each candidate runs the
+ * copy 4 times; dst is written), keep the fastest for this mapping pair and
+ * power-of-two record count, and use it in later llgb_copy / llgb_batch_create
+ * calls of this process.  *best (may be NULL) receives it.  Synchronizes the
+ * stream. */
+llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, llgb_launch_config* best);
+
+/* Forget every tuned launch shape. */
+llgb_status llgb_autotune_clear(void);
+
 /* -------------------------------------------------------------- n-body -- */
 
 /* One all-pairs n-body step (Sec. 5, Fig. 2) on a view whose record is the

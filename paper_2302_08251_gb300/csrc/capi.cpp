@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -72,6 +74,46 @@ size_t smem_needed(const JobDesc& J, const llgb_launch_config& c)
 }
 
 bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
+
+// Kernel mode of a planned job under a launch shape: its gather form when the
+// gather programs cover the destination image with the consumer threads,
+// else the general kernel (0).
+int job_mode(const JobDesc& J, int threads)
+{
+    int mode = J.gather;
+    if (mode == 0) return 0;
+    // words the gather programs cover: every run (interleaved), or the whole
+    // image up to its last slack (linear)
+    uint64_t words = (J.dst.img_bytes - kImageSlack) / 4u;
+    if (J.interleave) {
+        words = 0;
+        for (int q = 0; q < J.dst.nsegs; ++q) words += ((J.dst.segs[q].tile_bytes + 15u) & ~15u) / 4u;
+    }
+    // warp 0 of every CTA is the TMA producer; the rest run the programs
+    if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)(threads - 32)) mode = 0;
+    return mode;
+}
+
+// Launch shapes chosen by llgb_autotune, keyed by mapping pair and the
+// record count's power of two.
+std::mutex tune_mu;
+std::map<std::string, llgb_launch_config> tune_cache;
+
+std::string tune_key(const llgb_view* src, const llgb_view* dst)
+{
+    int bucket = 0;
+    while (bucket < 63 && (1ull << (bucket + 1)) <= src->plan.n) ++bucket;
+    return src->plan.sig + "|" + dst->plan.sig + "|" + std::to_string(bucket);
+}
+
+bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
+{
+    std::lock_guard<std::mutex> lock(tune_mu);
+    auto it = tune_cache.find(tune_key(src, dst));
+    if (it == tune_cache.end()) return false;
+    *out = it->second;
+    return true;
+}
 
 // The library's default launch shape for a pair: 2 CTAs of 256 threads per
 // SM; byte-move jobs (gather programs) take ~12 KB images and 4 source
@@ -149,7 +191,7 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     llgb_launch_config c{};
     if (cfg_in && cfg_in->tile_records != 0) {
         c = *cfg_in;
-    } else {
+    } else if (!tuned_config(src, dst, &c)) {
         st = default_config(src, dst, &c);
         if (st != LLGB_OK) return st;
     }
@@ -176,24 +218,150 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     args.dst_stages = (uint16_t)c.dst_stages;
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
-    int mode = args.job.gather;
-    if (mode != 0) {
-        // words the gather programs cover: every run (interleaved), or the
-        // whole image up to its last slack (linear)
-        uint64_t words = (args.job.dst.img_bytes - kImageSlack) / 4u;
-        if (args.job.interleave) {
-            words = 0;
-            for (int q = 0; q < args.job.dst.nsegs; ++q) words += ((args.job.dst.segs[q].tile_bytes + 15u) & ~15u) / 4u;
-        }
-        // warp 0 of every CTA is the TMA producer; the rest run the programs
-        if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)(c.threads - 32)) mode = 0;
-    }
+    const int mode = job_mode(args.job, c.threads);
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
     return LLGB_OK;
 }
 
 bool is_bitpacked(const llgb_view* v) { return v && v->plan.base >= BASE_BITS_INT; }
+
+}  // namespace
+
+// A batch: every job planned once, grouped by kernel mode; each group is one
+// launch of the copy kernel over a device descriptor table.
+struct llgb_batch {
+    struct Group {
+        int mode = 0;
+        int threads = 256;
+        int grid = 0;
+        size_t smem = 0;
+        std::vector<JobDesc> jobs;
+        std::vector<uint32_t> starts;  // first tile of each job, then the total
+        JobDesc* d_table = nullptr;
+        uint32_t* d_starts = nullptr;
+        CopyArgs args;
+    };
+    std::vector<Group> groups;
+    uint64_t bytes = 0;
+    uint64_t tiles = 0;
+    int device = 0;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+
+    ~llgb_batch()
+    {
+        if (done) {
+            cudaEventSynchronize(done);
+            cudaEventDestroy(done);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (capture) cudaStreamDestroy(capture);
+        for (Group& g : groups) {
+            if (g.d_table) cudaFree(g.d_table);
+            if (g.d_starts) cudaFree(g.d_starts);
+        }
+    }
+};
+
+namespace {
+
+llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch* b)
+{
+    const DeviceInfo dev = device_info();
+    const int sms = dev.sms > 0 ? dev.sms : 152;
+    const size_t smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
+    cudaGetDevice(&b->device);
+    llgb_batch::Group groups[3];
+    groups[0].mode = 0;
+    groups[1].mode = 2;
+    groups[2].mode = 4;
+    for (int32_t k = 0; k < n; ++k) {
+        llgb_status st = check_pair(src[k], dst[k]);
+        if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
+        if (src[k]->plan.n == 0) continue;
+        llgb_launch_config c{};
+        if (!tuned_config(src[k], dst[k], &c)) {
+            st = default_config(src[k], dst[k], &c);
+            if (st != LLGB_OK) return st;
+        }
+        JobDesc J;
+        std::string why;
+        st = plan_job(src[k]->plan, src[k]->ptrs, dst[k]->plan, dst[k]->ptrs, (uint32_t)c.tile_records, &J, &why);
+        if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + why);
+        const int mode = job_mode(J, 256);
+        llgb_batch::Group& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : 2)];
+        g.starts.push_back((uint32_t)b->tiles);
+        g.jobs.push_back(J);
+        for (uint64_t s : src[k]->plan.blob_sizes) b->bytes += s;
+        for (uint64_t s : dst[k]->plan.blob_sizes) b->bytes += s;
+        b->tiles += J.ntiles;
+    }
+    for (llgb_batch::Group& g : groups) {
+        if (g.jobs.empty()) continue;
+        // tile numbers are per group, starting at 0
+        uint64_t total = 0;
+        uint32_t src_bytes = 0, dst_bytes = 0;
+        for (size_t q = 0; q < g.jobs.size(); ++q) {
+            g.starts[q] = (uint32_t)total;
+            total += g.jobs[q].ntiles;
+            src_bytes = std::max(src_bytes, g.jobs[q].src.img_bytes);
+            dst_bytes = std::max(dst_bytes, g.jobs[q].dst.img_bytes);
+        }
+        if (total > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
+        g.starts.push_back((uint32_t)total);
+        g.threads = 256;
+        int ctas = 2;
+        uint16_t ns = g.mode != 0 ? 4 : 2, nd = 3;
+        auto need = [&]() {
+            return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
+        };
+        while (need() * ctas > smem_cap && (ns > 2 || nd > 2 || ctas > 1)) {
+            if (ns > 2) --ns;
+            else if (nd > 2) --nd;
+            else ctas = 1;
+        }
+        if (need() > smem_cap) return fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
+        g.smem = need();
+        g.grid = (int)std::min<uint64_t>(total, (uint64_t)sms * ctas);
+        memset(&g.args, 0, sizeof g.args);
+        cudaError_t e = cudaMalloc(&g.d_table, g.jobs.size() * sizeof(JobDesc));
+        if (e == cudaSuccess) e = cudaMalloc(&g.d_starts, g.starts.size() * sizeof(uint32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_table, g.jobs.data(), g.jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_starts, g.starts.data(), g.starts.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            b->groups.push_back(std::move(g));  // freed by the destructor
+            return e == cudaErrorMemoryAllocation ? fail(LLGB_ERR_OOM, "batch descriptor table")
+                                                  : cuda_fail(e, "batch descriptor table");
+        }
+        g.args.table = g.d_table;
+        g.args.tile_start = g.d_starts;
+        g.args.njobs = (uint32_t)g.jobs.size();
+        g.args.total_tiles = (uint32_t)total;
+        g.args.src_stage_bytes = src_bytes + kStageZeroBytes;
+        g.args.dst_stage_bytes = dst_bytes;
+        g.args.code_bytes = 0;
+        g.args.src_stages = ns;
+        g.args.dst_stages = nd;
+        g.args.chunk = (uint32_t)((total + g.grid - 1) / g.grid);
+        b->groups.push_back(std::move(g));
+    }
+    return LLGB_OK;
+}
+
+llgb_status batch_enqueue(llgb_batch* b, cudaStream_t stream)
+{
+    for (const llgb_batch::Group& g : b->groups) {
+        const cudaError_t e = launch_copy(g.args, g.mode, g.grid, g.threads, g.smem, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    }
+    return LLGB_OK;
+}
 
 }  // namespace
 
@@ -322,6 +490,7 @@ llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst, llgb_la
     if (!src || !dst || !out) return fail(LLGB_ERR_INVALID_ARG, "null argument");
     if (!same_record(src->plan, dst->plan) || src->plan.n != dst->plan.n)
         return fail(LLGB_ERR_MISMATCH, "views differ in record or count");
+    if (tuned_config(src, dst, out)) return LLGB_OK;
     return default_config(src, dst, out);
 }
 
@@ -381,6 +550,137 @@ llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* str
     }
     const cudaError_t e = launch_nbody(v, kind, eps, dt, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
+    return LLGB_OK;
+}
+
+llgb_status llgb_batch_create(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch** out)
+{
+    try {
+        if (!out || n < 0 || (n > 0 && (!src || !dst))) return fail(LLGB_ERR_INVALID_ARG, "bad batch arguments");
+        auto* b = new llgb_batch;
+        const llgb_status st = batch_build(n, src, dst, b);
+        if (st != LLGB_OK) {
+            delete b;
+            return st;
+        }
+        *out = b;
+        return LLGB_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+llgb_status llgb_batch_launch(llgb_batch* b, void* stream, int32_t use_graph)
+{
+    if (!b) return fail(LLGB_ERR_INVALID_ARG, "null batch");
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (!b->done && (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "batch event");
+    if (!use_graph) {
+        const llgb_status st = batch_enqueue(b, s);
+        if (st != LLGB_OK) return st;
+    } else {
+        if (!b->exec) {
+            for (const llgb_batch::Group& g : b->groups)
+                if ((e = prepare_copy(g.mode, g.smem)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
+            if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "capture stream");
+            if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(e, "begin capture");
+            const llgb_status st = batch_enqueue(b, b->capture);
+            e = cudaStreamEndCapture(b->capture, &b->graph);
+            if (st != LLGB_OK) return st;
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        }
+        if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    }
+    if ((e = cudaEventRecord(b->done, s)) != cudaSuccess) return cuda_fail(e, "batch event record");
+    return LLGB_OK;
+}
+
+llgb_status llgb_batch_info(const llgb_batch* b, int32_t* launches, uint64_t* tiles, uint64_t* bytes)
+{
+    if (!b) return fail(LLGB_ERR_INVALID_ARG, "null batch");
+    if (launches) *launches = (int32_t)b->groups.size();
+    if (tiles) *tiles = b->tiles;
+    if (bytes) *bytes = b->bytes;
+    return LLGB_OK;
+}
+
+void llgb_batch_destroy(llgb_batch* b) { delete b; }
+
+llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, llgb_launch_config* best)
+{
+    try {
+        llgb_status st = check_pair(src, dst);
+        if (st != LLGB_OK) return st;
+        llgb_launch_config base{};
+        st = default_config(src, dst, &base);
+        if (st != LLGB_OK) return st;
+        if (src->plan.n == 0) {
+            if (best) *best = base;
+            return LLGB_OK;
+        }
+        const cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const uint32_t q = tile_quantum(src->plan, dst->plan);
+        double sb = 0, db = 0;
+        uint32_t cb = 0;
+        bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
+        const double per_rec = std::max(std::max(sb, db), 1.0);
+        std::vector<llgb_launch_config> cands{base};
+        for (double target : {6144.0, 12288.0, 24576.0, 49152.0})
+            for (int threads : {256, 512})
+                for (int ns : {2, 4})
+                    for (int nd : {2, 3}) {
+                        llgb_launch_config c{};
+                        c.tile_records = (int32_t)std::max<uint64_t>(q, (uint64_t)(target / per_rec) / q * q);
+                        c.threads = threads;
+                        c.ctas_per_sm = threads == 256 ? 2 : 1;
+                        c.src_stages = ns;
+                        c.dst_stages = nd;
+                        cands.push_back(c);
+                    }
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        llgb_launch_config winner = base;
+        for (const llgb_launch_config& c : cands) {
+            if (run_copy(src, dst, &c, stream) != LLGB_OK) continue;  // shape does not fit this pair
+            cudaEventRecord(e0, s);
+            bool ok = true;
+            for (int r = 0; r < 3 && ok; ++r) ok = run_copy(src, dst, &c, stream) == LLGB_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || !ok) continue;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                winner = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        t_error.clear();
+        {
+            std::lock_guard<std::mutex> lock(tune_mu);
+            tune_cache[tune_key(src, dst)] = winner;
+        }
+        if (best) *best = winner;
+        return LLGB_OK;
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+llgb_status llgb_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(tune_mu);
+    tune_cache.clear();
     return LLGB_OK;
 }
 

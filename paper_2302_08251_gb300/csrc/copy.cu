@@ -736,6 +736,12 @@ __device__ void plain_copy(uint8_t* dst, const uint8_t* src, uint32_t bytes)
     for (uint32_t k = done + ctid(); k < bytes; k += cnum()) dst[k] = src[k];
 }
 
+// Global tile index of this CTA's k-th tile (see CopyArgs::chunk).
+__device__ __forceinline__ uint32_t tile_index(const CopyArgs& a, uint32_t first, uint32_t k)
+{
+    return a.chunk ? first * a.chunk + k : first + k * gridDim.x;
+}
+
 __device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g)
 {
     if (a.table == nullptr) return 0;
@@ -800,11 +806,11 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                          uint32_t count)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t G = gridDim.x, NS = a.src_stages, ND = a.dst_stages;
+    const uint32_t NS = a.src_stages, ND = a.dst_stages;
     LaneRuns in, out;
 
     auto issue_load = [&](uint32_t k) {
-        const uint32_t g = first + k * G;
+        const uint32_t g = tile_index(a, first, k);
         const uint32_t j = job_of(a, g);
         const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
         if ((int)j != in.job) {
@@ -826,7 +832,7 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             H.abort = 1;
             break;
         }
-        const uint32_t g = first + k * G;
+        const uint32_t g = tile_index(a, first, k);
         const uint32_t j = job_of(a, g);
         const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
         if ((int)j != out.job) {
@@ -861,7 +867,7 @@ template <int MODE>
 __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint8_t* dst_stage, uint8_t* codes,
                          uint32_t first, uint32_t count)
 {
-    const uint32_t G = gridDim.x, NS = a.src_stages, ND = a.dst_stages;
+    const uint32_t NS = a.src_stages, ND = a.dst_stages;
     const uint32_t zero_word = (a.src_stage_bytes - kStageZeroBytes) / 4u;
     const bool warp_leader = (threadIdx.x & 31u) == 0;
     GatherProgram<MODE> gp;
@@ -871,7 +877,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     int cur_job = -1;
 
     for (uint32_t k = 0; k < count; ++k) {
-        const uint32_t g = first + k * G;
+        const uint32_t g = tile_index(a, first, k);
         const uint32_t j = job_of(a, g);
         if ((int)j != cur_job) {
             consumer_sync();
@@ -969,8 +975,16 @@ __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ Co
 
     const uint32_t G = gridDim.x;
     const uint32_t first = blockIdx.x;
-    if (first >= a.total_tiles) return;
-    const uint32_t count = (a.total_tiles - first + G - 1u) / G;
+    uint32_t count;
+    if (a.chunk) {
+        const uint64_t begin = (uint64_t)first * a.chunk;
+        if (begin >= a.total_tiles) return;
+        const uint64_t left = a.total_tiles - begin;
+        count = left < a.chunk ? (uint32_t)left : a.chunk;
+    } else {
+        if (first >= a.total_tiles) return;
+        count = (a.total_tiles - first + G - 1u) / G;
+    }
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
     const uint32_t consumer_warps = blockDim.x / 32u - 1u;
 
@@ -1010,7 +1024,7 @@ size_t copy_shared_header_bytes() { return (sizeof(CopyShared) + 15u) & ~size_t(
 int gather_words_per_thread(int mode) { return mode == 2 ? GatherMax<2>::value : (mode == 4 ? GatherMax<4>::value : 0); }
 
 template <int MODE>
-static cudaError_t launch_mode(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream)
+static cudaError_t prepare_mode(size_t smem_bytes)
 {
     static thread_local int configured_dev = -1;
     static thread_local size_t configured_bytes = 0;
@@ -1023,6 +1037,23 @@ static cudaError_t launch_mode(const CopyArgs& args, int grid, int threads, size
         configured_dev = dev;
         configured_bytes = smem_bytes;
     }
+    return cudaSuccess;
+}
+
+cudaError_t prepare_copy(int mode, size_t smem_bytes)
+{
+    switch (mode) {
+    case 2: return prepare_mode<2>(smem_bytes);
+    case 4: return prepare_mode<4>(smem_bytes);
+    default: return prepare_mode<0>(smem_bytes);
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_mode(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream)
+{
+    cudaError_t e = prepare_mode<MODE>(smem_bytes);
+    if (e != cudaSuccess) return e;
     copy_kernel<MODE><<<grid, threads, smem_bytes, stream>>>(args);
     return cudaGetLastError();
 }

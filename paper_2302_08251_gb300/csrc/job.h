@@ -173,6 +173,7 @@ struct CopyArgs {
     uint32_t code_bytes;
     uint16_t src_stages;
     uint16_t dst_stages;
+    uint32_t chunk;              // 0: CTA b takes tiles b, b + grid, ...; else tiles [b*chunk, (b+1)*chunk)
 };
 
 }  // namespace llgb

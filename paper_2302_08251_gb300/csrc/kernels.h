@@ -15,6 +15,9 @@ namespace llgb {
 cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, size_t smem_bytes,
                         cudaStream_t stream);
 int gather_words_per_thread(int mode);
+// Raise the copy kernel's dynamic shared memory limit for `mode` to smem_bytes
+// (done by launch_copy too; call it before capturing a graph).
+cudaError_t prepare_copy(int mode, size_t smem_bytes);
 size_t copy_shared_header_bytes();
 cudaError_t read_device_status(unsigned* out, bool reset);
 

@@ -307,6 +307,15 @@ llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llg
             *why = "largest byte offset " + std::to_string(s - 1) + " does not fit the index type";
             return LLGB_ERR_INDEX_OVERFLOW;
         }
+    // Signature of the layout, for caches keyed by mapping pair.
+    std::string sig = "w" + std::to_string(v.wrap) + "b" + std::to_string(v.base) + "p" + std::to_string(v.aos_packed) +
+                      "a" + std::to_string(v.subarray_align) + "l" + std::to_string(v.lanes) + ":";
+    for (int f = 0; f < nf; ++f) sig += std::to_string(v.types[f]) + ",";
+    sig += ":";
+    for (const StoredLeaf& l : v.stored)
+        sig += std::to_string(l.type) + "/" + std::to_string(l.bits) + "/" + std::to_string(l.e) + "/" +
+               std::to_string(l.m) + ",";
+    v.sig = sig;
     *out = std::move(v);
     return LLGB_OK;
 }

@@ -54,6 +54,7 @@ struct ViewPlan {
     std::vector<uint64_t> blob_sizes;
     std::vector<uint64_t> seg_end;     // per stored leaf: end of its run region
     std::vector<int> leaf_blob;        // per stored leaf: blob index
+    std::string sig;                   // mapping signature (record, wrapper, layout), no sizes
 };
 
 int type_size(int32_t t);

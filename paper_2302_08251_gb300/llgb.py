@@ -80,6 +80,8 @@ EXPORTS = [
     "llgb_view_blob_count", "llgb_view_blob_size", "llgb_view_record_count",
     "llgb_view_bind", "llgb_copy", "llgb_pack", "llgb_unpack", "llgb_copy_config",
     "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
+    "llgb_batch_create", "llgb_batch_launch", "llgb_batch_info", "llgb_batch_destroy",
+    "llgb_autotune", "llgb_autotune_clear",
 ]
 
 _lib = None
@@ -120,6 +122,11 @@ def lib():
         L.llgb_copy_with.argtypes = [p, p, ctypes.POINTER(LaunchConfig), p]
         L.llgb_nbody_step.argtypes = [p, ctypes.c_float, ctypes.c_float, p]
         L.llgb_device_status.argtypes = [ctypes.POINTER(i32), i32]
+        L.llgb_batch_create.argtypes = [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)]
+        L.llgb_batch_launch.argtypes = [p, p, i32]
+        L.llgb_batch_info.argtypes = [p, ctypes.POINTER(i32), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.llgb_batch_destroy.argtypes = [p]
+        L.llgb_autotune.argtypes = [p, p, p, ctypes.POINTER(LaunchConfig)]
         _lib = L
     return _lib
 
@@ -284,6 +291,54 @@ def llgb_device_status(reset: bool = False) -> int:
     code = ctypes.c_int32()
     check(lib().llgb_device_status(ctypes.byref(code), int(reset)))
     return code.value
+
+
+class Batch:
+    """Many copies (src[k] -> dst[k]) planned once and launched together."""
+
+    def __init__(self, pairs):
+        self.pairs = list(pairs)  # keeps the views (and their blobs) alive
+        n = len(self.pairs)
+        srcs = (ctypes.c_void_p * max(1, n))(*[s.handle for s, _ in self.pairs])
+        dsts = (ctypes.c_void_p * max(1, n))(*[d.handle for _, d in self.pairs])
+        h = ctypes.c_void_p()
+        check(lib().llgb_batch_create(n, srcs, dsts, ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None, use_graph: bool = False) -> None:
+        check(lib().llgb_batch_launch(self.handle, _stream_ptr(stream), int(use_graph)))
+
+    def info(self) -> dict:
+        launches, tiles, nbytes = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().llgb_batch_info(self.handle, ctypes.byref(launches), ctypes.byref(tiles),
+                                    ctypes.byref(nbytes)))
+        return {"launches": launches.value, "tiles": tiles.value, "bytes": nbytes.value}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.llgb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def llgb_batch_create(pairs) -> Batch:
+    return Batch(pairs)
+
+
+def llgb_batch_launch(batch: Batch, stream=None, use_graph: bool = False) -> None:
+    batch.launch(stream, use_graph)
+
+
+def llgb_autotune(src: View, dst: View, stream=None) -> dict:
+    c = LaunchConfig()
+    check(lib().llgb_autotune(src.handle, dst.handle, _stream_ptr(stream), ctypes.byref(c)))
+    return c.as_dict()
+
+
+def llgb_autotune_clear() -> None:
+    check(lib().llgb_autotune_clear())
 
 
 copy = llgb_copy
