@@ -256,6 +256,30 @@ llgb_status llgb_batch_info(const llgb_batch* b, int32_t* launches, uint64_t* ti
 /* Waits for the batch's last queued launch, then frees it. */
 void llgb_batch_destroy(llgb_batch* b);
 
+/* Batched copy that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory while they run -- cudaMalloc/cudaFree may synchronise the whole
+ * device (too slow for latency-critical loops), a host framework's caching
+ * allocator may already own all free HBM (a fresh cudaMalloc then fails), or
+ * the deployment fixes its device memory at start-up.
+ *
+ * It moves src[k] -> dst[k] for k < n exactly as llgb_copy does (same bytes),
+ * queued on `stream`, with no cudaMalloc, cudaFree or other allocating call.
+ * The descriptor tables live in one static device array of this library
+ * (about 370 KB, holding at most 64 view pairs), which every GPU that loads
+ * the library keeps until the process exits.
+ *   - n <= 64; larger n returns LLGB_ERR_INVALID_ARG (split the work).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call on a device shares the array and overwrites all of it that
+ *     the call uses (no state survives between calls).  Calls that overlap on
+ *     the GPU -- on different streams, or from different host threads --
+ *     race on the array; order them (one stream, or events).
+ * Errors: as llgb_copy. */
+llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const* src, llgb_view* const* dst,
+                                    void* stream);
+
 /* Autotuner: time candidate launch shapes (tile records, stages, threads,
  * CTAs per SM) of llgb_copy(src, dst) on `stream` (each candidate runs the
  * copy 4 times; dst is written), keep the fastest for this mapping pair and

@@ -228,6 +228,38 @@ bool is_bitpacked(const llgb_view* v) { return v && v->plan.base >= BASE_BITS_IN
 
 }  // namespace
 
+// Helpers for the allocation-free batched entry point (noalloc.cu).
+namespace llgb {
+
+llgb_status internal_fail(llgb_status status, const char* message) { return fail(status, message); }
+
+llgb_status internal_plan_pair(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads)
+{
+    llgb_status st = check_pair(src, dst);
+    if (st != LLGB_OK) return st;
+    llgb_launch_config c{};
+    if (!tuned_config(src, dst, &c)) {
+        st = default_config(src, dst, &c);
+        if (st != LLGB_OK) return st;
+    }
+    std::string why;
+    st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, (uint32_t)c.tile_records, job, &why);
+    if (st != LLGB_OK) return fail(st, why);
+    *mode = job_mode(*job, threads);
+    return LLGB_OK;
+}
+
+bool internal_empty(const llgb_view* v) { return v->plan.n == 0; }
+
+void internal_device_limits(int* sms, size_t* smem_cap)
+{
+    const DeviceInfo dev = device_info();
+    *sms = dev.sms > 0 ? dev.sms : 152;
+    *smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
+}
+
+}  // namespace llgb
+
 // A batch: every job planned once, grouped by kernel mode; each group is one
 // launch of the copy kernel over a device descriptor table.
 struct llgb_batch {

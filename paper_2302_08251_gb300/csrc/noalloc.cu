@@ -1,0 +1,184 @@
+// noalloc.cu -- batched copy that allocates no device memory.
+//
+// llgb_batch_create keeps its descriptor tables in memory it obtains with
+// cudaMalloc.  Some callers cannot allocate device memory while they run:
+// cudaMalloc and cudaFree may synchronise the whole device, which stalls
+// latency-critical loops; a host framework's caching allocator may already
+// own all free HBM, so a fresh cudaMalloc fails; and some deployments fix
+// their device memory at start-up and forbid allocation afterwards.
+// llgb_batch_copy_noalloc serves them: the same copy kernel reads its
+// descriptor table from a fixed array in this library's static device
+// memory, which every GPU that loads the library holds until the process
+// exits.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "job.h"
+#include "kernels.h"
+#include "llgb.h"
+
+namespace llgb {
+llgb_status internal_fail(llgb_status status, const char* message);
+llgb_status internal_plan_pair(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads);
+bool internal_empty(const llgb_view* v);
+void internal_device_limits(int* sms, size_t* smem_cap);
+size_t copy_shared_header_bytes();
+}  // namespace llgb
+
+using namespace llgb;
+
+namespace {
+
+constexpr int kNoallocPairs = 64;      // most pairs one call accepts
+constexpr int kModes = 3;              // kernel modes: general, 2-word and 4-word gathers
+constexpr int kMaxDevices = 64;
+constexpr size_t kTableBytes = (size_t)kNoallocPairs * sizeof(JobDesc);
+constexpr size_t kStartsBytes = (size_t)kModes * (kNoallocPairs + 1) * sizeof(uint32_t);
+constexpr size_t kScratchBytes = (kTableBytes + kStartsBytes + 255) / 256 * 256;
+
+// The descriptor tables and tile starts of the current call (about 370 KB).
+// Shared by every call on a device; see llgb_batch_copy_noalloc.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex setup_mu;
+void* device_scratch[kMaxDevices];  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name only stands in for the symbol, so the address is asked
+// for once per device, with that device current.
+llgb_status scratch_address(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return internal_fail(LLGB_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(setup_mu);
+    if (!device_scratch[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return internal_fail(LLGB_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+        device_scratch[dev] = p;
+    }
+    *out = device_scratch[dev];
+    return LLGB_OK;
+}
+
+// Host staging of one call: the tables of all groups back to back, then the
+// tile starts of all groups.  Pageable host memory; cudaMemcpyAsync has
+// consumed it by the time it returns.
+struct Staging {
+    JobDesc jobs[kNoallocPairs];
+    uint32_t starts[kModes][kNoallocPairs + 1];
+};
+thread_local Staging staging;
+
+}  // namespace
+
+extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const* src, llgb_view* const* dst,
+                                               void* stream)
+{
+    if (n < 0 || (n > 0 && (!src || !dst))) return internal_fail(LLGB_ERR_INVALID_ARG, "bad batch arguments");
+    if (n > kNoallocPairs)
+        return internal_fail(LLGB_ERR_INVALID_ARG, "llgb_batch_copy_noalloc takes at most 64 view pairs per call");
+    void* scratch = nullptr;
+    llgb_status st = scratch_address(&scratch);
+    if (st != LLGB_OK) return st;
+
+    // Plan every pair and order the jobs by kernel mode.
+    int mode_of[kNoallocPairs];
+    int order[kNoallocPairs];
+    int count[kModes] = {0, 0, 0};
+    static thread_local JobDesc planned[kNoallocPairs];
+    int njobs = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (!src[k] || !dst[k]) return internal_fail(LLGB_ERR_INVALID_ARG, "null view");
+        if (internal_empty(src[k])) {
+            JobDesc probe;
+            int m = 0;
+            st = internal_plan_pair(src[k], dst[k], &probe, &m, 256);  // still validates the pair
+            if (st != LLGB_OK) return st;
+            continue;
+        }
+        int m = 0;
+        st = internal_plan_pair(src[k], dst[k], &planned[njobs], &m, 256);
+        if (st != LLGB_OK) return st;
+        mode_of[njobs] = m == 0 ? 0 : (m == 2 ? 1 : 2);
+        ++count[mode_of[njobs]];
+        ++njobs;
+    }
+    if (njobs == 0) return LLGB_OK;
+    int at[kModes] = {0, count[0], count[0] + count[1]};
+    for (int q = 0; q < njobs; ++q) order[at[mode_of[q]]++] = q;
+    for (int q = 0; q < njobs; ++q) staging.jobs[q] = planned[order[q]];
+
+    int sms = 152;
+    size_t smem_cap = 232448;
+    internal_device_limits(&sms, &smem_cap);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    struct Launch {
+        CopyArgs args;
+        int grid;
+        size_t smem;
+    };
+    static thread_local Launch launch[kModes];
+    int first = 0;
+    for (int g = 0; g < kModes; ++g) {
+        launch[g].grid = 0;
+        if (count[g] == 0) continue;
+        uint64_t total = 0;
+        uint32_t src_bytes = 0, dst_bytes = 0;
+        for (int q = 0; q < count[g]; ++q) {
+            const JobDesc& J = staging.jobs[first + q];
+            staging.starts[g][q] = (uint32_t)total;
+            total += J.ntiles;
+            src_bytes = src_bytes > J.src.img_bytes ? src_bytes : J.src.img_bytes;
+            dst_bytes = dst_bytes > J.dst.img_bytes ? dst_bytes : J.dst.img_bytes;
+        }
+        if (total > 0xFFFFFFFFull) return internal_fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
+        staging.starts[g][count[g]] = (uint32_t)total;
+        int ctas = 2;
+        uint16_t ns = g != 0 ? 4 : 2, nd = 3;
+        auto need = [&]() {
+            return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
+        };
+        while (need() * ctas > smem_cap && (ns > 2 || nd > 2 || ctas > 1)) {
+            if (ns > 2) --ns;
+            else if (nd > 2) --nd;
+            else ctas = 1;
+        }
+        if (need() > smem_cap) return internal_fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
+        CopyArgs& a = launch[g].args;
+        memset(&a, 0, sizeof a);
+        a.table = reinterpret_cast<const JobDesc*>(scratch) + first;
+        a.tile_start = reinterpret_cast<const uint32_t*>(static_cast<unsigned char*>(scratch) + kTableBytes) +
+                       (size_t)g * (kNoallocPairs + 1);
+        a.njobs = (uint32_t)count[g];
+        a.total_tiles = (uint32_t)total;
+        a.src_stage_bytes = src_bytes + kStageZeroBytes;
+        a.dst_stage_bytes = dst_bytes;
+        a.src_stages = ns;
+        a.dst_stages = nd;
+        launch[g].grid = (int)(total < (uint64_t)sms * ctas ? total : (uint64_t)sms * ctas);
+        a.chunk = (uint32_t)((total + launch[g].grid - 1) / launch[g].grid);
+        launch[g].smem = need();
+        first += count[g];
+    }
+
+    // One copy of the descriptors into the static array, then the launches,
+    // all in stream order.
+    cudaError_t e = cudaMemcpyAsync(scratch, staging.jobs, (size_t)njobs * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<unsigned char*>(scratch) + kTableBytes, staging.starts, sizeof staging.starts,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
+    for (int g = 0; g < kModes; ++g) {
+        if (launch[g].grid == 0) continue;
+        const int mode = g == 0 ? 0 : (g == 1 ? 2 : 4);
+        e = launch_copy(launch[g].args, mode, launch[g].grid, 256, launch[g].smem, s);
+        if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return LLGB_OK;
+}

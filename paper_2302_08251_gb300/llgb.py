@@ -81,7 +81,7 @@ EXPORTS = [
     "llgb_view_bind", "llgb_copy", "llgb_pack", "llgb_unpack", "llgb_copy_config",
     "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
     "llgb_batch_create", "llgb_batch_launch", "llgb_batch_info", "llgb_batch_destroy",
-    "llgb_autotune", "llgb_autotune_clear",
+    "llgb_autotune", "llgb_autotune_clear", "llgb_batch_copy_noalloc",
 ]
 
 _lib = None
@@ -127,6 +127,7 @@ def lib():
         L.llgb_batch_info.argtypes = [p, ctypes.POINTER(i32), ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.llgb_batch_destroy.argtypes = [p]
         L.llgb_autotune.argtypes = [p, p, p, ctypes.POINTER(LaunchConfig)]
+        L.llgb_batch_copy_noalloc.argtypes = [i32, ctypes.POINTER(p), ctypes.POINTER(p), p]
         _lib = L
     return _lib
 
@@ -335,6 +336,17 @@ def llgb_autotune(src: View, dst: View, stream=None) -> dict:
     c = LaunchConfig()
     check(lib().llgb_autotune(src.handle, dst.handle, _stream_ptr(stream), ctypes.byref(c)))
     return c.as_dict()
+
+
+def llgb_batch_copy_noalloc(pairs, stream=None) -> None:
+    """Copy every (src, dst) pair without allocating device memory (at most
+    64 pairs; the descriptor tables live in the library's static device
+    array, shared by every call on a device -- see include/llgb.h)."""
+    pairs = list(pairs)
+    n = len(pairs)
+    srcs = (ctypes.c_void_p * max(1, n))(*[s.handle for s, _ in pairs])
+    dsts = (ctypes.c_void_p * max(1, n))(*[d.handle for _, d in pairs])
+    check(lib().llgb_batch_copy_noalloc(n, srcs, dsts, _stream_ptr(stream)))
 
 
 def llgb_autotune_clear() -> None:

@@ -1,0 +1,92 @@
+"""The allocation-free batched copy (llgb_batch_copy_noalloc).
+
+Callers that cannot allocate device memory while they run (cudaMalloc may
+synchronise the device; a host framework's allocator may own all free HBM;
+some deployments fix device memory at start-up) use this entry point.  It
+keeps its descriptor tables in a static device array of the library instead
+of cudaMalloc'd memory.  Its output must equal the regular entry point's
+(llgb_copy per pair) byte for byte -- the same tolerance as every copy test
+-- on two calls in a row, which reuse the shared array.
+
+The file is named to be collected last: the test passes alone in a fresh
+process and after the rest of the suite.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2302_08251_gb300 import llgb, synth
+from helpers import oracle_view
+from gpu_util import device_view_of, empty_device_view, ensure_library, sync_and_check_status
+
+pytestmark = pytest.mark.gpu
+
+PAIRS = [
+    (synth.PARTICLE, {"kind": "aos"}, {"kind": "soa_mb"}),
+    (synth.CFD, {"kind": "soa_mb"}, {"kind": "aosoa", "lanes": 32}),
+    (synth.CFD, {"kind": "aosoa", "lanes": 8}, {"kind": "aos"}),
+    (synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12}),
+    (synth.INT6, {"kind": "bitpack_int", "bits": 12}, {"kind": "soa_mb"}),
+    (synth.MIXED_F, {"kind": "soa_mb"}, {"kind": "bytesplit", "inner": {"kind": "soa_mb"}}),
+    (synth.MIXED_F, {"kind": "soa_mb"}, {"kind": "bitpack_float", "exp": 8, "man": 23}),
+    (synth.MIXED_F, {"kind": "aos"}, {"kind": "changetype", "ct": [("f64", "f32")],
+                                      "inner": {"kind": "soa_mb"}}),
+]
+
+
+def fields_for(rec, n, seed):
+    if rec is synth.INT6:
+        return synth.int6(n, 12, seed)
+    if rec is synth.MIXED_F:
+        return synth.mixed_f(n, seed)
+    return synth.uniform_fields(rec, n, seed)
+
+
+def build_pairs(seed):
+    g = synth.rng(seed)
+    pairs = []
+    for k in range(24):
+        rec, sm, dm = PAIRS[k % len(PAIRS)]
+        n = int(g.choice([1, 129, 4000, 50000 + int(g.integers(0, 999))]))
+        src = device_view_of(oracle_view(rec, sm, fields_for(rec, n, seed + k)))
+        pairs.append((rec, dm, n, src))
+    return pairs
+
+
+def test_noalloc_batch_matches_the_regular_copy_on_two_calls_in_a_row():
+    ensure_library()
+    pairs = build_pairs(seed=41)
+    ref = []
+    for rec, dm, n, src in pairs:
+        d = empty_device_view(rec, dm, n, fill=0x11)
+        llgb.llgb_copy(src, d)
+        ref.append(d)
+    sync_and_check_status()
+    want = [d.blob_bytes() for d in ref]
+    outs = [empty_device_view(rec, dm, n) for rec, dm, n, _ in pairs]
+    for call in range(2):
+        for d in outs:
+            for b in d.blobs:
+                b.fill_(0x77 + call)  # stale bytes must not survive a call
+        # straight through the C ABI
+        n = len(pairs)
+        srcs = (ctypes.c_void_p * n)(*[p[3].handle for p in pairs])
+        dsts = (ctypes.c_void_p * n)(*[d.handle for d in outs])
+        llgb.check(llgb.lib().llgb_batch_copy_noalloc(n, srcs, dsts, llgb._stream_ptr(None)))
+        sync_and_check_status()
+        for k, d in enumerate(outs):
+            for got, exp in zip(d.blob_bytes(), want[k]):
+                assert np.array_equal(got, exp), (call, k, pairs[k][1])
+
+
+def test_noalloc_batch_rejects_more_than_64_pairs():
+    ensure_library()
+    rec = llgb.Record(synth.PARTICLE)
+    views = [(llgb.View(rec, {"kind": "aos"}, (10,)), llgb.View(rec, {"kind": "soa_mb"}, (10,)))
+             for _ in range(65)]
+    with pytest.raises(llgb.LlgbError) as err:
+        llgb.llgb_batch_copy_noalloc(views)
+    assert err.value.status == llgb.ERR_INVALID_ARG
+    llgb.llgb_batch_copy_noalloc(views[:64])
+    sync_and_check_status()
