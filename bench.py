@@ -357,6 +357,14 @@ def run_gpu(args):
     nbody = nbody_bench(device, args) if rank == 0 and not args.no_extras else None
     # end to end through host buffers
     e2e = e2e_bench(wl, stream, args) if rank == 0 and not args.no_extras else None
+    batched = serving = None
+    step_bytes = wl.bytes
+    if rank == 0 and not args.no_extras:
+        del wl
+        torch.cuda.empty_cache()
+        batched = batched_bench(device, args)
+        torch.cuda.empty_cache()
+        serving = serving_bench(device, args)
 
     if rank == 0:
         line = {
@@ -368,7 +376,7 @@ def run_gpu(args):
                                    "AoSoA8->AoSoA32 (u32, static inner extents); C1 2^26 INT6 "
                                    "BitpackInt b=12 pack+unpack; C2 2^25 MIXED_F BitpackFloat "
                                    "E8M23 pack+unpack, Bytesplit, ChangeType f64->f32",
-                       "bytes_per_step": wl.bytes, "l2": "inputs > L2 (no flush needed)",
+                       "bytes_per_step": step_bytes, "l2": "inputs > L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "traffic": traffic,
@@ -379,6 +387,8 @@ def run_gpu(args):
             "gpu_launches": nrows * args.steps,
             "e2e": e2e,
             "nbody": nbody,
+            "batched": batched,
+            "serving": serving,
         }
         if not args.no_cpu_baseline and not args.no_extras:
             v, sample, _ = oracle_sample()
@@ -422,6 +432,73 @@ def nbody_bench(device, args):
             "roofline": {"bound": "alu", "achieved": best, "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(best / peak, 4),
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz (nominal)"}}
+
+
+def batched_bench(device, args, target_bytes=24 * (1 << 30)):
+    """Config-4 requests (log-uniform record counts, mixed mapping pairs) in
+    arrival order up to ~24 GB of algorithmic bytes: one launch per view
+    (llgb_copy each) against one batched launch replayed from a CUDA graph,
+    same bytes checked on the device."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, serve
+    reqs = serve.workload(count=4096)
+    ex = serve.GpuExecutor(streams=1, seed=11)
+    chosen, total = [], 0
+    for r in reqs:
+        nb = ex.nbytes(r)
+        if total + nb > target_bytes:
+            break
+        chosen.append(r)
+        total += nb
+    pairs, alt = [], []
+    for r in chosen:
+        ex.allocate(r)
+        src, dst, _ = r.views
+        pairs.append((src, dst))
+        alt.append(llgb.View(ex._record(r.record), r.dst_map, (r.n,)))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    reps = max(2, min(args.steps, 5))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def per_view():
+        for (src, _), d in zip(pairs, alt):
+            llgb.llgb_copy(src, d, stream)
+    batch = llgb.Batch(pairs)
+    ms_view = timed(per_view)
+    ms_batch = timed(lambda: batch.launch(stream, use_graph=True))
+    same = all(torch.equal(x, y) for (_, d), a in zip(pairs, alt) for x, y in zip(d.blobs, a.blobs))
+    info = batch.info()
+    batch.close()
+    return {"requests": len(chosen), "bytes": total, "kernel_launches_batched": info["launches"],
+            "per_view": {"ms": round(ms_view, 3), "GB/s": round(total / ms_view / 1e6, 1),
+                         "launches": len(chosen)},
+            "batched_graph": {"ms": round(ms_batch, 3), "GB/s": round(total / ms_batch / 1e6, 1)},
+            "speedup": round(ms_view / ms_batch, 3), "identical_bytes": bool(same)}
+
+
+def serving_bench(device, args):
+    """The continuous-batching request loop on the config-4 stream: 4,096
+    requests, Poisson arrivals at 2,000 req/s, 64 GB HBM budget, 4 streams."""
+    from paper_2302_08251_gb300 import serve
+    reqs = serve.workload(count=4096)
+    ex = serve.GpuExecutor(streams=4, seed=12)
+    srv = serve.Server(ex, budget_bytes=64 * serve.GB, deadline_s=60.0)
+    stats = srv.run(reqs)
+    out = stats.summary()
+    out["arrival_rate_hz"] = 2000.0
+    out["budget_GB"] = 64
+    return out
 
 
 def e2e_bench(wl, stream, args):

@@ -215,6 +215,21 @@ class Record:
             self.handle = None
 
 
+def blob_sizes(record: Record, mapping: dict, extents, index_type: str = "u64") -> list:
+    """Blob sizes a view of `record` under `mapping` would have (host planning
+    only; nothing is allocated or bound)."""
+    keep: list = []
+    e = extents_desc(extents, index_type)
+    m = mapping_desc(mapping, keep)
+    h = ctypes.c_void_p()
+    L = lib()
+    check(L.llgb_view_create(record.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(h)))
+    try:
+        return [int(L.llgb_view_blob_size(h, k)) for k in range(L.llgb_view_blob_count(h))]
+    finally:
+        L.llgb_view_destroy(h)
+
+
 class View:
     """A view: mapping + blobs.  Blobs are torch uint8 tensors on the device
     (allocated here unless given) and are bound to the C view."""
