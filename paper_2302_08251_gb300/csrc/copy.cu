@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fconv.cuh"
 #include "job.h"
 #include "kernels.h"
@@ -349,10 +351,17 @@ __device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc&
 // ------------------------------------------------------ fast value loops --
 //
 // A VALUE item whose element sizes and conversion are among the common cases
-// runs here: the recipe is fixed at compile time and every thread keeps
-// kFastBatch records in flight (all loads issued before any store).
-
-constexpr int kFastBatch = 4;
+// runs here.  Lane l of a warp takes V consecutive records (V = 1, 2 or 4,
+// chosen by the planner per item) of each "super-group" of 32 V records, so
+//  * an affine leaf's elements of a lane sit at a lane constant plus a step
+//    per super-group, and are moved with vector loads / stores where they
+//    are contiguous;
+//  * a w-bit stream's super-group is exactly C = V w whole words (32 <= C <=
+//    64 for w >= 8), and the lane's codes form one C-bit chunk at a lane-
+//    constant bit offset: a lane reads its chunk with three word loads and
+//    two funnel shifts, and assembles output word k from the (at most two,
+//    for C >= 32) chunks that reach it, fetched with warp shuffles -- codes
+//    are stored as whole words, never ORed into shared memory.
 
 enum FastLoad { FL_AFF = 0, FL_AL = 1, FL_BITS = 2 };
 enum FastStore { FS_AFF = 0, FS_AL = 1, FS_BITS = 2 };
@@ -367,139 +376,474 @@ __device__ __forceinline__ uint64_t ld_sz(const uint8_t* p)
     return *reinterpret_cast<const uint64_t*>(p);
 }
 
+// Shared-memory accesses at 32-bit shared-window addresses.  The loops
+// below are separate functions that see the stage images only through
+// pointers, so they address them explicitly (no 64-bit generic addressing).
+// Loads carry no memory clobber: within a loop the source image is only
+// read and the destination image only written.
 template <int SZ>
-__device__ __forceinline__ void st_sz(uint8_t* p, uint64_t v)
+__device__ __forceinline__ uint64_t lds(uint32_t a)
 {
-    if (SZ == 1) *p = (uint8_t)v;
-    else if (SZ == 2) *reinterpret_cast<uint16_t*>(p) = (uint16_t)v;
-    else if (SZ == 4) *reinterpret_cast<uint32_t*>(p) = (uint32_t)v;
-    else *reinterpret_cast<uint64_t*>(p) = v;
+    if constexpr (SZ == 1) {
+        uint16_t v;
+        asm("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
+        return v & 0xFFu;
+    } else if constexpr (SZ == 2) {
+        uint16_t v;
+        asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+        return v;
+    } else if constexpr (SZ == 4) {
+        uint32_t v;
+        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+        return v;
+    } else {
+        uint64_t v;
+        asm("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+        return v;
+    }
 }
 
-// LK/SK: how the source / destination element is reached; SZL/SZS: element
-// bytes (affine or whole-byte streams); CV: the conversion, applied on the
-// load side (stream -> leaf) when CONV_ON_LOAD, else on the store side.
-template <int LK, int SK, int SZL, int SZS, int CV, bool CONV_ON_LOAD>
-__device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* __restrict__ simg,
-                                       uint8_t* __restrict__ dimg, Span sp, uint32_t nvalid)
+template <int SZ>
+__device__ __forceinline__ void sts(uint32_t a, uint64_t v)
 {
-    const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
-    const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
-    const uint32_t wa = A.bits, wb = I.d_bits;
-    const uint32_t amask = wa >= 32u ? 0xFFFFFFFFu : ((1u << wa) - 1u);
-    const bool sgn = I.is_signed;
-    const int se = CONV_ON_LOAD ? I.s_e : I.l_e, sm = CONV_ON_LOAD ? I.s_m : I.l_m;
-    const int de = CONV_ON_LOAD ? I.l_e : I.d_e, dm = CONV_ON_LOAD ? I.l_m : I.d_m;
-    const uint64_t bmask = low_bits64(wb);
-    for (uint32_t r0 = sp.r0; r0 < sp.r1; r0 += kFastBatch * sp.step) {
-        uint64_t v[kFastBatch];
+    if constexpr (SZ == 1) asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "h"((uint16_t)(v & 0xFFu)));
+    else if constexpr (SZ == 2) asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v));
+    else if constexpr (SZ == 4) asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"((uint32_t)v));
+    else asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v));
+}
+
+__device__ __forceinline__ uint2 lds_v2(uint32_t a)
+{
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds_v4(uint32_t a)
+{
+    uint4 v;
+    asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts_v2(uint32_t a, uint32_t x, uint32_t y)
+{
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y));
+}
+
+__device__ __forceinline__ void sts_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w)
+{
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
+}
+
+// One side's lane constants: element v of the lane's records in super-group
+// g sits at off + g * step + v * vstride; `vec`: the V elements are
+// contiguous and aligned for vector access.
+struct LaneRun {
+    uint32_t off, step, vstride;
+    bool vec;
+};
+
+template <int V, int SZ>
+__device__ __forceinline__ bool run_vec_ok(uint32_t off, uint32_t step, uint32_t vstride)
+{
+    constexpr uint32_t A = (V * SZ) >= 16 ? 16u : (uint32_t)(V * SZ);
+    return V * SZ >= 4 && vstride == (uint32_t)SZ && off % A == 0u && step % A == 0u;
+}
+
+// Affine leaves with one lane, or a power-of-two lane count that V divides
+// and that divides 32 V (the planner checks).
+template <int V, int SZ>
+__device__ __forceinline__ LaneRun affine_run(const LeafDesc& L, uint32_t lane)
+{
+    const uint32_t r = (uint32_t)V * lane;
+    LaneRun R;
+    R.step = ((32u * V) >> L.lshift) * L.bstride;
+    R.off = L.sbase + (r >> L.lshift) * L.bstride + (r & (L.lanes - 1u)) * L.size;
+    R.vstride = L.lanes == 1 ? L.bstride : L.size;
+    R.vec = run_vec_ok<V, SZ>(R.off, R.step, R.vstride);
+    return R;
+}
+
+// Whole-byte streams: a dense array of SZ-byte codes.
+template <int V, int SZ>
+__device__ __forceinline__ LaneRun stream_run(const LeafDesc& L, uint32_t lane)
+{
+    LaneRun R;
+    R.step = 32u * V * SZ;
+    R.off = L.sbase + (uint32_t)V * lane * SZ;
+    R.vstride = SZ;
+    R.vec = run_vec_ok<V, SZ>(R.off, R.step, R.vstride);
+    return R;
+}
+
+// The V elements of a lane as 32-bit words (V * SZ >= 4 bytes, vector path).
+template <int V, int SZ, typename T>
+__device__ __forceinline__ void words_to_elems(const uint32_t* w, T (&x)[V])
+{
 #pragma unroll
-        for (int u = 0; u < kFastBatch; ++u) {
-            const uint32_t r = r0 + u * sp.step;
-            uint64_t c = 0;
-            if (r < nvalid) {
-                if (LK == FL_AFF) {
-                    c = ld_sz<SZL>(simg + eoff(A, r));
-                } else if (LK == FL_AL) {
-                    c = ld_sz<SZL>(simg + A.sbase + r * SZL);
-                } else {
-                    const uint32_t pos = r * wa;
-                    const uint32_t* wd = reinterpret_cast<const uint32_t*>(simg + A.sbase) + (pos >> 5);
-                    if (wa <= 32u)
-                        c = __funnelshift_r(wd[0], wd[1], pos & 31u) & amask;
-                    else
-                        c = ld_bits(simg + A.sbase, pos, wa);
-                }
-            }
-            v[u] = c;
-        }
+    for (int v = 0; v < V; ++v) {
+        if constexpr (SZ == 8) x[v] = (T)((uint64_t)w[2 * v] | ((uint64_t)w[2 * v + 1] << 32));
+        else if constexpr (SZ == 4) x[v] = w[v];
+        else if constexpr (SZ == 2) x[v] = (w[v / 2] >> (16 * (v % 2))) & 0xFFFFu;
+        else x[v] = (w[v / 4] >> (8 * (v % 4))) & 0xFFu;
+    }
+}
+
+template <int V, int SZ, typename T>
+__device__ __forceinline__ void elems_to_words(const T (&x)[V], uint32_t* w)
+{
 #pragma unroll
-        for (int u = 0; u < kFastBatch; ++u) {
-            const uint32_t r = r0 + u * sp.step;
-            if (r >= sp.r1) break;
-            uint64_t x = v[u];
-            if (CV == FC_INT) {
-                if (CONV_ON_LOAD && sgn && wa < 32u && ((x >> (wa - 1u)) & 1u)) x |= ~(uint64_t)amask;
-                if (CONV_ON_LOAD) x &= 0xFFFFFFFFull;
-                else x &= bmask;
-            } else if (r < nvalid) {
-                if (CV == FC_D2F) {
-                    const double d = __longlong_as_double((long long)x);
-                    x = (d == d) ? (uint64_t)__float_as_uint(__double2float_rn(d)) : fconv_general(x, 11, 52, 8, 23);
-                } else if (CV == FC_F2D) {
-                    const float f = __uint_as_float((uint32_t)x);
-                    x = (f == f) ? (uint64_t)__double_as_longlong((double)f) : fconv_general(x, 8, 23, 11, 52);
-                } else {
-                    x = fconv(x, se, sm, de, dm);
-                }
-            }
-            if (SK == FS_AFF)
-                st_sz<SZS>(dimg + eoff(B, r), x);
-            else if (SK == FS_AL)
-                st_sz<SZS>(dimg + B.sbase + r * SZS, x);
-            else
-                or_bits(dimg + B.sbase, r * wb, wb, x);
+    for (int q = 0; q < V * SZ / 4; ++q) w[q] = 0u;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if constexpr (SZ == 8) {
+            w[2 * v] = (uint32_t)x[v];
+            w[2 * v + 1] = (uint32_t)((uint64_t)x[v] >> 32);
+        } else if constexpr (SZ == 4) {
+            w[v] = (uint32_t)x[v];
+        } else if constexpr (SZ == 2) {
+            w[v / 2] |= ((uint32_t)x[v] & 0xFFFFu) << (16 * (v % 2));
+        } else {
+            w[v / 4] |= ((uint32_t)x[v] & 0xFFu) << (8 * (v % 4));
         }
     }
 }
 
-// Runs a VALUE item in its specialised loop; false when it has none.
-__device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
-                                         Span sp, uint32_t nvalid)
+template <int V, int SZ, typename T>
+__device__ __forceinline__ void ld_run(uint32_t p, const LaneRun& R, T (&x)[V])
 {
+    constexpr int BYTES = V * SZ;
+    if constexpr (BYTES >= 4) {
+        if (R.vec) {
+            uint32_t w[BYTES / 4];
+            if constexpr (BYTES % 16 == 0) {
+#pragma unroll
+                for (int q = 0; q < BYTES / 16; ++q) {
+                    const uint4 t = lds_v4(p + 16u * q);
+                    w[4 * q] = t.x;
+                    w[4 * q + 1] = t.y;
+                    w[4 * q + 2] = t.z;
+                    w[4 * q + 3] = t.w;
+                }
+            } else if constexpr (BYTES == 8) {
+                const uint2 t = lds_v2(p);
+                w[0] = t.x;
+                w[1] = t.y;
+            } else {
+                w[0] = (uint32_t)lds<4>(p);
+            }
+            words_to_elems<V, SZ, T>(w, x);
+            return;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = (T)lds<SZ>(p + v * R.vstride);
+}
+
+template <int V, int SZ, typename T>
+__device__ __forceinline__ void st_run(uint32_t p, const LaneRun& R, const T (&x)[V])
+{
+    constexpr int BYTES = V * SZ;
+    if constexpr (BYTES >= 4) {
+        if (R.vec) {
+            uint32_t w[BYTES / 4];
+            elems_to_words<V, SZ, T>(x, w);
+            if constexpr (BYTES % 16 == 0) {
+#pragma unroll
+                for (int q = 0; q < BYTES / 16; ++q) sts_v4(p + 16u * q, w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            } else if constexpr (BYTES == 8) {
+                sts_v2(p, w[0], w[1]);
+            } else {
+                sts<4>(p, w[0]);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) sts<SZ>(p + v * R.vstride, (uint64_t)x[v]);
+}
+
+// x << s and x >> s with PTX semantics: shift amounts of 32 or more (also
+// "negative" ones, as unsigned) give 0.
+__device__ __forceinline__ uint32_t shl_c(uint32_t x, uint32_t s)
+{
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
+    return r;
+}
+
+// floor(a / b) for a < 2^15 and 0 < b <= 2^7: a float quotient is within one
+// of the exact one, and one integer check each way makes it exact.
+__device__ __forceinline__ uint32_t small_div(uint32_t a, uint32_t b)
+{
+    uint32_t q = (uint32_t)__fmul_rz((float)a, __frcp_rn((float)b));
+    if (q * b > a) --q;
+    if ((q + 1u) * b <= a) ++q;
+    return q;
+}
+
+// Lane constants of a stream of C-bit chunks (C = V w bits per lane; a
+// super-group is C words).  Reading: the lane's chunk starts `sh` bits into
+// word `word` of the super-group.  Writing, round m (words k = lane + 32 m
+// < C): the chunk of lane l0 reaches word k from chunk bit rsh on; the next
+// chunks (nterm - 1 of them; at most one when C >= 32) start inside word k
+// at bit j C - rsh (t1 for j = 1; 32 when there is none).
+struct ChunkLane {
+    uint32_t word, sh;
+    uint32_t l0[2], rsh[2], t1[2], nterm[2], jmax[2];
+};
+
+__device__ __forceinline__ ChunkLane chunk_lane(uint32_t C, uint32_t lane, bool writing)
+{
+    ChunkLane K;
+    const uint32_t bit = lane * C;
+    K.word = bit >> 5;
+    K.sh = bit & 31u;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        K.l0[m] = 0u;
+        K.rsh[m] = 0u;
+        K.t1[m] = 32u;
+        K.nterm[m] = 0u;
+        K.jmax[m] = 0u;
+        if (!writing) continue;
+        const uint32_t k = lane + 32u * m;
+        if (k < C) {
+            const uint32_t b0 = 32u * k;
+            K.l0[m] = small_div(b0, C);
+            K.rsh[m] = b0 - K.l0[m] * C;
+            K.nterm[m] = min(31u, small_div(b0 + 31u, C)) - K.l0[m] + 1u;
+            if (K.nterm[m] >= 2u) K.t1[m] = C - K.rsh[m];
+        }
+        K.jmax[m] = __reduce_max_sync(0xFFFFFFFFu, K.nterm[m]);
+    }
+    return K;
+}
+
+// Word k = lane + 32 m of a super-group whose lanes hold chunks (lo, hi).
+// MANY: chunks narrower than 32 bits, so more than two reach a word.
+template <bool MANY>
+__device__ __forceinline__ uint32_t chunk_word(uint32_t lo, uint32_t hi, uint32_t C, const ChunkLane& K, int m)
+{
+    const uint32_t l0 = K.l0[m];
+    const uint32_t lo0 = __shfl_sync(0xFFFFFFFFu, lo, l0);
+    const uint32_t hi0 = __shfl_sync(0xFFFFFFFFu, hi, l0);
+    uint32_t word = (uint32_t)((((uint64_t)hi0 << 32) | lo0) >> K.rsh[m]);
+    if (!MANY) {
+        const uint32_t lo1 = __shfl_sync(0xFFFFFFFFu, lo, (l0 + 1u) & 31u);
+        return word | shl_c(lo1, K.t1[m]);
+    }
+    for (uint32_t j = 1; j < K.jmax[m]; ++j) {
+        const uint32_t v = __shfl_sync(0xFFFFFFFFu, lo, (l0 + j) & 31u);
+        word |= j < K.nterm[m] ? shl_c(v, j * C - K.rsh[m]) : 0u;
+    }
+    return word;
+}
+
+// The item fields a conversion needs, held in registers for a whole loop.
+struct ConvRegs {
+    uint32_t wa, wb;
+    bool is_signed;
+    int se, sm, de, dm;  // stored -> logical (on load) or logical -> stored
+};
+
+template <int CV, bool ON_LOAD, typename T>
+__device__ __forceinline__ T fast_convert(T x, const ConvRegs& c)
+{
+    if (CV == FC_INT) {
+        if (ON_LOAD) {
+            if (c.is_signed) {
+                const uint32_t up = 32u - c.wa;  // 0 for 32-bit codes
+                return (T)(uint32_t)(((int32_t)((uint32_t)x << up)) >> up);
+            }
+            return (T)(uint32_t)x;
+        }
+        return x;  // the pack masks codes to their width
+    }
+    if (CV == FC_D2F) return (T)f64_to_f32_bits((uint64_t)x);
+    if (CV == FC_F2D) return (T)f32_to_f64_bits((uint32_t)x);
+    return (T)fconv((uint64_t)x, c.se, c.sm, c.de, c.dm);
+}
+
+// LK / SK: how the source / destination element is reached; SZL / SZS:
+// element bytes of affine leaves and whole-byte streams; CV: the conversion,
+// applied on the load side (stream -> leaf) when CONV_ON_LOAD; V: records
+// per lane; MANY: stream chunks narrower than 32 bits.  Super-groups
+// [g0, g1) of the tile; records at or past nvalid read as zero (and so are
+// written as zero).  Super-groups whose records are all valid run without
+// any checks.
+template <int LK, int SK, int SZL, int SZS, int CV, bool CONV_ON_LOAD, int V, bool MANY>
+__device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                       uint32_t g0, uint32_t g1, uint32_t nvalid)
+{
+    // element / code type: 32-bit where every value and code fits
+    using T = typename std::conditional<(SZL <= 4 && SZS <= 4 && V > 1), uint32_t, uint64_t>::type;
+    constexpr uint32_t B = 4u / V;  // super-groups in flight: 4 records per lane
+    const uint32_t lane = threadIdx.x & 31u;
+    const LeafDesc LA = J.src.leaves[I.src_leaf];
+    const LeafDesc LB = J.dst.leaves[I.dst_leaf];
+    ConvRegs cr;
+    cr.wa = LA.bits;
+    cr.wb = I.d_bits;
+    cr.is_signed = I.is_signed != 0;
+    cr.se = CONV_ON_LOAD ? I.s_e : I.l_e;
+    cr.sm = CONV_ON_LOAD ? I.s_m : I.l_m;
+    cr.de = CONV_ON_LOAD ? I.l_e : I.d_e;
+    cr.dm = CONV_ON_LOAD ? I.l_m : I.d_m;
+    const uint32_t wa = cr.wa, wb = cr.wb;
+    const uint32_t sa = smem_addr(simg), da = smem_addr(dimg);
+
+    LaneRun RA{}, RB{};
+    ChunkLane KA{}, KB{};
+    uint32_t ca = 0u, cb = 0u, abase = 0u, bbase = 0u;
+    if (LK == FL_AFF) RA = affine_run<V, SZL>(LA, lane);
+    else if (LK == FL_AL) RA = stream_run<V, SZL>(LA, lane);
+    else {
+        ca = (uint32_t)V * wa;
+        KA = chunk_lane(ca, lane, false);
+        abase = sa + LA.sbase + 4u * KA.word;
+    }
+    if (SK == FS_AFF) RB = affine_run<V, SZS>(LB, lane);
+    else if (SK == FS_AL) RB = stream_run<V, SZS>(LB, lane);
+    else {
+        cb = (uint32_t)V * wb;
+        KB = chunk_lane(cb, lane, true);
+        bbase = da + LB.sbase + 4u * lane;
+    }
+    const T amask = (T)low_bits64((int)wa), bmask = (T)low_bits64((int)wb);
+
+    auto body = [&](uint32_t g, auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
+        T x[B][V];
+#pragma unroll
+        for (uint32_t b = 0; b < B; ++b) {
+            const uint32_t gg = g + b;
+            const uint32_t rec0 = 32u * V * gg + (uint32_t)V * lane;
+            if (CHECK) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[b][v] = 0u;
+                if (gg >= g1 || rec0 >= nvalid) continue;
+            }
+            if (LK == FL_BITS) {
+                const uint32_t p = abase + 4u * gg * ca;
+                const uint32_t w0 = (uint32_t)lds<4>(p), w1 = (uint32_t)lds<4>(p + 4u), w2 = (uint32_t)lds<4>(p + 8u);
+                const uint64_t chunk = ((uint64_t)__funnelshift_r(w1, w2, KA.sh) << 32) | __funnelshift_r(w0, w1, KA.sh);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const T c = (T)(chunk >> (v * wa)) & amask;
+                    x[b][v] = (!CHECK || rec0 + v < nvalid) ? c : (T)0u;
+                }
+            } else {
+                const uint32_t p = sa + RA.off + gg * RA.step;
+                if (!CHECK || rec0 + V <= nvalid) {
+                    ld_run<V, SZL, T>(p, RA, x[b]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) x[b][v] = rec0 + v < nvalid ? (T)lds<SZL>(p + v * RA.vstride) : (T)0u;
+                }
+            }
+        }
+#pragma unroll
+        for (uint32_t b = 0; b < B; ++b)
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[b][v] = fast_convert<CV, CONV_ON_LOAD>(x[b][v], cr);
+#pragma unroll
+        for (uint32_t b = 0; b < B; ++b) {
+            const uint32_t gg = g + b;
+            if (CHECK && gg >= g1) break;
+            if (SK == FS_BITS) {
+                uint64_t chunk = 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) chunk |= (uint64_t)(x[b][v] & bmask) << (v * wb);
+                const uint32_t lo = (uint32_t)chunk, hi = (uint32_t)(chunk >> 32);
+                const uint32_t q = bbase + 4u * gg * cb;
+                const uint32_t w0 = chunk_word<MANY>(lo, hi, cb, KB, 0);
+                if (lane < cb) sts<4>(q, w0);
+                if (cb > 32u) {
+                    const uint32_t w1 = chunk_word<MANY>(lo, hi, cb, KB, 1);
+                    if (lane + 32u < cb) sts<4>(q + 128u, w1);
+                }
+            } else {
+                st_run<V, SZS, T>(da + RB.off + gg * RB.step, RB, x[b]);
+            }
+        }
+    };
+    const uint32_t gfull = min(g1, max(g0, nvalid / (32u * V)));  // super-groups below hold valid records only
+    uint32_t g = g0;
+    for (; g + B <= gfull; g += B) body(g, std::false_type{});
+    for (; g < g1; g += B) body(g, std::true_type{});
+}
+
+// Runs a VALUE item over quads [q0, q1) (128 records each) in its
+// specialised loop; false when it has none.
+__device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                         uint32_t q0, uint32_t q1, uint32_t nvalid)
+{
+#define LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, V, MANY) \
+    fast_loop<LK, SK, SZL, SZS, CV, OL, V, MANY>(I, J, simg, dimg, q0 * (4u / V), q1 * (4u / V), nvalid)
+// streams: V from the width; chunks under 32 bits (widths below 8) take MANY
+#define LLGB_FAST(K, LK, SK, SZL, SZS, CV, OL)                                             \
+    case K:                                                                                \
+        if (I.vpl == 4) {                                                                  \
+            if (width < 8u) LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, 4, true);                \
+            else LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, 4, false);                          \
+        } else if (I.vpl == 2) LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, 2, false);            \
+        else LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, 1, false);                              \
+        return true;
+#define LLGB_FAST1(K, LK, SK, SZL, SZS, CV, OL, V) \
+    case K: LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, V, false); return true;
+    const uint32_t width = I.sop == S_BITS_INT || I.sop == S_BITS_FLOAT ? I.d_bits : I.s_bits;
     switch (I.fast) {
-    case FK_PACK_INT32: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_INT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_INT32: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_INT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_D_F32: fast_loop<FL_AFF, FS_AL, 8, 4, FC_D2F, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL32_FROM8: fast_loop<FL_AFF, FS_AL, 8, 4, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL32_FROM4: fast_loop<FL_AFF, FS_AL, 4, 4, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL64_FROM8: fast_loop<FL_AFF, FS_AL, 8, 8, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL64_FROM4: fast_loop<FL_AFF, FS_AL, 4, 8, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL16_FROM8: fast_loop<FL_AFF, FS_AL, 8, 2, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL16_FROM4: fast_loop<FL_AFF, FS_AL, 4, 2, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_BITS_FROM8: fast_loop<FL_AFF, FS_BITS, 8, 8, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_BITS_FROM4: fast_loop<FL_AFF, FS_BITS, 4, 4, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_F32_D: fast_loop<FL_AL, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL32_TO8: fast_loop<FL_AL, FS_AFF, 4, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL32_TO4: fast_loop<FL_AL, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL64_TO8: fast_loop<FL_AL, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL64_TO4: fast_loop<FL_AL, FS_AFF, 8, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL16_TO8: fast_loop<FL_AL, FS_AFF, 2, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL16_TO4: fast_loop<FL_AL, FS_AFF, 2, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_BITS_TO8: fast_loop<FL_BITS, FS_AFF, 8, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_BITS_TO4: fast_loop<FL_BITS, FS_AFF, 4, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_CT_D_F32: fast_loop<FL_AFF, FS_AFF, 8, 4, FC_D2F, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_CT_F32_D: fast_loop<FL_AFF, FS_AFF, 4, 8, FC_F2D, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL8_FROM8: fast_loop<FL_AFF, FS_AL, 8, 1, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_PACK_AL8_FROM4: fast_loop<FL_AFF, FS_AL, 4, 1, FC_RT, false>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL8_TO8: fast_loop<FL_AL, FS_AFF, 1, 8, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
-    case FK_UNPACK_AL8_TO4: fast_loop<FL_AL, FS_AFF, 1, 4, FC_RT, true>(I, J, simg, dimg, sp, nvalid); return true;
+        LLGB_FAST(FK_PACK_INT32, FL_AFF, FS_BITS, 4, 4, FC_INT, false)
+        LLGB_FAST(FK_UNPACK_INT32, FL_BITS, FS_AFF, 4, 4, FC_INT, true)
+        LLGB_FAST(FK_PACK_BITS_FROM8, FL_AFF, FS_BITS, 8, 8, FC_RT, false)
+        LLGB_FAST(FK_PACK_BITS_FROM4, FL_AFF, FS_BITS, 4, 4, FC_RT, false)
+        LLGB_FAST(FK_UNPACK_BITS_TO8, FL_BITS, FS_AFF, 8, 8, FC_RT, true)
+        LLGB_FAST(FK_UNPACK_BITS_TO4, FL_BITS, FS_AFF, 4, 4, FC_RT, true)
+        LLGB_FAST1(FK_PACK_D_F32, FL_AFF, FS_AL, 8, 4, FC_D2F, false, 2)
+        LLGB_FAST1(FK_PACK_AL32_FROM8, FL_AFF, FS_AL, 8, 4, FC_RT, false, 2)
+        LLGB_FAST1(FK_PACK_AL32_FROM4, FL_AFF, FS_AL, 4, 4, FC_RT, false, 4)
+        LLGB_FAST1(FK_PACK_AL64_FROM8, FL_AFF, FS_AL, 8, 8, FC_RT, false, 2)
+        LLGB_FAST1(FK_PACK_AL64_FROM4, FL_AFF, FS_AL, 4, 8, FC_RT, false, 4)
+        LLGB_FAST1(FK_PACK_AL16_FROM8, FL_AFF, FS_AL, 8, 2, FC_RT, false, 2)
+        LLGB_FAST1(FK_PACK_AL16_FROM4, FL_AFF, FS_AL, 4, 2, FC_RT, false, 4)
+        LLGB_FAST1(FK_PACK_AL8_FROM8, FL_AFF, FS_AL, 8, 1, FC_RT, false, 2)
+        LLGB_FAST1(FK_PACK_AL8_FROM4, FL_AFF, FS_AL, 4, 1, FC_RT, false, 4)
+        LLGB_FAST1(FK_UNPACK_F32_D, FL_AL, FS_AFF, 4, 8, FC_F2D, true, 2)
+        LLGB_FAST1(FK_UNPACK_AL32_TO8, FL_AL, FS_AFF, 4, 8, FC_RT, true, 2)
+        LLGB_FAST1(FK_UNPACK_AL32_TO4, FL_AL, FS_AFF, 4, 4, FC_RT, true, 4)
+        LLGB_FAST1(FK_UNPACK_AL64_TO8, FL_AL, FS_AFF, 8, 8, FC_RT, true, 2)
+        LLGB_FAST1(FK_UNPACK_AL64_TO4, FL_AL, FS_AFF, 8, 4, FC_RT, true, 4)
+        LLGB_FAST1(FK_UNPACK_AL16_TO8, FL_AL, FS_AFF, 2, 8, FC_RT, true, 2)
+        LLGB_FAST1(FK_UNPACK_AL16_TO4, FL_AL, FS_AFF, 2, 4, FC_RT, true, 4)
+        LLGB_FAST1(FK_UNPACK_AL8_TO8, FL_AL, FS_AFF, 1, 8, FC_RT, true, 2)
+        LLGB_FAST1(FK_UNPACK_AL8_TO4, FL_AL, FS_AFF, 1, 4, FC_RT, true, 4)
+        LLGB_FAST1(FK_CT_D_F32, FL_AFF, FS_AFF, 8, 4, FC_D2F, false, 2)
+        LLGB_FAST1(FK_CT_F32_D, FL_AFF, FS_AFF, 4, 8, FC_F2D, true, 2)
     default: return false;
     }
+#undef LLGB_FAST1
+#undef LLGB_FAST
+#undef LLGB_FAST_V
 }
 
-// Zero the bit streams that values are ORed into (all but whole-byte widths).
-__device__ __forceinline__ bool zero_streams(const JobDesc& J, uint8_t* dimg)
+// Zero the bit streams that generic items OR their codes into.
+__device__ __noinline__ void zero_streams(const JobDesc& J, uint8_t* dimg)
 {
-    bool any = false;
     for (int k = 0; k < J.npacks; ++k) {
         const PackDesc& P = J.packs[k];
-        if (P.aligned) continue;
+        if (!P.ored) continue;
         uint4* z = reinterpret_cast<uint4*>(dimg + P.dst_sbase);
         for (uint32_t q = ctid(); q < (P.bytes + 15u) / 16u; q += cnum()) z[q] = make_uint4(0, 0, 0, 0);
-        any = true;
     }
-    return any;
 }
 
-// Every item runs over the tile in units of 128 records handed to warps
-// round-robin: a unit loads its descriptors once for 4 records per lane,
-// and jobs with few items still keep every warp busy.
-constexpr uint32_t kUnitRecords = 128;
-
-__device__ __forceinline__ void run_item_span(const JobDesc& J, const ItemDesc& I, const uint8_t* simg, uint8_t* dimg,
-                                              Span sp, uint32_t nvalid)
+// Quads [q0, q1) (128 records each) of one item.
+__device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc& I, const uint8_t* simg,
+                                               uint8_t* dimg, uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
+    const Span sp{128u * q0 + (threadIdx.x & 31u), 128u * q1, 32u};
     if (I.op == ITEM_MOVE) {
         const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
         const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);
@@ -509,7 +853,7 @@ __device__ __forceinline__ void run_item_span(const JobDesc& J, const ItemDesc& 
         case 2: move_loop<2>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
         default: move_loop<1>(A, B, I.src_byte, I.dst_byte, I.size, simg, dimg, sp, nvalid); break;
         }
-    } else if (!run_fast(I, J, simg, dimg, sp, nvalid)) {
+    } else if (!run_fast(I, J, simg, dimg, q0, q1, nvalid)) {
         switch (I.lop) {
         case L_DIRECT: value_dispatch<L_DIRECT>(I, J, simg, dimg, sp, nvalid); break;
         case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, sp, nvalid); break;
@@ -520,14 +864,33 @@ __device__ __forceinline__ void run_item_span(const JobDesc& J, const ItemDesc& 
     }
 }
 
-__device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid)
+// The tile's work is nitems x (tile / 128) quads, laid out item by item, cut
+// into cnum/32 equal contiguous shares (sizes differ by one quad at most);
+// consumer warp w takes share w of every tile of a job.
+struct ItemShare {
+    uint32_t item, quad, count;  // first item and quad, quads in the share
+};
+
+__device__ __forceinline__ ItemShare item_share(const JobDesc& J)
 {
-    const uint32_t lane = threadIdx.x & 31u, wid = ctid() >> 5, nw = cnum() >> 5;
-    const uint32_t chunks = J.tile / kUnitRecords;
-    const uint32_t units = J.nitems * chunks;
-    for (uint32_t u = wid; u < units; u += nw) {
-        const uint32_t it = u / chunks, c = u - it * chunks;
-        run_item_span(J, J.items[it], simg, dimg, Span{c * kUnitRecords + lane, (c + 1) * kUnitRecords, 32u}, nvalid);
+    const uint32_t w = ctid() >> 5, nw = cnum() >> 5;
+    const uint32_t Q = J.tile >> 7;
+    const uint32_t total = (uint32_t)J.nitems * Q;  // <= 64 items x 2^10 quads
+    const uint32_t lo = total * w / nw, hi = total * (w + 1u) / nw;
+    const uint32_t it = Q ? lo / Q : 0u;
+    return ItemShare{it, lo - it * Q, hi - lo};
+}
+
+__device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid, ItemShare S)
+{
+    const uint32_t Q = J.tile >> 7;
+    uint32_t it = S.item, q0 = S.quad, left = S.count;
+    while (left) {
+        const uint32_t q1 = min(Q, q0 + left);
+        run_item_quads(J, J.items[it], simg, dimg, q0, q1, nvalid);
+        left -= q1 - q0;
+        ++it;
+        q0 = 0;
     }
 }
 
@@ -808,6 +1171,7 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
     LaneRuns in, out;
+    uint32_t issued = 0;  // tiles whose loads have been issued: 0 .. issued-1
 
     auto issue_load = [&](uint32_t k) {
         const uint32_t g = tile_index(a, first, k);
@@ -817,6 +1181,7 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             const JobDesc* J = a.table ? a.table + j : &a.job;
             lane_runs_load(in, J->src, J, (int)j, lane);
         }
+        issued = k + 1u;
         if (!(t < in.nfull && in.bulk)) return;
         const uint32_t s = k % NS;
         if (lane == 0) mbar_arrive_expect_tx(&H.full[s], in.total);
@@ -856,9 +1221,29 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             }
             issue_load(k + NS);
         }
-        if (H.abort) break;
+        if (*reinterpret_cast<volatile int*>(&H.abort)) break;
     }
     bulk_wait_all();
+    if (*reinterpret_cast<volatile int*>(&H.abort)) {
+        // the consumers may have left: wait (bounded) for the loads of the
+        // last NS issued tiles, which may still be landing in shared memory
+        for (uint32_t k = issued > NS ? issued - NS : 0u; k < issued; ++k) {
+            const uint32_t g = tile_index(a, first, k);
+            const uint32_t j = job_of(a, g);
+            const JobDesc* J = a.table ? a.table + j : &a.job;
+            const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+            if (t < J->nfull && J->src.bulk_ok) (void)mbar_wait_bounded(&H.full[k % NS], (k / NS) & 1u);
+        }
+    }
+}
+
+// Bounded wait that gives up at once after an abort (the phase may never
+// complete then); a timeout records the abort for every role.
+__device__ __forceinline__ void wait_or_abort(CopyShared& H, uint64_t* bar, uint32_t parity)
+{
+    volatile int* abort_flag = &H.abort;
+    if (*abort_flag) return;
+    if (!mbar_wait_bounded(bar, parity)) *abort_flag = 1;
 }
 
 // Consumer warps: convert each tile from its source stage into a destination
@@ -875,6 +1260,9 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     uint32_t phase = 0;        // per source stage: parity of the next full phase
     uint32_t zeroed = 0;       // destination stages whose padding bytes are zero (current job)
     int cur_job = -1;
+    uint32_t s = 0, d = 0;     // stages of tile k: k % NS, k % ND
+    uint32_t dround = 0;       // parity of k / ND
+    ItemShare share{0u, 0u, 0u};
 
     for (uint32_t k = 0; k < count; ++k) {
         const uint32_t g = tile_index(a, first, k);
@@ -887,6 +1275,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             consumer_sync();
             cur_job = (int)j;
             zeroed = 0;
+            if (MODE == 0) share = item_share(H.job);
             if (MODE != 0) {
                 gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
                 build_gather<MODE>(H.job, zero_word, gather_words, gp);
@@ -895,38 +1284,48 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
         const JobDesc& J = H.job;
         const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
         const uint32_t nvalid = (t + 1u < J.ntiles) ? J.tile : (uint32_t)(J.n - (uint64_t)t * J.tile);
-        const uint32_t s = k % NS, d = k % ND;
         uint8_t* simg = src_stage + s * a.src_stage_bytes;
         uint8_t* dimg = dst_stage + d * a.dst_stage_bytes;
         const bool bulk_in = t < J.nfull && J.src.bulk_ok;
         const bool bulk_out = t < J.nfull && J.dst.bulk_ok;
 
-        bool ok = true;
+        // Consumer warps run without a per-tile barrier: each waits on the
+        // stage barriers itself, so warps may drift apart by up to
+        // min(src_stages, dst_stages) tiles.  The barriers below are taken
+        // at the same tiles by every warp, aborted or not (a wait that timed
+        // out sets H.abort, and later waits return at once).
+        bool sync_needed = false;
         if (bulk_in) {
-            ok = mbar_wait_bounded(&H.full[s], (phase >> s) & 1u);
+            wait_or_abort(H, &H.full[s], (phase >> s) & 1u);
             phase ^= 1u << s;
         } else {
+            consumer_sync();  // every warp is done with the stage's previous tile
             const bool last = (t + 1u == J.ntiles);
             for (int q = 0; q < J.src.nsegs; ++q) {
                 const SegDesc& S = J.src.segs[q];
                 plain_copy(simg + S.sbase, J.src.blobs[S.blob] + S.gbase + (uint64_t)t * S.tile_bytes,
                            last ? S.tail_bytes : S.tile_bytes);
             }
+            sync_needed = true;
         }
-        ok = mbar_wait_bounded(&H.dempty[d], ((k / ND) + 1u) & 1u) && ok;
-        if (!ok) H.abort = 1;
-        consumer_sync();
-        if (H.abort) break;
+        wait_or_abort(H, &H.dempty[d], dround ^ 1u);
 
         // Items write leaf bytes only: their stage must start with zero padding.
-        // (A gather program writes every word, zeros included.)
+        // (A gather program writes every word, zeros included.)  The store
+        // of the stage's previous tile has read it (dempty), and that tile's
+        // writers all arrived before the store was issued.
         const bool items_here = MODE == 0 || t >= J.nfull;
         if (items_here && !(zeroed & (1u << d))) {
             uint4* z = reinterpret_cast<uint4*>(dimg);
             for (uint32_t w = ctid(); w < a.dst_stage_bytes / 16u; w += cnum()) z[w] = make_uint4(0, 0, 0, 0);
             zeroed |= 1u << d;
-            consumer_sync();
+            sync_needed = true;
         }
+        if (MODE == 0 && J.ored) {
+            zero_streams(J, dimg);
+            sync_needed = true;
+        }
+        if (sync_needed) consumer_sync();
         if (t == 0) {
             for (int q = 0; q < J.nzeros; ++q) {
                 const ZeroRun& Z = J.zeros[q];
@@ -942,8 +1341,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                 run_moves(J, simg, dimg, nvalid);
             }
         } else {
-            if (zero_streams(J, dimg)) consumer_sync();
-            run_items(J, simg, dimg, nvalid);
+            run_items(J, simg, dimg, nvalid, share);
         }
         fence_proxy_async();
         __syncwarp();
@@ -959,6 +1357,11 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             __syncwarp();
         }
         if (warp_leader) mbar_arrive(&H.dfull[d]);
+        if (++s == NS) s = 0;
+        if (++d == ND) {
+            d = 0;
+            dround ^= 1u;
+        }
     }
 }
 

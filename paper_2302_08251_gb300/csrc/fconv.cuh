@@ -8,8 +8,9 @@
 // its sign and the top bits of its payload and has its top mantissa bit set.
 //
 // Formats are (E exponent bits, M mantissa bits), IEEE layout sign|exp|man,
-// bias 2^(E-1)-1.  Hardware conversions (cvt.rn) are used for the standard
-// pairs whenever the input is not a NaN; they round the same way.
+// bias 2^(E-1)-1.  For the standard pairs of a non-NaN input, f64 <-> f32
+// takes the integer routines below and f32 <-> f16 / bf16 the hardware
+// conversions (cvt.rn), which round the same way.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -77,6 +78,38 @@ __device__ __noinline__ uint64_t fconv_general(uint64_t x, int se, int sm, int d
     return out_sign | code;
 }
 
+// f64 -> f32 with integer operations (the FP64 pipe of this GPU is narrow).
+// Results in the normal f32 range are rounded here: the top 23 mantissa bits
+// are kept, the 29 below decide the rounding, and a carry out of the
+// mantissa moves into the exponent (all-ones exponent: INF).  Zero, NaN, INF
+// and subnormal results go through fconv_general.
+__device__ __forceinline__ uint32_t f64_to_f32_bits(uint64_t x)
+{
+    const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
+    const uint32_t s = hi & 0x80000000u;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e - 897u < 254u) {  // f32 exponent 1 .. 254 before rounding
+        uint32_t r = ((e - 896u) << 23) | (__funnelshift_l(lo, hi, 3) & 0x7FFFFFu);
+        const uint32_t rest = lo & 0x1FFFFFFFu;
+        r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+        return s | r;
+    }
+    if (e > 1150u && e != 0x7FFu) return s | 0x7F800000u;   // beyond the f32 range: INF
+    if ((hi & 0x7FFFFFFFu) == 0u && lo == 0u) return s;      // signed zero
+    return (uint32_t)fconv_general(x, 11, 52, 8, 23);
+}
+
+// f32 -> f64 (exact) with integer operations: a normal input only rebiases
+// its exponent and moves its mantissa up by 29 bits.
+__device__ __forceinline__ uint64_t f32_to_f64_bits(uint32_t u)
+{
+    const uint32_t s = u & 0x80000000u, a = u & 0x7FFFFFFFu;
+    if (a - 0x00800000u < 0x7F000000u)  // exponent 1 .. 254
+        return ((uint64_t)(s | ((a >> 3) + (896u << 20))) << 32) | (uint64_t)(u << 29);
+    if (a == 0u) return (uint64_t)s << 32;
+    return fconv_general(u, 8, 23, 11, 52);  // subnormal, INF, NaN
+}
+
 __device__ __forceinline__ bool is_nan_bits(uint64_t x, int e, int m)
 {
     const uint64_t all = (1ull << e) - 1ull;
@@ -88,12 +121,11 @@ __device__ __forceinline__ uint64_t fconv(uint64_t x, int se, int sm, int de, in
 {
     if (!is_nan_bits(x, se, sm)) {
         if (se == 11 && sm == 52) {
-            const double d = __longlong_as_double((long long)x);
-            if (de == 8 && dm == 23) return (uint64_t)__float_as_uint(__double2float_rn(d));
+            if (de == 8 && dm == 23) return f64_to_f32_bits(x);
             if (de == 11 && dm == 52) return x;
         } else if (se == 8 && sm == 23) {
             const float f = __uint_as_float((uint32_t)x);
-            if (de == 11 && dm == 52) return (uint64_t)__double_as_longlong((double)f);
+            if (de == 11 && dm == 52) return f32_to_f64_bits((uint32_t)x);
             if (de == 5 && dm == 10) return (uint64_t)__half_as_ushort(__float2half_rn(f));
             if (de == 8 && dm == 7) return (uint64_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
             if (de == 8 && dm == 23) return x;

@@ -78,7 +78,8 @@ struct ItemDesc {
     uint8_t s_bits;      // source bits (L_BITS_*)
     uint8_t d_bits;      // destination bits (S_BITS_*)
     uint8_t fast;        // FastKind of the specialised loop, FK_GENERIC if none
-    uint8_t pad[3];
+    uint8_t vpl;         // specialised loop: consecutive records per lane (1, 2, 4)
+    uint8_t pad[2];
 };
 
 // Specialised VALUE loops (element sizes and conversion fixed at compile time).
@@ -112,15 +113,17 @@ enum FastKind : uint8_t {
     FK_UNPACK_AL8_TO4
 };
 
-// A bit-stream destination leaf.  Values are ORed into the stream, so the
-// consumers zero its `bytes` at `dst_sbase` before every tile -- unless the
-// width is 8, 16, 32 or 64 bits, where codes are stored whole.
+// A bit-stream destination leaf.  Specialised loops store whole words of the
+// stream; a generic item ORs its codes into it (unless the width is 8, 16,
+// 32 or 64 bits), and then the consumers zero the stream's `bytes` at
+// `dst_sbase` before every tile (`ored`).
 struct PackDesc {
     uint32_t dst_sbase;  // destination image offset of the stream
     uint32_t bytes;      // stream bytes per tile
     uint8_t bits;
     uint8_t aligned;
-    uint8_t pad[6];
+    uint8_t ored;
+    uint8_t pad[5];
 };
 
 struct SideDesc {
@@ -159,6 +162,8 @@ struct JobDesc {
     uint16_t nzeros;
     uint8_t gather;      // full tiles use gather programs: 0 no, 2 or 4 source words
     uint8_t interleave;  // 4-word gathers: deal destination words round-robin over the runs
+    uint8_t ored;        // some PackDesc has `ored` set: zero those streams before every tile
+    uint8_t pad[7];
 };
 
 // Launch-wide parameters of the copy kernel.

@@ -472,9 +472,8 @@ static int fast_kind(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
     const bool a_al = A.kind == LEAF_BITS && (A.bits == 8 || A.bits == 16 || A.bits == 32 || A.bits == 64);
     const bool b_al = B.kind == LEAF_BITS && (B.bits == 8 || B.bits == 16 || B.bits == 32 || B.bits == 64);
     const int size = it.size;
-    // integers: plain leaf <-> bit stream of at most 32 bits, 4-byte leaves
-    // (whole-byte widths are stored whole by the generic loop, not ORed)
-    if (it.lop == L_DIRECT && it.sop == S_BITS_INT && a_aff && size == 4 && A.align >= 4 && it.d_bits <= 32 && !b_al)
+    // integers: plain 4-byte leaf <-> bit stream of at most 32 bits
+    if (it.lop == L_DIRECT && it.sop == S_BITS_INT && a_aff && size == 4 && A.align >= 4 && it.d_bits <= 32)
         return FK_PACK_INT32;
     if (it.lop == L_BITS_INT && it.sop == S_DIRECT && b_aff && size == 4 && B.align >= 4 && A.bits <= 32)
         return FK_UNPACK_INT32;
@@ -503,6 +502,45 @@ static int fast_kind(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
         B.align >= 8 && fmt_is(it.s_e, it.s_m, 8, 23))
         return FK_CT_F32_D;
     return FK_GENERIC;
+}
+
+// The specialised loops give each lane V consecutive records of every 32 V:
+// V = 4, 2 or 1 for streams of <= 16, <= 32 or more bits (a lane's codes
+// then fill 32..64 bits), and 16 bytes over the widest affine element
+// otherwise.  An affine leaf must keep a lane's V records at a constant
+// stride: one lane, or a power-of-two lane count that V divides and that
+// divides 32 V.
+static bool affine_for(const LeafDesc& L, int V)
+{
+    if (L.kind != LEAF_AFFINE) return true;
+    if (L.lanes == 1) return true;
+    return L.lshift != 0xFF && L.lanes % (uint32_t)V == 0 && L.lanes <= 32u * (uint32_t)V;
+}
+
+static void set_fast_kind(ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
+{
+    const int k = fast_kind(it, A, B);
+    int V = 0;
+    switch (k) {
+    case FK_GENERIC: break;
+    case FK_PACK_INT32:
+    case FK_PACK_BITS_FROM8:
+    case FK_PACK_BITS_FROM4: V = it.d_bits <= 16 ? 4 : (it.d_bits <= 32 ? 2 : 1); break;
+    case FK_UNPACK_INT32:
+    case FK_UNPACK_BITS_TO8:
+    case FK_UNPACK_BITS_TO4: V = A.bits <= 16 ? 4 : (A.bits <= 32 ? 2 : 1); break;
+    default: {
+        const int widest = std::max(A.kind == LEAF_AFFINE ? (int)A.size : 0, B.kind == LEAF_AFFINE ? (int)B.size : 0);
+        V = 16 / widest;
+    }
+    }
+    if (k != FK_GENERIC && affine_for(A, V) && affine_for(B, V)) {
+        it.fast = (uint8_t)k;
+        it.vpl = (uint8_t)V;
+    } else {
+        it.fast = FK_GENERIC;
+        it.vpl = 0;
+    }
 }
 
 llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, const ViewPlan& dst,
@@ -546,8 +584,8 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         }
     }
 
-    // Bit-stream destination leaves: values are ORed into their streams, which
-    // the consumers zero first unless the width is a whole number of bytes.
+    // Bit-stream destination leaves (whether a generic item ORs into one is
+    // known once the items exist, below).
     for (int g = 0; g < (int)dst.stored.size(); ++g) {
         if (dst.base < BASE_BITS_INT) break;
         if (job->npacks >= kMaxPacks) {
@@ -639,9 +677,16 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
                 it.d_m = (uint8_t)dst.stored[b.first].m;
             }
             if (b.op == L_BITS_INT || b.op == L_BITS_FLOAT) it.d_bits = (uint8_t)dst.stored[b.first].bits;
-            it.fast = (uint8_t)fast_kind(it, job->src.leaves[a.first], job->dst.leaves[b.first]);
+            set_fast_kind(it, job->src.leaves[a.first], job->dst.leaves[b.first]);
             if (!add(it)) return too_many();
         }
+    }
+    for (int k = 0; k < job->nitems; ++k) {
+        const ItemDesc& it = job->items[k];
+        if (it.op != ITEM_VALUE || (it.sop != S_BITS_INT && it.sop != S_BITS_FLOAT)) continue;
+        PackDesc& P = job->packs[it.dst_leaf];
+        P.ored = (it.fast == FK_GENERIC && !P.aligned) ? 1 : 0;
+        job->ored |= P.ored;
     }
     // Jobs made only of byte moves run full tiles through gather programs:
     // 2 source words per destination word when every move is at least

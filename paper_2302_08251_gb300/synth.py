@@ -113,6 +113,28 @@ def special_f64(n: int, seed: int) -> np.ndarray:
     return out.view(np.float64)
 
 
+def f32_range_f64(n: int, seed: int) -> np.ndarray:
+    """f64 values whose exponents lie in and around the f32 range, with the
+    29 mantissa bits below an f32 mantissa set to exactly half an f32 ulp
+    (a tie), one unit either side of it, zero, or random: the cases where
+    rounding f64 -> f32 to nearest even can go wrong."""
+    g = rng(seed)
+    sign = g.integers(0, 2, n, dtype=np.uint64) << np.uint64(63)
+    # f64 exponents 1023-130 .. 1023+130 (f32 subnormals .. beyond f32 max)
+    exp = g.integers(1023 - 130, 1023 + 131, n, dtype=np.uint64) << np.uint64(52)
+    top = g.integers(0, 1 << 23, n, dtype=np.uint64) << np.uint64(29)
+    half = np.uint64(1 << 28)
+    low_choices = np.stack([np.full(n, half, np.uint64), np.full(n, half - np.uint64(1), np.uint64),
+                            np.full(n, half + np.uint64(1), np.uint64), np.zeros(n, np.uint64),
+                            g.integers(0, 1 << 29, n, dtype=np.uint64)])
+    low = low_choices[g.integers(0, 5, n), np.arange(n)]
+    top_all = np.full(n, np.uint64(((1 << 23) - 1) << 29), np.uint64)
+    # a quarter of the values carry an all-ones f32 mantissa (rounding carries into the exponent)
+    top = np.where(g.integers(0, 4, n) == 0, top_all, top)
+    bits = sign | exp | top | low
+    return bits.view(np.float64)
+
+
 def special_f32(n: int, seed: int) -> np.ndarray:
     """f32 counterpart of ``special_f64``."""
     g = rng(seed)

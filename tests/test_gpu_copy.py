@@ -285,3 +285,64 @@ def test_bitpack_int_many_tiles_per_cta(b):
     cfg = {"tile_records": 128, "src_stages": 2, "dst_stages": 2, "threads": 128, "ctas_per_sm": 1}
     run_pair(synth.INT6, fields, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": b}, cfg)
     run_pair(synth.INT6, fields, {"kind": "bitpack_int", "bits": b}, {"kind": "aos"}, cfg)
+
+
+# ---- the specialised value loops: lane-constant addressing of 32-record
+# groups, shuffle-assembled stream words, integer f64 <-> f32 conversion ----
+
+SHAPES = [
+    {"tile_records": 128, "src_stages": 2, "dst_stages": 2, "threads": 128, "ctas_per_sm": 1},
+    {"tile_records": 384, "src_stages": 2, "dst_stages": 3, "threads": 512, "ctas_per_sm": 1},
+    {"tile_records": 1152, "src_stages": 2, "dst_stages": 2, "threads": 256, "ctas_per_sm": 1},
+]
+
+
+@pytest.mark.parametrize("cfg", SHAPES, ids=lambda c: f"t{c['tile_records']}x{c['threads']}")
+@pytest.mark.parametrize("b", [8, 16, 32])
+def test_bitpack_int_whole_byte_widths(b, cfg):
+    n = 200000 + 77
+    fields = synth.int6(n, b, seed=3 * b)
+    packed = {"kind": "bitpack_int", "bits": b}
+    for other in ({"kind": "soa_mb"}, {"kind": "aosoa", "lanes": 8}, {"kind": "aosoa", "lanes": 64}):
+        run_pair(synth.INT6, fields, other, packed, cfg)
+        run_pair(synth.INT6, fields, packed, other, cfg)
+
+
+@pytest.mark.parametrize("cfg", SHAPES, ids=lambda c: f"t{c['tile_records']}x{c['threads']}")
+@pytest.mark.parametrize("b", [1, 2, 5, 12, 13, 24, 31])
+def test_bitpack_int_group_boundaries(b, cfg):
+    # tiles of 4, 12 and 36 groups over 3, 15 and 7 consumer warps: item
+    # shares start and end inside items
+    n = 150000 + 31
+    fields = synth.int6(n, b, seed=b)
+    packed = {"kind": "bitpack_int", "bits": b}
+    run_pair(synth.INT6, fields, {"kind": "aosoa", "lanes": 16}, packed, cfg)
+    run_pair(synth.INT6, fields, packed, {"kind": "aosoa", "lanes": 4}, cfg)
+
+
+@pytest.mark.parametrize("em", [(11, 40), (8, 40), (10, 30), (11, 51), (9, 24)],
+                         ids=lambda x: f"E{x[0]}M{x[1]}")
+def test_bitpack_float_codes_wider_than_32_bits(em):
+    e, m = em
+    n = 90000 + 5
+    fields = synth.mixed_f(n, seed=e * m)
+    fields[1] = synth.special_f64(n, seed=e)[:n]
+    fields[3] = synth.special_f32(n, seed=m)[:n]
+    packed = {"kind": "bitpack_float", "exp": e, "man": m}
+    for cfg in SHAPES[:2]:
+        run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, packed, cfg)
+        run_pair(synth.MIXED_F, fields, packed, {"kind": "aos"}, cfg)
+
+
+def test_f64_to_f32_rounding_ties_and_range_edges():
+    n = 300000 + 9
+    fields = synth.mixed_f(n, seed=8)
+    for k in range(3):
+        fields[k] = synth.f32_range_f64(n, seed=20 + k)
+    f32 = {"kind": "bitpack_float", "exp": 8, "man": 23}
+    ct = {"kind": "changetype", "ct": [("f64", "f32")], "inner": {"kind": "soa_mb"}}
+    for cfg in (None, SHAPES[1]):
+        run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, f32, cfg)
+        run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, ct, cfg)
+        run_pair(synth.MIXED_F, fields, ct, {"kind": "aos"}, cfg)
+        run_pair(synth.MIXED_F, fields, f32, {"kind": "soa_mb"}, cfg)

@@ -216,6 +216,18 @@ def test_f64_to_f32_matches_numpy_cast():
     assert np.array_equal(got[ok], want[ok])
 
 
+def test_f64_to_f32_ties_and_range_edges_match_numpy_cast():
+    # exact ties, one unit either side, mantissa carries into the exponent,
+    # overflow to INF and results in the f32 subnormal range
+    xs = synth.f32_range_f64(400000, seed=11)
+    got = oracle.convert_array(xs.view(np.uint64), *F64, *F32).astype(np.uint32)
+    with np.errstate(over="ignore"):
+        want = xs.astype(np.float32).view(np.uint32)
+    assert np.array_equal(got, want)
+    widened = oracle.convert_array(want.astype(np.uint64), *F32, *F64)
+    assert np.array_equal(widened, want.view(np.float32).astype(np.float64).view(np.uint64))
+
+
 def test_f32_to_f16_matches_numpy_cast():
     g = synth.rng(7)
     xs = synth.special_f32(1 << 20, seed=2)
