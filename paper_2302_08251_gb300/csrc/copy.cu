@@ -775,6 +775,129 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
     for (; g < g1; g += B) body(g, std::true_type{});
 }
 
+// ------------------------------------------------------- byte planes --
+//
+// Bytesplit (Sec. 3 of the paper) stores byte j of every value of a leaf in
+// plane j.  Lane l takes 4 consecutive records of a super-group of 128: the
+// 4 SZ-byte values are a 4 x SZ byte matrix, and plane j's word for those
+// records is its column j.  SZ = 4 is one 4 x 4 byte transpose (8 PRMT),
+// SZ = 8 two, SZ = 2 two PRMT per direction; the transpose is its own
+// inverse, so splitting and joining share it.
+
+__device__ __forceinline__ void transpose4x4(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d)
+{
+    const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
+    const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
+    a = __byte_perm(t0, t2, 0x5410);
+    b = __byte_perm(t0, t2, 0x7632);
+    c = __byte_perm(t1, t3, 0x5410);
+    d = __byte_perm(t1, t3, 0x7632);
+}
+
+// The 4 records' values as SZ words (row-major: word q holds bytes
+// 4q .. 4q+3 of the 4 x SZ matrix read value by value) <-> plane words.
+template <int SZ>
+__device__ __forceinline__ void rows_to_planes(uint32_t (&w)[SZ])
+{
+    if constexpr (SZ == 2) {
+        const uint32_t p0 = __byte_perm(w[0], w[1], 0x6420), p1 = __byte_perm(w[0], w[1], 0x7531);
+        w[0] = p0;
+        w[1] = p1;
+    } else if constexpr (SZ == 4) {
+        transpose4x4(w[0], w[1], w[2], w[3]);
+    } else {
+        // values are (lo, hi) word pairs: lo words give planes 0..3, hi words 4..7
+        uint32_t a = w[0], b = w[2], c = w[4], d = w[6];
+        uint32_t e = w[1], f = w[3], g = w[5], h = w[7];
+        transpose4x4(a, b, c, d);
+        transpose4x4(e, f, g, h);
+        w[0] = a; w[1] = b; w[2] = c; w[3] = d;
+        w[4] = e; w[5] = f; w[6] = g; w[7] = h;
+    }
+}
+
+template <int SZ>
+__device__ __forceinline__ void planes_to_rows(uint32_t (&w)[SZ])
+{
+    if constexpr (SZ == 2) {
+        const uint32_t r0 = __byte_perm(w[0], w[1], 0x5140), r1 = __byte_perm(w[0], w[1], 0x7362);
+        w[0] = r0;
+        w[1] = r1;
+    } else if constexpr (SZ == 4) {
+        transpose4x4(w[0], w[1], w[2], w[3]);
+    } else {
+        uint32_t a = w[0], b = w[1], c = w[2], d = w[3];
+        uint32_t e = w[4], f = w[5], g = w[6], h = w[7];
+        transpose4x4(a, b, c, d);
+        transpose4x4(e, f, g, h);
+        w[0] = a; w[2] = b; w[4] = c; w[6] = d;
+        w[1] = e; w[3] = f; w[5] = g; w[7] = h;
+    }
+}
+
+// JOIN false: leaf -> planes (store side split); true: planes -> leaf.
+template <int SZ, bool JOIN>
+__device__ __noinline__ void split_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                        uint32_t g0, uint32_t g1, uint32_t nvalid)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t sa = smem_addr(simg), da = smem_addr(dimg);
+    const LeafDesc& LW = JOIN ? J.dst.leaves[I.dst_leaf] : J.src.leaves[I.src_leaf];
+    const LaneRun RW = affine_run<4, SZ>(LW, lane);
+    const uint32_t wbase = (JOIN ? da : sa) + RW.off;
+    LaneRun RP[SZ];
+    uint32_t pbase[SZ];
+#pragma unroll
+    for (int j = 0; j < SZ; ++j) {
+        RP[j] = affine_run<4, 1>(JOIN ? J.src.leaves[I.src_leaf + j] : J.dst.leaves[I.dst_leaf + j], lane);
+        pbase[j] = (JOIN ? sa : da) + RP[j].off;
+    }
+    for (uint32_t g = g0; g < g1; ++g) {
+        const uint32_t rec0 = 128u * g + 4u * lane;
+        const uint32_t nv = rec0 >= nvalid ? 0u : min(4u, nvalid - rec0);  // valid records of the lane
+        uint32_t w[SZ];
+        if (!JOIN) {
+            uint64_t x[4];
+            if (nv == 4u) {
+                ld_run<4, SZ, uint64_t>(wbase + g * RW.step, RW, x);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[v] = (uint32_t)v < nv ? lds<SZ>(wbase + g * RW.step + v * RW.vstride) : 0u;
+            }
+            elems_to_words<4, SZ, uint64_t>(x, w);
+            rows_to_planes<SZ>(w);
+#pragma unroll
+            for (int j = 0; j < SZ; ++j) {
+                const uint32_t a = pbase[j] + g * RP[j].step;
+                if (RP[j].vec) {
+                    sts<4>(a, w[j]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) sts<1>(a + v * RP[j].vstride, (w[j] >> (8 * v)) & 0xFFu);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < SZ; ++j) {
+                const uint32_t a = pbase[j] + g * RP[j].step;
+                if (RP[j].vec) {
+                    w[j] = (uint32_t)lds<4>(a);
+                } else {
+                    w[j] = 0u;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) w[j] |= (uint32_t)lds<1>(a + v * RP[j].vstride) << (8 * v);
+                }
+                // bytes of records at or past nvalid read as zero
+                w[j] &= nv >= 4u ? 0xFFFFFFFFu : ((1u << (8u * nv)) - 1u);
+            }
+            planes_to_rows<SZ>(w);
+            uint64_t x[4];
+            words_to_elems<4, SZ, uint64_t>(w, x);
+            st_run<4, SZ, uint64_t>(wbase + g * RW.step, RW, x);
+        }
+    }
+}
+
 // Runs a VALUE item over quads [q0, q1) (128 records each) in its
 // specialised loop; false when it has none.
 __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
@@ -821,6 +944,12 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
         LLGB_FAST1(FK_UNPACK_AL8_TO4, FL_AL, FS_AFF, 1, 4, FC_RT, true, 4)
         LLGB_FAST1(FK_CT_D_F32, FL_AFF, FS_AFF, 8, 4, FC_D2F, false, 2)
         LLGB_FAST1(FK_CT_F32_D, FL_AFF, FS_AFF, 4, 8, FC_F2D, true, 2)
+    case FK_SPLIT2: split_loop<2, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
+    case FK_SPLIT4: split_loop<4, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
+    case FK_SPLIT8: split_loop<8, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
+    case FK_JOIN2: split_loop<2, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
+    case FK_JOIN4: split_loop<4, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
+    case FK_JOIN8: split_loop<8, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
     default: return false;
     }
 #undef LLGB_FAST1

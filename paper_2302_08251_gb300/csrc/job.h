@@ -110,7 +110,13 @@ enum FastKind : uint8_t {
     FK_PACK_AL8_FROM8,    // -> 8-bit stream
     FK_PACK_AL8_FROM4,
     FK_UNPACK_AL8_TO8,
-    FK_UNPACK_AL8_TO4
+    FK_UNPACK_AL8_TO4,
+    FK_SPLIT2,            // 2 / 4 / 8-byte leaf -> its byte planes (Bytesplit store)
+    FK_SPLIT4,
+    FK_SPLIT8,
+    FK_JOIN2,             // byte planes -> 2 / 4 / 8-byte leaf (Bytesplit load)
+    FK_JOIN4,
+    FK_JOIN8
 };
 
 // A bit-stream destination leaf.  Specialised loops store whole words of the

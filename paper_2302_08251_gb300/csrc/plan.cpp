@@ -617,6 +617,33 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         const int size = type_size(t);
         const bool a_bytes = a.op == L_DIRECT || a.op == L_SPLIT;
         const bool b_bytes = b.op == L_DIRECT || b.op == L_SPLIT;
+        if (a_bytes && b_bytes && a.op != b.op && (size == 2 || size == 4 || size == 8)) {
+            // A leaf to its byte planes or back (Bytesplit, Sec. 3): one item
+            // transposes the bytes of 4 records per lane when every leaf
+            // involved keeps a lane's 4 records at a constant stride.
+            const bool split = b.op == L_SPLIT;
+            const LeafDesc& whole = split ? job->src.leaves[a.first] : job->dst.leaves[b.first];
+            const int planes0 = split ? b.first : a.first;
+            bool ok = affine_for(whole, 4) && whole.kind == LEAF_AFFINE && whole.align >= size;
+            for (int j = 0; j < size && ok; ++j) {
+                const LeafDesc& P = split ? job->dst.leaves[planes0 + j] : job->src.leaves[planes0 + j];
+                ok = P.kind == LEAF_AFFINE && affine_for(P, 4);
+            }
+            if (ok) {
+                ItemDesc it{};
+                it.op = ITEM_VALUE;
+                it.size = (uint8_t)size;
+                it.lop = (uint8_t)a.op;
+                it.sop = (uint8_t)b.op;
+                it.src_leaf = (uint8_t)a.first;
+                it.dst_leaf = (uint8_t)b.first;
+                const int k = size == 2 ? 0 : (size == 4 ? 1 : 2);
+                it.fast = (uint8_t)((split ? FK_SPLIT2 : FK_JOIN2) + k);
+                it.vpl = 4;
+                if (!add(it)) return too_many();
+                continue;
+            }
+        }
         if (a_bytes && b_bytes) {
             if (a.op == L_DIRECT && b.op == L_DIRECT) {
                 ItemDesc it{};

@@ -346,3 +346,21 @@ def test_f64_to_f32_rounding_ties_and_range_edges():
         run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, ct, cfg)
         run_pair(synth.MIXED_F, fields, ct, {"kind": "aos"}, cfg)
         run_pair(synth.MIXED_F, fields, f32, {"kind": "soa_mb"}, cfg)
+
+
+BYTES_REC = [("a", "u8"), ("b", "i16"), ("c", "f32"), ("d", "f64"), ("e", "u64"), ("f", "u16")]
+
+
+@pytest.mark.parametrize("cfg", SHAPES, ids=lambda c: f"t{c['tile_records']}x{c['threads']}")
+@pytest.mark.parametrize("inner", [{"kind": "soa_mb"}, {"kind": "aos"}, {"kind": "aosoa", "lanes": 8},
+                                   {"kind": "aosoa", "lanes": 64}, {"kind": "soa_sb"}], ids=str)
+def test_bytesplit_planes_many_tiles(inner, cfg):
+    # 2-, 4- and 8-byte leaves to byte planes and back through 4 x 4 byte
+    # transposes; 1-byte leaves stay plain moves; a ragged last tile
+    n = 100000 + 45
+    fields = synth.uniform_fields(BYTES_REC, n, 12)
+    bs = {"kind": "bytesplit", "inner": inner}
+    run_pair(BYTES_REC, fields, {"kind": "soa_mb"}, bs, cfg)
+    run_pair(BYTES_REC, fields, {"kind": "aos"}, bs, cfg)
+    run_pair(BYTES_REC, fields, bs, {"kind": "soa_mb"}, cfg)
+    run_pair(BYTES_REC, fields, bs, {"kind": "aosoa", "lanes": 16}, cfg)
