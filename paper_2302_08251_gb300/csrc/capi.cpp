@@ -46,7 +46,9 @@ llgb_status cuda_fail(cudaError_t e, const char* what)
 
 struct DeviceInfo {
     int sms = 0;
-    int max_smem = 0;
+    int max_smem = 0;       // dynamic shared memory one CTA may opt into
+    int smem_per_sm = 0;    // shared memory of an SM
+    int reserved_smem = 0;  // shared memory the system reserves per CTA
 };
 
 DeviceInfo device_info()
@@ -60,8 +62,21 @@ DeviceInfo device_info()
     if (cache[dev].sms == 0) {
         cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&cache[dev].max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&cache[dev].smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&cache[dev].reserved_smem, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     }
     return cache[dev];
+}
+
+// `ctas` CTAs of `smem` dynamic shared memory each are resident on one SM
+// together (without a device: the limits of this GPU family).
+bool smem_fits(size_t smem, int ctas)
+{
+    const DeviceInfo dev = device_info();
+    const size_t per_cta = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
+    const size_t per_sm = dev.smem_per_sm > 0 ? (size_t)dev.smem_per_sm : 233472;
+    const size_t reserved = dev.max_smem > 0 ? (size_t)dev.reserved_smem : 1024;
+    return smem <= per_cta && (size_t)ctas * (smem + reserved) <= per_sm;
 }
 
 bool same_record(const ViewPlan& a, const ViewPlan& b) { return a.types == b.types; }
@@ -115,15 +130,16 @@ bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config
     return true;
 }
 
-// The library's default launch shape for a pair: 2 CTAs of 256 threads per
-// SM; byte-move jobs (gather programs) take ~12 KB images and 4 source
-// stages, value jobs ~24 KB images and 2 source stages (from launch-shape
-// sweeps on GB300).
+// Default launch shape (from launch-shape sweeps on GB300).  Gather jobs (byte permutations) run 256-thread
+// CTAs, two per SM, on ~12 KB tiles (a thread's gather program covers at
+// most a fixed number of destination words).  Other jobs run one 512-thread
+// CTA per SM with two source and two destination stages of the largest
+// tile that fits (at most 4096 records): per-tile costs are then spread over
+// the most records.  Small views keep at least two tiles per CTA.
 llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
-    const size_t smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
     const uint32_t q = tile_quantum(src->plan, dst->plan);
     if (q == 0) return fail(LLGB_ERR_UNSUPPORTED, "AoSoA lane counts give no usable tile size");
     std::vector<void*> none_s(src->plan.blob_sizes.size(), nullptr), none_d(dst->plan.blob_sizes.size(), nullptr);
@@ -133,25 +149,34 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
         return fail(LLGB_ERR_UNSUPPORTED, why);
     const bool gather = probe.gather != 0;
     llgb_launch_config c{};
-    c.threads = 256;
-    c.ctas_per_sm = 2;
-    c.src_stages = gather ? 4 : 2;
-    c.dst_stages = 3;
     double sb = 0, db = 0;
     uint32_t cb = 0;
     bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
-    const double per_rec = std::max(std::max(sb, db), 1.0);
-    uint64_t tile = (uint64_t)((gather ? 12288.0 : 24576.0) / per_rec) / q * q;
+    uint64_t tile;
+    if (gather) {
+        c.threads = 256;
+        c.ctas_per_sm = 2;
+        c.src_stages = 4;
+        c.dst_stages = 3;
+        tile = (uint64_t)(12288.0 / std::max(std::max(sb, db), 1.0)) / q * q;
+    } else {
+        c.threads = 512;
+        c.ctas_per_sm = 1;
+        c.src_stages = 2;
+        c.dst_stages = 2;
+        const double budget = 227.0 * 1024 - (double)copy_shared_header_bytes() - 64.0;
+        tile = (uint64_t)(budget / (2.0 * (std::max(sb, 1.0) + std::max(db, 1.0)))) / q * q;
+        tile = std::min<uint64_t>(tile, 4096 / q * q);
+    }
     if (tile < q) tile = q;
-    // Small views: keep at least two tiles per SM where the records allow.
     const uint64_t n = src->plan.n;
-    const uint64_t want = (n + 2ull * sms - 1) / (2ull * sms);
+    const uint64_t want = (n + 2ull * sms * c.ctas_per_sm - 1) / (2ull * sms * c.ctas_per_sm);
     const uint64_t small = std::max<uint64_t>(q, (want + q - 1) / q * q);
     tile = std::min(tile, small);
     for (;;) {
         if (plan_job(src->plan, none_s, dst->plan, none_d, (uint32_t)tile, &probe, &why) != LLGB_OK)
             return fail(LLGB_ERR_UNSUPPORTED, why);
-        if (smem_needed(probe, c) * c.ctas_per_sm <= smem_cap) break;
+        if (smem_fits(smem_needed(probe, c), c.ctas_per_sm)) break;
         if (c.src_stages > 2) {
             --c.src_stages;
             continue;
@@ -205,7 +230,7 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     if (st != LLGB_OK) return fail(st, why);
     const DeviceInfo dev = device_info();
     const size_t smem = smem_needed(args.job, c);
-    if (dev.max_smem > 0 && smem * (size_t)c.ctas_per_sm > (size_t)dev.max_smem + 1024 * (c.ctas_per_sm - 1))
+    if (!smem_fits(smem, c.ctas_per_sm))
         return fail(LLGB_ERR_INVALID_ARG, "launch config needs more shared memory than an SM has");
     args.table = nullptr;
     args.tile_start = nullptr;
@@ -258,6 +283,8 @@ void internal_device_limits(int* sms, size_t* smem_cap)
     *smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
 }
 
+bool internal_smem_fits(size_t smem, int ctas) { return smem_fits(smem, ctas); }
+
 }  // namespace llgb
 
 // A batch: every job planned once, grouped by kernel mode; each group is one
@@ -305,7 +332,6 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
-    const size_t smem_cap = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
     cudaGetDevice(&b->device);
     llgb_batch::Group groups[3];
     groups[0].mode = 0;
@@ -345,18 +371,18 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         }
         if (total > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
         g.starts.push_back((uint32_t)total);
-        g.threads = 256;
         int ctas = 2;
-        uint16_t ns = g.mode != 0 ? 4 : 2, nd = 3;
+        uint16_t ns = g.mode != 0 ? 4 : 2, nd = g.mode != 0 ? 3 : 2;
         auto need = [&]() {
             return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
         };
-        while (need() * ctas > smem_cap && (ns > 2 || nd > 2 || ctas > 1)) {
+        while (!smem_fits(need(), ctas) && (ns > 2 || nd > 2 || ctas > 1)) {
             if (ns > 2) --ns;
             else if (nd > 2) --nd;
             else ctas = 1;
         }
-        if (need() > smem_cap) return fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
+        if (!smem_fits(need(), 1)) return fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
+        g.threads = ctas == 1 ? 512 : 256;  // one CTA per SM: a full-size one
         g.smem = need();
         g.grid = (int)std::min<uint64_t>(total, (uint64_t)sms * ctas);
         memset(&g.args, 0, sizeof g.args);
@@ -664,7 +690,7 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
         bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
         const double per_rec = std::max(std::max(sb, db), 1.0);
         std::vector<llgb_launch_config> cands{base};
-        for (double target : {6144.0, 12288.0, 24576.0, 49152.0})
+        for (double target : {6144.0, 12288.0, 24576.0, 49152.0, 73728.0})
             for (int threads : {256, 512})
                 for (int ns : {2, 4})
                     for (int nd : {2, 3}) {

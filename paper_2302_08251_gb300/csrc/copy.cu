@@ -630,15 +630,16 @@ __device__ __forceinline__ uint32_t chunk_word(uint32_t lo, uint32_t hi, uint32_
     const uint32_t lo0 = __shfl_sync(0xFFFFFFFFu, lo, l0);
     const uint32_t hi0 = __shfl_sync(0xFFFFFFFFu, hi, l0);
     uint32_t word = (uint32_t)((((uint64_t)hi0 << 32) | lo0) >> K.rsh[m]);
-    if (!MANY) {
+    if constexpr (!MANY) {
         const uint32_t lo1 = __shfl_sync(0xFFFFFFFFu, lo, (l0 + 1u) & 31u);
         return word | shl_c(lo1, K.t1[m]);
+    } else {
+        for (uint32_t j = 1; j < K.jmax[m]; ++j) {
+            const uint32_t v = __shfl_sync(0xFFFFFFFFu, lo, (l0 + j) & 31u);
+            word |= j < K.nterm[m] ? shl_c(v, j * C - K.rsh[m]) : 0u;
+        }
+        return word;
     }
-    for (uint32_t j = 1; j < K.jmax[m]; ++j) {
-        const uint32_t v = __shfl_sync(0xFFFFFFFFu, lo, (l0 + j) & 31u);
-        word |= j < K.nterm[m] ? shl_c(v, j * C - K.rsh[m]) : 0u;
-    }
-    return word;
 }
 
 // The item fields a conversion needs, held in registers for a whole loop.

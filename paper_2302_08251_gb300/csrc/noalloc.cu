@@ -25,6 +25,7 @@ llgb_status internal_fail(llgb_status status, const char* message);
 llgb_status internal_plan_pair(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads);
 bool internal_empty(const llgb_view* v);
 void internal_device_limits(int* sms, size_t* smem_cap);
+bool internal_smem_fits(size_t smem, int ctas);
 size_t copy_shared_header_bytes();
 }  // namespace llgb
 
@@ -121,6 +122,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
     struct Launch {
         CopyArgs args;
         int grid;
+        int threads;
         size_t smem;
     };
     static thread_local Launch launch[kModes];
@@ -140,16 +142,17 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
         if (total > 0xFFFFFFFFull) return internal_fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
         staging.starts[g][count[g]] = (uint32_t)total;
         int ctas = 2;
-        uint16_t ns = g != 0 ? 4 : 2, nd = 3;
+        uint16_t ns = g != 0 ? 4 : 2, nd = g != 0 ? 3 : 2;
         auto need = [&]() {
             return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
         };
-        while (need() * ctas > smem_cap && (ns > 2 || nd > 2 || ctas > 1)) {
+        while (!internal_smem_fits(need(), ctas) && (ns > 2 || nd > 2 || ctas > 1)) {
             if (ns > 2) --ns;
             else if (nd > 2) --nd;
             else ctas = 1;
         }
-        if (need() > smem_cap) return internal_fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
+        if (!internal_smem_fits(need(), 1)) return internal_fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
+        launch[g].threads = ctas == 1 ? 512 : 256;
         CopyArgs& a = launch[g].args;
         memset(&a, 0, sizeof a);
         a.table = reinterpret_cast<const JobDesc*>(scratch) + first;
@@ -177,7 +180,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
     for (int g = 0; g < kModes; ++g) {
         if (launch[g].grid == 0) continue;
         const int mode = g == 0 ? 0 : (g == 1 ? 2 : 4);
-        e = launch_copy(launch[g].args, mode, launch[g].grid, 256, launch[g].smem, s);
+        e = launch_copy(launch[g].args, mode, launch[g].grid, launch[g].threads, launch[g].smem, s);
         if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     }
     return LLGB_OK;
