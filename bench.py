@@ -132,7 +132,8 @@ class ClockSampler:
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+             "clocks.mem,clocks.max.mem,temperature.gpu")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -163,7 +164,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], None, set()
+        sm, mem, temp, smax, mmax, reasons = [], [], [], None, None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
@@ -177,7 +178,15 @@ class ClockSampler:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(nm)
+            try:
+                mem.append(float(parts[9]))
+                mmax = float(parts[10])
+                temp.append(float(parts[11]))
+            except (IndexError, ValueError):
+                pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "mem_mhz": statistics.median(mem) if mem else None, "mem_max_mhz": mmax,
+                "gpu_temp_c": statistics.median(temp) if temp else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 

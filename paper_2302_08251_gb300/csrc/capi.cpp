@@ -104,8 +104,8 @@ int job_mode(const JobDesc& J, int threads)
         words = 0;
         for (int q = 0; q < J.dst.nsegs; ++q) words += ((J.dst.segs[q].tile_bytes + 15u) & ~15u) / 4u;
     }
-    // warp 0 of every CTA is the TMA producer; the rest run the programs
-    if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)(threads - 32)) mode = 0;
+    // the producer warps of every CTA issue TMA copies; the rest run the programs
+    if (words > (uint64_t)gather_words_per_thread(mode) * (uint64_t)(threads - 32 * (int)producer_warps(mode))) mode = 0;
     return mode;
 }
 
@@ -176,6 +176,11 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
     for (;;) {
         if (plan_job(src->plan, none_s, dst->plan, none_d, (uint32_t)tile, &probe, &why) != LLGB_OK)
             return fail(LLGB_ERR_UNSUPPORTED, why);
+        // a gather job keeps its tile within what the CTA's programs cover
+        if (gather && tile > q && job_mode(probe, c.threads) == 0) {
+            tile -= q;
+            continue;
+        }
         if (smem_fits(smem_needed(probe, c), c.ctas_per_sm)) break;
         if (c.src_stages > 2) {
             --c.src_stages;

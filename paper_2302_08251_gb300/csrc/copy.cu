@@ -4,18 +4,25 @@
 //
 // One persistent kernel serves every mapping pair and, through a descriptor
 // table, many views per launch.  Each CTA walks its share of tiles with one
-// producer warp and several consumer warps, synchronised by mbarriers:
+// load warp, one store warp and several consumer warps, synchronised by
+// mbarriers:
 //
-//   1. the producer brings the source runs of a tile into a shared-memory
+//   1. the load warp brings the source runs of a tile into a shared-memory
 //      image with 1-D TMA bulk copies (cp.async.bulk + mbarrier transaction
 //      counts), `src_stages` tiles ahead of the consumers;
 //   2. the consumers convert the tile into a destination image: jobs made of
 //      byte moves run per-thread gather programs (PRMT); other jobs run their
 //      items (a leaf moved byte for byte, or a value loaded, converted and
-//      stored) one record per thread, and bit-stream destinations gather the
-//      codes that overlap each 32-bit output word;
-//   3. the producer writes the destination runs back with bulk stores
-//      (cp.async.bulk ... bulk_group) as soon as the consumers release them.
+//      stored), each warp over its fixed share of the tile, in loops
+//      specialised for the common cases (V consecutive records per lane,
+//      stream words assembled with warp shuffles, byte planes by 4 x 4
+//      byte transposes);
+//   3. the store warp writes the destination runs back with bulk stores
+//      (cp.async.bulk ... bulk_group) as soon as the consumers release them,
+//      and hands each destination stage back once its store has read it.
+//
+// Value kernels have a load warp and a store warp; gather kernels, whose
+// consumers need every warp, one warp that does both.
 //
 // The last tile of a view, and views whose runs are not 16-byte aligned, use
 // plain coalesced loads and stores instead of TMA.  Every wait on an mbarrier
@@ -146,14 +153,30 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // ------------------------------------------------------- image access --
 
-// Warp 0 of a CTA is the TMA producer; the other warps are consumers, and
-// every per-tile loop below is strided over the consumer threads only.
-__device__ __forceinline__ uint32_t ctid() { return threadIdx.x - 32u; }
-__device__ __forceinline__ uint32_t cnum() { return blockDim.x - 32u; }
+// The head of a CTA's dynamic shared memory; the stage images follow it.
+struct __align__(16) CopyShared {
+    uint64_t full[8];    // source stage s holds its tile (TMA transaction count)
+    uint64_t empty[8];   // consumers are done reading source stage s
+    uint64_t dfull[4];   // consumers have written destination stage d
+    uint64_t dempty[4];  // the store of destination stage d has read it
+    int abort;
+    uint32_t cons_base;  // first consumer thread: 32 x the producer warps
+    int pad[2];
+    JobDesc job;         // the consumers' copy of the current job
+};
+
+extern __shared__ __align__(128) uint8_t g_smem[];
+
+// The first warps of a CTA issue the TMA loads and stores (producer_warps
+// of the kernel mode); the other warps are consumers, and every per-tile
+// loop below is strided over them only.
+__device__ __forceinline__ uint32_t cons_base() { return reinterpret_cast<const CopyShared*>(g_smem)->cons_base; }
+__device__ __forceinline__ uint32_t ctid() { return threadIdx.x - cons_base(); }
+__device__ __forceinline__ uint32_t cnum() { return blockDim.x - cons_base(); }
 
 __device__ __forceinline__ void consumer_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"r"(blockDim.x - 32u) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(cnum()) : "memory");
 }
 
 __device__ __forceinline__ uint64_t ld_elem(const uint8_t* p, int size, int align)
@@ -1195,9 +1218,10 @@ __device__ __forceinline__ void run_gather(const GatherProgram<FORM>& G, const u
             e[k] = s[G.idx23[k] >> 16];
         }
     }
+    const uint32_t c0 = ctid(), cn = cnum();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const uint32_t w = FORM == 4 ? (G.dstw[k / 2] >> (16 * (k & 1))) & 0xFFFFu : ctid() + k * cnum();
+        const uint32_t w = FORM == 4 ? (G.dstw[k / 2] >> (16 * (k & 1))) & 0xFFFFu : c0 + k * cn;
         if (FORM == 4 ? w != 0xFFFFu : w < nwords) {
             if (FORM == 2) {
                 d[w] = __byte_perm(a[k], b[k], G.sel01[k] & 0xFFFFu);
@@ -1213,20 +1237,21 @@ __device__ __forceinline__ void run_gather(const GatherProgram<FORM>& G, const u
 // Plain copy of `bytes` between global and shared memory by the consumers.
 __device__ void plain_copy(uint8_t* dst, const uint8_t* src, uint32_t bytes)
 {
+    const uint32_t c0 = ctid(), cn = cnum();
     const uintptr_t both = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src);
     uint32_t done = 0;
     if ((both & 15u) == 0) {
         const uint32_t n16 = bytes / 16u;
-        for (uint32_t k = ctid(); k < n16; k += cnum())
+        for (uint32_t k = c0; k < n16; k += cn)
             reinterpret_cast<uint4*>(dst)[k] = reinterpret_cast<const uint4*>(src)[k];
         done = n16 * 16u;
     } else if ((both & 3u) == 0) {
         const uint32_t n4 = bytes / 4u;
-        for (uint32_t k = ctid(); k < n4; k += cnum())
+        for (uint32_t k = c0; k < n4; k += cn)
             reinterpret_cast<uint32_t*>(dst)[k] = reinterpret_cast<const uint32_t*>(src)[k];
         done = n4 * 4u;
     }
-    for (uint32_t k = done + ctid(); k < bytes; k += cnum()) dst[k] = src[k];
+    for (uint32_t k = done + c0; k < bytes; k += cn) dst[k] = src[k];
 }
 
 // Global tile index of this CTA's k-th tile (see CopyArgs::chunk).
@@ -1246,16 +1271,6 @@ __device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g)
     }
     return lo;
 }
-
-struct __align__(16) CopyShared {
-    uint64_t full[8];    // source stage s holds its tile (TMA transaction count)
-    uint64_t empty[8];   // consumers are done reading source stage s
-    uint64_t dfull[4];   // consumers have written destination stage d
-    uint64_t dempty[4];  // the store of destination stage d has read it
-    int abort;
-    int pad[3];
-    JobDesc job;         // the consumers' copy of the current job
-};
 
 __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
@@ -1293,13 +1308,30 @@ __device__ __forceinline__ void lane_runs_load(LaneRuns& L, const SideDesc& S, c
     L.total = __reduce_add_sync(0xFFFFFFFFu, L.bytes);
 }
 
-// Producer warp: TMA loads `src_stages` tiles ahead, bulk stores as the
-// consumers finish each destination stage.
+// After an abort the consumers may have left: wait (bounded) for the loads
+// of the last src_stages issued tiles, which may still be landing in shared
+// memory, before the CTA exits.
+__device__ void drain_loads(const CopyArgs& a, CopyShared& H, uint32_t first, uint32_t issued)
+{
+    const uint32_t NS = a.src_stages;
+    for (uint32_t k = issued > NS ? issued - NS : 0u; k < issued; ++k) {
+        const uint32_t g = tile_index(a, first, k);
+        const uint32_t j = job_of(a, g);
+        const JobDesc* J = a.table ? a.table + j : &a.job;
+        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        if (t < J->nfull && J->src.bulk_ok) (void)mbar_wait_bounded(&H.full[k % NS], (k / NS) & 1u);
+    }
+}
+
+// One warp for both directions (gather kernels, whose consumers are cheap
+// per byte and need every warp): TMA loads `src_stages` tiles ahead, bulk
+// stores as the consumers finish each destination stage.
 __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint8_t* dst_stage, uint32_t first,
                          uint32_t count)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
+    volatile int* abort_flag = &H.abort;
     LaneRuns in, out;
     uint32_t issued = 0;  // tiles whose loads have been issued: 0 .. issued-1
 
@@ -1324,7 +1356,7 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     for (uint32_t k = 0; k < count; ++k) {
         const uint32_t d = k % ND;
         if (!mbar_wait_bounded(&H.dfull[d], (k / ND) & 1u)) {
-            H.abort = 1;
+            *abort_flag = 1;
             break;
         }
         const uint32_t g = tile_index(a, first, k);
@@ -1337,34 +1369,101 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
         if (t < out.nfull && out.bulk && (int)lane < out.nsegs)
             bulk_store(const_cast<uint8_t*>(out.gptr) + (uint64_t)t * out.bytes,
                        dst_stage + d * a.dst_stage_bytes + out.sbase, out.bytes);
-        // One group per tile (empty for tiles the consumers stored): keeping
-        // ND-1 groups in flight, the group of tile k-ND+1 has read its stage,
-        // which tile k+1 reuses.
-        bulk_commit();
-        bulk_wait_read((int)ND - 1);
-        __syncwarp();
-        if (lane == 0 && k + 1 >= ND) mbar_arrive(&H.dempty[(k + 1) % ND]);
+        bulk_commit();  // one group per tile (empty for tiles the consumers stored)
+        // The consumers released tile k's source stage before they arrived
+        // on dfull: its next load goes out before any wait on the stores.
         if (k + NS < count) {
             if (!mbar_wait_bounded(&H.empty[k % NS], (k / NS) & 1u)) {
-                H.abort = 1;
+                *abort_flag = 1;
                 break;
             }
             issue_load(k + NS);
         }
-        if (*reinterpret_cast<volatile int*>(&H.abort)) break;
+        // Release stage d for tile k+ND as soon as tile k's store has read it.
+        bulk_wait_read(0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&H.dempty[d]);
+        if (*abort_flag) break;
     }
     bulk_wait_all();
-    if (*reinterpret_cast<volatile int*>(&H.abort)) {
-        // the consumers may have left: wait (bounded) for the loads of the
-        // last NS issued tiles, which may still be landing in shared memory
-        for (uint32_t k = issued > NS ? issued - NS : 0u; k < issued; ++k) {
-            const uint32_t g = tile_index(a, first, k);
-            const uint32_t j = job_of(a, g);
+    if (*abort_flag) drain_loads(a, H, first, issued);
+}
+
+// Load warp: brings tile k into source stage k % NS with TMA bulk loads as
+// soon as the consumers have released the stage's previous tile.
+__device__ void load_producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint32_t first, uint32_t count)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t NS = a.src_stages;
+    volatile int* abort_flag = &H.abort;
+    LaneRuns in;
+    uint32_t issued = 0;        // tiles whose loads have been issued: 0 .. issued-1
+    uint32_t s = 0, round = 0;  // k % NS, (k / NS) & 1
+    for (uint32_t k = 0; k < count; ++k) {
+        if (k >= NS && !mbar_wait_bounded(&H.empty[s], round ^ 1u)) {
+            *abort_flag = 1;
+            break;
+        }
+        const uint32_t g = tile_index(a, first, k);
+        const uint32_t j = job_of(a, g);
+        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        if ((int)j != in.job) {
             const JobDesc* J = a.table ? a.table + j : &a.job;
-            const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
-            if (t < J->nfull && J->src.bulk_ok) (void)mbar_wait_bounded(&H.full[k % NS], (k / NS) & 1u);
+            lane_runs_load(in, J->src, J, (int)j, lane);
+        }
+        issued = k + 1u;
+        if (t < in.nfull && in.bulk) {
+            if (lane == 0) mbar_arrive_expect_tx(&H.full[s], in.total);
+            if ((int)lane < in.nsegs)
+                bulk_load(src_stage + s * a.src_stage_bytes + in.sbase, in.gptr + (uint64_t)t * in.bytes, in.bytes,
+                          &H.full[s]);
+        }
+        if (*abort_flag) break;
+        if (++s == NS) {
+            s = 0;
+            round ^= 1u;
         }
     }
+    if (*abort_flag) drain_loads(a, H, first, issued);
+}
+
+// Store warp: writes destination stage k % ND back with TMA bulk stores once
+// the consumers have finished tile k, and releases the stage for tile k+ND
+// as soon as the store has read it.  Loads and stores are issued by two
+// warps so that neither waits behind the other's (serial) issue.
+__device__ void store_producer(const CopyArgs& a, CopyShared& H, uint8_t* dst_stage, uint32_t first, uint32_t count)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t ND = a.dst_stages;
+    volatile int* abort_flag = &H.abort;
+    LaneRuns out;
+    uint32_t d = 0, round = 0;  // k % ND, (k / ND) & 1
+    for (uint32_t k = 0; k < count; ++k) {
+        if (!mbar_wait_bounded(&H.dfull[d], round)) {
+            *abort_flag = 1;
+            break;
+        }
+        const uint32_t g = tile_index(a, first, k);
+        const uint32_t j = job_of(a, g);
+        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        if ((int)j != out.job) {
+            const JobDesc* J = a.table ? a.table + j : &a.job;
+            lane_runs_load(out, J->dst, J, (int)j, lane);
+        }
+        if (t < out.nfull && out.bulk && (int)lane < out.nsegs)
+            bulk_store(const_cast<uint8_t*>(out.gptr) + (uint64_t)t * out.bytes,
+                       dst_stage + d * a.dst_stage_bytes + out.sbase, out.bytes);
+        bulk_commit();  // one group per tile (empty for tiles the consumers stored)
+        bulk_wait_read(0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&H.dempty[d]);
+        if (*abort_flag) break;
+        if (++d == ND) {
+            d = 0;
+            round ^= 1u;
+        }
+    }
+    bulk_wait_all();
 }
 
 // Bounded wait that gives up at once after an abort (the phase may never
@@ -1500,9 +1599,8 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
 template <int MODE>
 __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ CopyArgs a)
 {
-    extern __shared__ __align__(128) uint8_t smem[];
-    CopyShared& H = *reinterpret_cast<CopyShared*>(smem);
-    uint8_t* src_stage = smem + align16(sizeof(CopyShared));
+    CopyShared& H = *reinterpret_cast<CopyShared*>(g_smem);
+    uint8_t* src_stage = g_smem + align16(sizeof(CopyShared));
     uint8_t* dst_stage = src_stage + a.src_stages * a.src_stage_bytes;
     uint8_t* codes = dst_stage + a.dst_stages * a.dst_stage_bytes;
 
@@ -1519,7 +1617,8 @@ __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ Co
         count = (a.total_tiles - first + G - 1u) / G;
     }
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
-    const uint32_t consumer_warps = blockDim.x / 32u - 1u;
+    constexpr uint32_t P = producer_warps(MODE);
+    const uint32_t consumer_warps = blockDim.x / 32u - P;
 
     // The last 16 bytes of every source stage hold zeros: gather programs
     // read destination padding from there.
@@ -1537,10 +1636,15 @@ __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ Co
         }
         fence_barrier_init();
         H.abort = 0;
+        H.cons_base = 32u * P;
     }
     __syncthreads();
 
-    if (threadIdx.x < 32u)
+    if (P == 2 && threadIdx.x < 32u)
+        load_producer(a, H, src_stage, first, count);
+    else if (P == 2 && threadIdx.x < 64u)
+        store_producer(a, H, dst_stage, first, count);
+    else if (P == 1 && threadIdx.x < 32u)
         producer(a, H, src_stage, dst_stage, first, count);
     else
         consumer<MODE>(a, H, src_stage, dst_stage, codes, first, count);

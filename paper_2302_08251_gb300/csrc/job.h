@@ -22,6 +22,9 @@ constexpr int kMaxPacks = 16;   // bit-stream destination leaves
 constexpr int kImageSlack = 16; // bytes after every run in an image
 constexpr int kMaxZeros = 32;   // destination byte ranges owned by no leaf
 constexpr int kStageZeroBytes = 16;  // zero block at the end of every source stage
+// Warps of a CTA that issue its TMA copies: value kernels (mode 0) have a
+// load warp and a store warp; gather kernels one warp for both.
+constexpr unsigned producer_warps(int mode) { return mode == 0 ? 2u : 1u; }
 
 // One contiguous run of a tile in a blob.  For tile t it covers
 // [gbase + t * tile_bytes, + tile_bytes) (the last tile: tail_bytes) and
