@@ -249,6 +249,8 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
     const int mode = job_mode(args.job, c.threads);
+    if (c.threads / 32 <= (int)producer_warps(mode))
+        return fail(LLGB_ERR_INVALID_ARG, "launch config leaves no consumer warp");
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
     return LLGB_OK;

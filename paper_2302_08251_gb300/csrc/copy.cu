@@ -388,7 +388,8 @@ __device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc&
 
 enum FastLoad { FL_AFF = 0, FL_AL = 1, FL_BITS = 2 };
 enum FastStore { FS_AFF = 0, FS_AL = 1, FS_BITS = 2 };
-enum FastConv { FC_INT = 0, FC_D2F = 1, FC_F2D = 2, FC_RT = 3 };
+// FC_SAME: one float format on both sides (only a NaN changes: it is quieted).
+enum FastConv { FC_INT = 0, FC_D2F = 1, FC_F2D = 2, FC_RT = 3, FC_SAME = 4 };
 
 template <int SZ>
 __device__ __forceinline__ uint64_t ld_sz(const uint8_t* p)
@@ -670,6 +671,7 @@ struct ConvRegs {
     uint32_t wa, wb;
     bool is_signed;
     int se, sm, de, dm;  // stored -> logical (on load) or logical -> stored
+    uint64_t absmask, inf, quiet;  // FC_SAME: |x| above the INF code is a NaN
 };
 
 template <int CV, bool ON_LOAD, typename T>
@@ -687,6 +689,7 @@ __device__ __forceinline__ T fast_convert(T x, const ConvRegs& c)
     }
     if (CV == FC_D2F) return (T)f64_to_f32_bits((uint64_t)x);
     if (CV == FC_F2D) return (T)f32_to_f64_bits((uint32_t)x);
+    if (CV == FC_SAME) return (x & (T)c.absmask) > (T)c.inf ? (x | (T)c.quiet) : x;
     return (T)fconv((uint64_t)x, c.se, c.sm, c.de, c.dm);
 }
 
@@ -715,6 +718,13 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
     cr.sm = CONV_ON_LOAD ? I.s_m : I.l_m;
     cr.de = CONV_ON_LOAD ? I.l_e : I.d_e;
     cr.dm = CONV_ON_LOAD ? I.l_m : I.d_m;
+    if constexpr (CV == FC_SAME) {
+        cr.absmask = low_bits64(cr.se + cr.sm);
+        cr.inf = low_bits64(cr.se) << cr.sm;
+        cr.quiet = 1ull << (cr.sm > 0 ? cr.sm - 1 : 0);
+    } else {
+        cr.absmask = cr.inf = cr.quiet = 0;
+    }
     const uint32_t wa = cr.wa, wb = cr.wb;
     const uint32_t sa = smem_addr(simg), da = smem_addr(dimg);
 
@@ -940,6 +950,13 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
         return true;
 #define LLGB_FAST1(K, LK, SK, SZL, SZS, CV, OL, V) \
     case K: LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, V, false); return true;
+// stream and leaf of one float format: no rounding, only NaN quieting
+#define LLGB_FAST_SAME(K, LK, SK, SZL, SZS, OL, V)                    \
+    case K:                                                          \
+        if (OL ? (I.s_e == I.l_e && I.s_m == I.l_m) : (I.l_e == I.d_e && I.l_m == I.d_m)) \
+            LLGB_FAST_V(LK, SK, SZL, SZS, FC_SAME, OL, V, false);        \
+        else LLGB_FAST_V(LK, SK, SZL, SZS, FC_RT, OL, V, false);        \
+        return true;
     const uint32_t width = I.sop == S_BITS_INT || I.sop == S_BITS_FLOAT ? I.d_bits : I.s_bits;
     switch (I.fast) {
         LLGB_FAST(FK_PACK_INT32, FL_AFF, FS_BITS, 4, 4, FC_INT, false)
@@ -950,8 +967,8 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
         LLGB_FAST(FK_UNPACK_BITS_TO4, FL_BITS, FS_AFF, 4, 4, FC_RT, true)
         LLGB_FAST1(FK_PACK_D_F32, FL_AFF, FS_AL, 8, 4, FC_D2F, false, 2)
         LLGB_FAST1(FK_PACK_AL32_FROM8, FL_AFF, FS_AL, 8, 4, FC_RT, false, 2)
-        LLGB_FAST1(FK_PACK_AL32_FROM4, FL_AFF, FS_AL, 4, 4, FC_RT, false, 4)
-        LLGB_FAST1(FK_PACK_AL64_FROM8, FL_AFF, FS_AL, 8, 8, FC_RT, false, 2)
+        LLGB_FAST_SAME(FK_PACK_AL32_FROM4, FL_AFF, FS_AL, 4, 4, false, 4)
+        LLGB_FAST_SAME(FK_PACK_AL64_FROM8, FL_AFF, FS_AL, 8, 8, false, 2)
         LLGB_FAST1(FK_PACK_AL64_FROM4, FL_AFF, FS_AL, 4, 8, FC_RT, false, 4)
         LLGB_FAST1(FK_PACK_AL16_FROM8, FL_AFF, FS_AL, 8, 2, FC_RT, false, 2)
         LLGB_FAST1(FK_PACK_AL16_FROM4, FL_AFF, FS_AL, 4, 2, FC_RT, false, 4)
@@ -959,8 +976,8 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
         LLGB_FAST1(FK_PACK_AL8_FROM4, FL_AFF, FS_AL, 4, 1, FC_RT, false, 4)
         LLGB_FAST1(FK_UNPACK_F32_D, FL_AL, FS_AFF, 4, 8, FC_F2D, true, 2)
         LLGB_FAST1(FK_UNPACK_AL32_TO8, FL_AL, FS_AFF, 4, 8, FC_RT, true, 2)
-        LLGB_FAST1(FK_UNPACK_AL32_TO4, FL_AL, FS_AFF, 4, 4, FC_RT, true, 4)
-        LLGB_FAST1(FK_UNPACK_AL64_TO8, FL_AL, FS_AFF, 8, 8, FC_RT, true, 2)
+        LLGB_FAST_SAME(FK_UNPACK_AL32_TO4, FL_AL, FS_AFF, 4, 4, true, 4)
+        LLGB_FAST_SAME(FK_UNPACK_AL64_TO8, FL_AL, FS_AFF, 8, 8, true, 2)
         LLGB_FAST1(FK_UNPACK_AL64_TO4, FL_AL, FS_AFF, 8, 4, FC_RT, true, 4)
         LLGB_FAST1(FK_UNPACK_AL16_TO8, FL_AL, FS_AFF, 2, 8, FC_RT, true, 2)
         LLGB_FAST1(FK_UNPACK_AL16_TO4, FL_AL, FS_AFF, 2, 4, FC_RT, true, 4)
@@ -976,6 +993,7 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
     case FK_JOIN8: split_loop<8, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
     default: return false;
     }
+#undef LLGB_FAST_SAME
 #undef LLGB_FAST1
 #undef LLGB_FAST
 #undef LLGB_FAST_V

@@ -81,18 +81,21 @@ __device__ __noinline__ uint64_t fconv_general(uint64_t x, int se, int sm, int d
 // f64 -> f32 with integer operations (the FP64 pipe of this GPU is narrow).
 // Results in the normal f32 range are rounded here: the top 23 mantissa bits
 // are kept, the 29 below decide the rounding, and a carry out of the
-// mantissa moves into the exponent (all-ones exponent: INF).  Zero, NaN, INF
-// and subnormal results go through fconv_general.
+// mantissa moves into the exponent (rebiased from 1023 to 127; a carry into
+// the all-ones exponent gives INF).  Zero, NaN, INF and subnormal results go
+// through fconv_general.
 __device__ __forceinline__ uint32_t f64_to_f32_bits(uint64_t x)
 {
     const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
     const uint32_t s = hi & 0x80000000u;
     const uint32_t e = (hi >> 20) & 0x7FFu;
     if (e - 897u < 254u) {  // f32 exponent 1 .. 254 before rounding
-        uint32_t r = ((e - 896u) << 23) | (__funnelshift_l(lo, hi, 3) & 0x7FFFFFu);
-        const uint32_t rest = lo & 0x1FFFFFFFu;
-        r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
-        return s | r;
+        // Drop the low 29 bits rounding to nearest, ties to even: adding
+        // 2^28 - 1 plus the lowest kept bit carries into bit 29 exactly when
+        // the dropped part exceeds half, or equals it with an odd kept part.
+        // A carry out of the mantissa moves into the exponent.
+        const uint64_t a = (((uint64_t)(hi & 0x7FFFFFFFu) << 32) | lo) + 0x0FFFFFFFull + ((lo >> 29) & 1u);
+        return s | ((uint32_t)(a >> 29) - (896u << 23));
     }
     if (e > 1150u && e != 0x7FFu) return s | 0x7F800000u;   // beyond the f32 range: INF
     if ((hi & 0x7FFFFFFFu) == 0u && lo == 0u) return s;      // signed zero
