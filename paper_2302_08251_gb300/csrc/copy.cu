@@ -389,7 +389,7 @@ __device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc&
 enum FastLoad { FL_AFF = 0, FL_AL = 1, FL_BITS = 2 };
 enum FastStore { FS_AFF = 0, FS_AL = 1, FS_BITS = 2 };
 // FC_SAME: one float format on both sides (only a NaN changes: it is quieted).
-enum FastConv { FC_INT = 0, FC_D2F = 1, FC_F2D = 2, FC_RT = 3, FC_SAME = 4 };
+enum FastConv { FC_INT = 0, FC_D2F = 1, FC_F2D = 2, FC_RT = 3, FC_SAME = 4, FC_NONE = 5 };
 
 template <int SZ>
 __device__ __forceinline__ uint64_t ld_sz(const uint8_t* p)
@@ -687,6 +687,7 @@ __device__ __forceinline__ T fast_convert(T x, const ConvRegs& c)
         }
         return x;  // the pack masks codes to their width
     }
+    if (CV == FC_NONE) return x;
     if (CV == FC_D2F) return (T)f64_to_f32_bits((uint64_t)x);
     if (CV == FC_F2D) return (T)f32_to_f64_bits((uint32_t)x);
     if (CV == FC_SAME) return (x & (T)c.absmask) > (T)c.inf ? (x | (T)c.quiet) : x;
@@ -985,6 +986,10 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
         LLGB_FAST1(FK_UNPACK_AL8_TO4, FL_AL, FS_AFF, 1, 4, FC_RT, true, 4)
         LLGB_FAST1(FK_CT_D_F32, FL_AFF, FS_AFF, 8, 4, FC_D2F, false, 2)
         LLGB_FAST1(FK_CT_F32_D, FL_AFF, FS_AFF, 4, 8, FC_F2D, true, 2)
+        LLGB_FAST1(FK_MOVE1, FL_AFF, FS_AFF, 1, 1, FC_NONE, false, 4)
+        LLGB_FAST1(FK_MOVE2, FL_AFF, FS_AFF, 2, 2, FC_NONE, false, 4)
+        LLGB_FAST1(FK_MOVE4, FL_AFF, FS_AFF, 4, 4, FC_NONE, false, 4)
+        LLGB_FAST1(FK_MOVE8, FL_AFF, FS_AFF, 8, 8, FC_NONE, false, 2)
     case FK_SPLIT2: split_loop<2, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
     case FK_SPLIT4: split_loop<4, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
     case FK_SPLIT8: split_loop<8, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
@@ -1015,6 +1020,7 @@ __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc&
                                                uint8_t* dimg, uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
     const Span sp{128u * q0 + (threadIdx.x & 31u), 128u * q1, 32u};
+    if (I.op == ITEM_MOVE && I.fast != FK_GENERIC && run_fast(I, J, simg, dimg, q0, q1, nvalid)) return;
     if (I.op == ITEM_MOVE) {
         const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
         const LeafRegs B = leaf_regs(J.dst.leaves[I.dst_leaf]);

@@ -119,7 +119,11 @@ enum FastKind : uint8_t {
     FK_SPLIT8,
     FK_JOIN2,             // byte planes -> 2 / 4 / 8-byte leaf (Bytesplit load)
     FK_JOIN4,
-    FK_JOIN8
+    FK_JOIN8,
+    FK_MOVE1,             // whole 1 / 2 / 4 / 8-byte element between affine leaves
+    FK_MOVE2,             // (MOVE items of jobs that also convert values)
+    FK_MOVE4,
+    FK_MOVE8
 };
 
 // A bit-stream destination leaf.  Specialised loops store whole words of the

@@ -653,6 +653,14 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
                 it.dst_leaf = (uint8_t)b.first;
                 it.gran = (uint8_t)std::min<int>(
                     size, std::min<int>(job->src.leaves[a.first].align, job->dst.leaves[b.first].align));
+                // whole aligned elements: the specialised loops (V = 4, 2 for 8 bytes)
+                const int V = size == 8 ? 2 : 4;
+                if (it.gran == size && (size == 1 || size == 2 || size == 4 || size == 8) &&
+                    job->src.leaves[a.first].kind == LEAF_AFFINE && job->dst.leaves[b.first].kind == LEAF_AFFINE &&
+                    affine_for(job->src.leaves[a.first], V) && affine_for(job->dst.leaves[b.first], V)) {
+                    it.fast = (uint8_t)(FK_MOVE1 + (size == 1 ? 0 : size == 2 ? 1 : size == 4 ? 2 : 3));
+                    it.vpl = (uint8_t)V;
+                }
                 if (!add(it)) return too_many();
             } else {
                 for (int j = 0; j < size; ++j) {

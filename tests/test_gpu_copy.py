@@ -364,3 +364,17 @@ def test_bytesplit_planes_many_tiles(inner, cfg):
     run_pair(BYTES_REC, fields, {"kind": "aos"}, bs, cfg)
     run_pair(BYTES_REC, fields, bs, {"kind": "soa_mb"}, cfg)
     run_pair(BYTES_REC, fields, bs, {"kind": "aosoa", "lanes": 16}, cfg)
+
+
+@pytest.mark.parametrize("cfg", SHAPES, ids=lambda c: f"t{c['tile_records']}x{c['threads']}")
+@pytest.mark.parametrize("inner", [{"kind": "soa_mb"}, {"kind": "aos"}, {"kind": "aosoa", "lanes": 8},
+                                   {"kind": "aosoa", "lanes": 64}], ids=str)
+def test_moves_beside_conversions(inner, cfg):
+    # one f64 leaf changes type, so the job converts values and its 1-, 2-,
+    # 4- and 8-byte leaves run as whole-element moves in the value loops
+    n = 120000 + 13
+    fields = synth.uniform_fields(BYTES_REC, n, 21)
+    ct = {"kind": "changetype", "ct": [("f64", "f32")], "inner": inner}
+    for other in ({"kind": "soa_mb"}, {"kind": "aos"}, {"kind": "aosoa", "lanes": 32}):
+        run_pair(BYTES_REC, fields, other, ct, cfg)
+        run_pair(BYTES_REC, fields, ct, other, cfg)
