@@ -204,6 +204,34 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
     return LLGB_OK;
 }
 
+// A job of a batch, planned at its launch shape's tile -- capped so that its
+// source and destination images each stay within a quarter of a CTA's
+// shared memory: a batch kernel sizes every stage for the largest image of
+// its group, and two source plus two destination stages of any mix of such
+// jobs then fit.
+llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads)
+{
+    llgb_launch_config c{};
+    if (!tuned_config(src, dst, &c)) {
+        const llgb_status st = default_config(src, dst, &c);
+        if (st != LLGB_OK) return st;
+    }
+    const DeviceInfo dev = device_info();
+    const size_t per_cta = dev.max_smem > 0 ? (size_t)dev.max_smem : 232448;
+    const size_t side_cap = (per_cta - copy_shared_header_bytes()) / 4 - kStageZeroBytes;
+    const uint32_t q = tile_quantum(src->plan, dst->plan);
+    uint32_t tile = (uint32_t)c.tile_records;
+    std::string why;
+    for (;;) {
+        const llgb_status st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, tile, job, &why);
+        if (st != LLGB_OK) return fail(st, why);
+        if ((job->src.img_bytes <= side_cap && job->dst.img_bytes <= side_cap) || tile <= q) break;
+        tile -= q;
+    }
+    *mode = job_mode(*job, threads);
+    return LLGB_OK;
+}
+
 llgb_status check_pair(const llgb_view* src, const llgb_view* dst)
 {
     if (!src || !dst) return fail(LLGB_ERR_INVALID_ARG, "null view");
@@ -269,16 +297,7 @@ llgb_status internal_plan_pair(const llgb_view* src, const llgb_view* dst, JobDe
 {
     llgb_status st = check_pair(src, dst);
     if (st != LLGB_OK) return st;
-    llgb_launch_config c{};
-    if (!tuned_config(src, dst, &c)) {
-        st = default_config(src, dst, &c);
-        if (st != LLGB_OK) return st;
-    }
-    std::string why;
-    st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, (uint32_t)c.tile_records, job, &why);
-    if (st != LLGB_OK) return fail(st, why);
-    *mode = job_mode(*job, threads);
-    return LLGB_OK;
+    return plan_batch_job(src, dst, job, mode, threads);
 }
 
 bool internal_empty(const llgb_view* v) { return v->plan.n == 0; }
@@ -348,16 +367,10 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         llgb_status st = check_pair(src[k], dst[k]);
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
         if (src[k]->plan.n == 0) continue;
-        llgb_launch_config c{};
-        if (!tuned_config(src[k], dst[k], &c)) {
-            st = default_config(src[k], dst[k], &c);
-            if (st != LLGB_OK) return st;
-        }
         JobDesc J;
-        std::string why;
-        st = plan_job(src[k]->plan, src[k]->ptrs, dst[k]->plan, dst[k]->ptrs, (uint32_t)c.tile_records, &J, &why);
-        if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + why);
-        const int mode = job_mode(J, 256);
+        int mode = 0;
+        st = plan_batch_job(src[k], dst[k], &J, &mode, 256);
+        if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
         llgb_batch::Group& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : 2)];
         g.starts.push_back((uint32_t)b->tiles);
         g.jobs.push_back(J);

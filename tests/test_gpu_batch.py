@@ -132,3 +132,28 @@ def test_autotune_picks_a_valid_shape_and_copies_stay_exact():
     for g_blob, e_blob in zip(dst.blob_bytes(), dst_o.blobs):
         assert np.array_equal(g_blob, e_blob)
     llgb.llgb_autotune_clear()
+
+
+def test_batch_of_large_jobs_with_opposite_image_sizes():
+    # a pack (large source image, small destination) and an unpack (small
+    # source, large destination) at full-size tiles share one batch kernel,
+    # whose stages take the largest image of each side
+    n = 1 << 21
+    fields = synth.int6(n, 12, 31)
+    jobs = [({"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12}),
+            ({"kind": "bitpack_int", "bits": 12}, {"kind": "aos"}),
+            ({"kind": "aos"}, {"kind": "aosoa", "lanes": 32})]
+    pairs, expect = [], []
+    for sm, dm in jobs:
+        src_o = oracle_view(synth.INT6, sm, fields)
+        dst_o = oracle.OracleView(synth.INT6, dm, n)
+        src_o.copy_to(dst_o)
+        pairs.append((device_view_of(src_o), empty_device_view(synth.INT6, dm, n)))
+        expect.append(dst_o)
+    batch = llgb.Batch(pairs)
+    batch.launch(use_graph=True)
+    sync_and_check_status()
+    for (_, d), dst_o in zip(pairs, expect):
+        for g_blob, e_blob in zip(d.blob_bytes(), dst_o.blobs):
+            assert np.array_equal(g_blob, e_blob)
+    batch.close()

@@ -90,3 +90,26 @@ def test_noalloc_batch_rejects_more_than_64_pairs():
     assert err.value.status == llgb.ERR_INVALID_ARG
     llgb.llgb_batch_copy_noalloc(views[:64])
     sync_and_check_status()
+
+
+def test_noalloc_batch_of_large_jobs_with_opposite_image_sizes():
+    # full-size tiles: a pack (large source image) and an unpack (large
+    # destination image) in one call share each kernel's stage sizes
+    ensure_library()
+    n = 1 << 21
+    fields = synth.int6(n, 12, 5)
+    jobs = [({"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12}),
+            ({"kind": "bitpack_int", "bits": 12}, {"kind": "aos"})]
+    views, ref = [], []
+    for sm, dm in jobs:
+        src = device_view_of(oracle_view(synth.INT6, sm, fields))
+        r = empty_device_view(synth.INT6, dm, n, fill=0x11)
+        llgb.llgb_copy(src, r)
+        views.append((src, empty_device_view(synth.INT6, dm, n, fill=0x22)))
+        ref.append(r)
+    sync_and_check_status()
+    llgb.llgb_batch_copy_noalloc(views)
+    sync_and_check_status()
+    for (_, d), r in zip(views, ref):
+        for got, exp in zip(d.blob_bytes(), r.blob_bytes()):
+            assert np.array_equal(got, exp)
