@@ -130,12 +130,15 @@ bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config
     return true;
 }
 
-// Default launch shape (from launch-shape sweeps on GB300).  Gather jobs (byte permutations) run 256-thread
-// CTAs, two per SM, on ~12 KB tiles (a thread's gather program covers at
-// most a fixed number of destination words).  Other jobs run one 512-thread
-// CTA per SM with two source and two destination stages of the largest
-// tile that fits (at most 4096 records): per-tile costs are then spread over
-// the most records.  Small views keep at least two tiles per CTA.
+// Default launch shape (from launch-shape sweeps on GB300).
+//  * Gather jobs (byte permutations) run two 256-thread CTAs per SM on
+//    ~12 KB tiles (a thread's gather program covers at most a fixed number
+//    of destination words) -- or, with four or more destination runs per
+//    tile, one 512-thread CTA on ~30 KB tiles.
+//  * Other jobs run one 512-thread CTA per SM with two source and two
+//    destination stages of the largest tile that fits (at most 4096
+//    records): per-tile costs are then spread over the most records.
+// Small views keep at least two tiles per CTA.
 llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
 {
     const DeviceInfo dev = device_info();
@@ -153,7 +156,16 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
     uint32_t cb = 0;
     bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
     uint64_t tile;
-    if (gather) {
+    if (gather && probe.dst.nsegs >= 4) {
+        // many destination runs (SoA-like destinations): one 512-thread CTA
+        // per SM, whose programs cover ~30 KB tiles, issues a quarter as many
+        // bulk stores per byte as two 256-thread CTAs on 12 KB tiles
+        c.threads = 512;
+        c.ctas_per_sm = 1;
+        c.src_stages = 4;
+        c.dst_stages = 2;
+        tile = (uint64_t)(30720.0 / std::max(std::max(sb, db), 1.0)) / q * q;
+    } else if (gather) {
         c.threads = 256;
         c.ctas_per_sm = 2;
         c.src_stages = 4;
