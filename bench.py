@@ -18,7 +18,8 @@ value = algorithmic bytes (every source blob byte read + every destination
 blob byte written) of the step / device time of the step, in GB/s.  Every
 input is larger than L2, so no flush is needed between steps.  The n-body
 consumer (65,536 particles) is timed in its own loop and reported under
-"nbody".
+"nbody"; "sweeps" holds the other bit widths and float formats of the
+bit-packing rows and the small 65,536-particle case (warm and cold L2).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs the whole per-GPU workload on its own GPU (weak
@@ -235,14 +236,29 @@ def dist_env():
 
 # ---------------------------------------------------------- CPU oracle --
 
-def oracle_sample(seconds_budget=12.0, seed=1):
+def oracle_copy_threaded(src, dst, threads):
+    """The oracle's copy over record ranges on `threads` host threads (ctypes
+    releases the GIL).  Ranges start at multiples of 1024 records, so no two
+    threads share a bit-stream word or an AoSoA block."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = src.n
+    step = max(1024, (n + threads - 1) // threads // 1024 * 1024)
+    ranges = [(i, min(n, i + step)) for i in range(0, n, step)]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda r: src.copy_to(dst, r[0], r[1]), ranges))
+
+
+def oracle_sample(seconds_budget=12.0, seed=1, threads=None):
     """Time the oracle copy on a bounded sample of every row: the first
-    records of each workload, sized so the whole sample takes ~10-30 s."""
+    records of each workload, sized so the whole single-thread sample takes
+    ~10-30 s; the same sample is then timed on all host cores.  Returns
+    (single-thread GB/s, all-cores GB/s, threads, sample, single-thread s)."""
     import numpy as np
     import oracle
     from paper_2302_08251_gb300 import synth
     oracle.build()
-    total_bytes, total_time, parts = 0, 0.0, []
+    threads = threads or os.cpu_count() or 1
+    total_bytes, total_time, total_mt, parts = 0, 0.0, 0.0, []
     per_row = seconds_budget / len(rows_spec())
     for name, cfg, src_map, dst_map in rows_spec():
         m = 4096
@@ -267,11 +283,17 @@ def oracle_sample(seconds_budget=12.0, seed=1):
             if dt * 4 > per_row or m >= cfg["n"]:
                 break
             m *= 4
+        dst_mt = oracle.OracleView(rec, dst_map, m)
+        t0 = time.perf_counter()
+        oracle_copy_threaded(src, dst_mt, threads)
+        dt_mt = time.perf_counter() - t0
         nbytes = sum(src.blob_sizes) + sum(dst.blob_sizes)
         total_bytes += nbytes
         total_time += dt
+        total_mt += dt_mt
         parts.append(f"{name}: {m} records")
-    return total_bytes / total_time / 1e9, "; ".join(parts), total_time
+    return (total_bytes / total_time / 1e9, total_bytes / total_mt / 1e9, threads, "; ".join(parts),
+            total_time)
 
 
 def run_reference(args):
@@ -280,10 +302,11 @@ def run_reference(args):
         return 0
     for _ in range(args.warmup):
         oracle_sample(seconds_budget=2.0)
-    vals, times, sample = [], [], ""
+    vals, singles, times, sample, threads = [], [], [], "", 1
     for _ in range(args.steps):
-        v, sample, t = oracle_sample(seconds_budget=8.0)
+        v1, v, threads, sample, t = oracle_sample(seconds_budget=8.0)
         vals.append(v)
+        singles.append(v1)
         times.append(t)
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
@@ -292,9 +315,10 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bytes/int/f64",
             "data": "synthetic (seeded)",
             "config": {"workload": "llama re-layout suite (C1 b=12, C2 E8M23/bytesplit/"
-                                   "changetype, C3 512^3 pairs), bounded sample", "parallelism": "none"},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                                   "changetype, C3 512^3 pairs), bounded sample",
+                       "parallelism": "host threads over record ranges"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "single_thread_value": statistics.median(singles), "sample": sample},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -366,7 +390,7 @@ def run_gpu(args):
     nbody = nbody_bench(device, args) if rank == 0 and not args.no_extras else None
     # end to end through host buffers
     e2e = e2e_bench(wl, stream, args) if rank == 0 and not args.no_extras else None
-    batched = serving = None
+    batched = serving = sweeps = None
     step_bytes = wl.bytes
     if rank == 0 and not args.no_extras:
         del wl
@@ -374,6 +398,8 @@ def run_gpu(args):
         batched = batched_bench(device, args)
         torch.cuda.empty_cache()
         serving = serving_bench(device, args)
+        torch.cuda.empty_cache()
+        sweeps = sweeps_bench(device)
 
     if rank == 0:
         line = {
@@ -398,11 +424,13 @@ def run_gpu(args):
             "nbody": nbody,
             "batched": batched,
             "serving": serving,
+            "sweeps": sweeps,
         }
         if not args.no_cpu_baseline and not args.no_extras:
-            v, sample, _ = oracle_sample()
-            line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1,
-                                    "kind": "oracle", "sample": sample}
+            v1, v, threads, sample, _ = oracle_sample()
+            line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": threads,
+                                    "kind": "oracle", "single_thread_value": round(v1, 4),
+                                    "sample": sample}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -441,6 +469,100 @@ def nbody_bench(device, args):
             "roofline": {"bound": "alu", "achieved": best, "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(best / peak, 4),
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz (nominal)"}}
+
+
+def time_copy(src, dst, reps=10):
+    """Median device ms of `reps` single copies (CUDA events per launch)."""
+    import torch
+    from paper_2302_08251_gb300 import llgb
+    llgb.llgb_copy(src, dst)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        llgb.llgb_copy(src, dst)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def sweeps_bench(device):
+    """The configurations the suite's step holds one point of: BitpackInt at
+    b in {1, 3, 7, 12, 17, 31} (2^26 INT6 records), BitpackFloat at the 12
+    (E, M) formats (2^25 MIXED_F records), both from / to SoA multi-blob;
+    and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose
+    3.7 MB fit L2: its latency is reported warm and with L2 flushed."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, synth
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    out = {}
+    soa = {"kind": "soa_mb"}
+
+    def entry(nbytes, ms):
+        g = nbytes / (ms * 1e-3) / 1e9
+        return {"ms": round(ms, 4), "GB/s": round(g, 1), "frac": round(g / hbm, 4)}
+
+    n = 1 << 26
+    rec = llgb.Record(synth.INT6)
+    c1 = {}
+    for b in (1, 3, 7, 12, 17, 31):
+        fields = synth.device_fields("int6", n, 11 + b, device=device, bits=b)
+        base = llgb.View(rec, soa, (n,), blobs=[f.view(torch.uint8) for f in fields])
+        packed = llgb.View(rec, {"kind": "bitpack_int", "bits": b}, (n,))
+        plain = llgb.View(rec, soa, (n,))
+        nbytes = (sum(llgb.blob_sizes(rec, soa, (n,))) +
+                  sum(llgb.blob_sizes(rec, {"kind": "bitpack_int", "bits": b}, (n,))))
+        c1[f"b={b}"] = {"pack": entry(nbytes, time_copy(base, packed)), "unpack": entry(nbytes, time_copy(packed, plain))}
+        del fields, base, packed, plain
+        torch.cuda.empty_cache()
+    out["C1 BitpackInt, 2^26 INT6 records, SoA-MB <-> BitpackIntSoA"] = c1
+
+    n = 1 << 25
+    rec = llgb.Record(synth.MIXED_F)
+    fields = synth.device_fields("mixed_f", n, 17, device=device)
+    base = llgb.View(rec, soa, (n,), blobs=[f.contiguous().view(torch.uint8) for f in fields])
+    plain = llgb.View(rec, soa, (n,))
+    c2 = {}
+    for e in (5, 8, 11):
+        for m in (2, 10, 23, 52):
+            mp = {"kind": "bitpack_float", "exp": e, "man": m}
+            packed = llgb.View(rec, mp, (n,))
+            nbytes = sum(llgb.blob_sizes(rec, soa, (n,))) + sum(llgb.blob_sizes(rec, mp, (n,)))
+            c2[f"E{e}M{m}"] = {"pack": entry(nbytes, time_copy(base, packed)),
+                               "unpack": entry(nbytes, time_copy(packed, plain))}
+            del packed
+            torch.cuda.empty_cache()
+    out["C2 BitpackFloat, 2^25 MIXED_F records, SoA-MB <-> BitpackFloatSoA"] = c2
+    del fields, base, plain
+    torch.cuda.empty_cache()
+
+    n = 65536
+    rec = llgb.Record(synth.PARTICLE)
+    fields = synth.device_fields("particle", n, 3, device=device)
+    base = llgb.View(rec, soa, (n,), blobs=[f.view(torch.uint8) for f in fields])
+    aos = llgb.View(rec, {"kind": "aos"}, (n,))
+    llgb.llgb_copy(base, aos)
+    dst = llgb.View(rec, soa, (n,))
+    nbytes = 2 * 28 * n
+    warm = time_copy(aos, dst, reps=50)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2
+    cold = []
+    for _ in range(30):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        llgb.llgb_copy(aos, dst)
+        b.record()
+        b.synchronize()
+        cold.append(a.elapsed_time(b))
+    cold_ms = statistics.median(cold)
+    out["C0 AoS -> SoA-MB, 65,536 particles (3.7 MB)"] = {
+        "warm_us": round(warm * 1e3, 2), "cold_l2_us": round(cold_ms * 1e3, 2),
+        "cold_l2_GB/s": round(nbytes / (cold_ms * 1e-3) / 1e9, 1)}
+    return out
 
 
 def batched_bench(device, args, target_bytes=24 * (1 << 30)):

@@ -672,6 +672,7 @@ struct ConvRegs {
     bool is_signed;
     int se, sm, de, dm;  // stored -> logical (on load) or logical -> stored
     uint64_t absmask, inf, quiet;  // FC_SAME: |x| above the INF code is a NaN
+    FmtConv fc;                    // FC_RT
 };
 
 template <int CV, bool ON_LOAD, typename T>
@@ -691,7 +692,7 @@ __device__ __forceinline__ T fast_convert(T x, const ConvRegs& c)
     if (CV == FC_D2F) return (T)f64_to_f32_bits((uint64_t)x);
     if (CV == FC_F2D) return (T)f32_to_f64_bits((uint32_t)x);
     if (CV == FC_SAME) return (x & (T)c.absmask) > (T)c.inf ? (x | (T)c.quiet) : x;
-    return (T)fconv((uint64_t)x, c.se, c.sm, c.de, c.dm);
+    return (T)fmt_convert((uint64_t)x, c.fc);
 }
 
 // LK / SK: how the source / destination element is reached; SZL / SZS:
@@ -726,6 +727,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
     } else {
         cr.absmask = cr.inf = cr.quiet = 0;
     }
+    if constexpr (CV == FC_RT) cr.fc = fmt_conv(cr.se, cr.sm, cr.de, cr.dm);
     const uint32_t wa = cr.wa, wb = cr.wb;
     const uint32_t sa = smem_addr(simg), da = smem_addr(dimg);
 

@@ -113,6 +113,66 @@ __device__ __forceinline__ uint64_t f32_to_f64_bits(uint32_t u)
     return fconv_general(u, 8, 23, 11, 52);  // subnormal, INF, NaN
 }
 
+// Conversion between two fixed formats, set up once per loop.  A value whose
+// result is a normal number takes a few integer operations: the exponent is
+// rebiased by adding a constant to the magnitude bits, and a narrowing drops
+// k = sm - dm mantissa bits rounding to nearest, ties to even (add 2^(k-1) - 1
+// plus the lowest kept bit; a carry moves into the exponent, up to INF).
+// Zeros and finite values beyond the target's range are handled here too;
+// NaN, INF, subnormal inputs and subnormal results go to fconv_general.
+struct FmtConv {
+    int se, sm, de, dm;
+    int k;              // sm - dm: bits dropped (> 0) or appended (< 0)
+    uint64_t absmask;   // magnitude bits of the source
+    uint64_t in_inf;    // source INF code: magnitudes at or above are INF / NaN
+    uint64_t lo, span;  // magnitudes in [lo, lo + span) give normal results
+    uint64_t ovf;       // finite magnitudes at or above overflow to INF (~0: none)
+    uint64_t half;      // narrowing: 2^(k-1) - 1
+    uint64_t rebias;    // added to the shifted magnitude: (d_bias - s_bias) << dm, mod 2^64
+    uint64_t inf_out;   // target INF code
+};
+
+__host__ __device__ inline FmtConv fmt_conv(int se, int sm, int de, int dm)
+{
+    FmtConv c;
+    c.se = se;
+    c.sm = sm;
+    c.de = de;
+    c.dm = dm;
+    c.k = sm - dm;
+    c.absmask = (se + sm >= 64) ? ~0ull : ((1ull << (se + sm)) - 1ull);
+    c.in_inf = ((1ull << se) - 1ull) << sm;
+    const int64_t s_bias = (1ll << (se - 1)) - 1, d_bias = (1ll << (de - 1)) - 1;
+    // source exponents e whose result exponent e - s_bias + d_bias is 1 .. 2^de - 2
+    const int64_t e_lo = s_bias - d_bias + 1, e_hi = (1ll << de) - 2 + s_bias - d_bias;
+    const int64_t a = e_lo > 1 ? e_lo : 1, b = e_hi < (1ll << se) - 2 ? e_hi : (1ll << se) - 2;
+    if (b >= a) {
+        c.lo = (uint64_t)a << sm;
+        c.span = ((uint64_t)(b + 1) << sm) - c.lo;
+    } else {
+        c.lo = 0;
+        c.span = 0;
+    }
+    c.ovf = e_hi + 1 <= (1ll << se) - 2 ? ((uint64_t)(e_hi + 1) << sm) : ~0ull;
+    c.half = c.k > 0 ? (1ull << (c.k - 1)) - 1ull : 0ull;
+    c.rebias = (uint64_t)((d_bias - s_bias) * (int64_t)(1ll << dm));
+    c.inf_out = ((1ull << de) - 1ull) << dm;
+    return c;
+}
+
+__device__ __forceinline__ uint64_t fmt_convert(uint64_t x, const FmtConv& c)
+{
+    const uint64_t a = x & c.absmask;
+    const uint64_t sign = (x >> (c.se + c.sm) & 1ull) << (c.de + c.dm);
+    if (a - c.lo < c.span) {
+        const uint64_t r = c.k > 0 ? ((a + c.half + ((a >> c.k) & 1ull)) >> c.k) : (a << -c.k);
+        return sign | (r + c.rebias);
+    }
+    if (a == 0) return sign;
+    if (a >= c.ovf && a < c.in_inf) return sign | c.inf_out;
+    return fconv_general(x, c.se, c.sm, c.de, c.dm);
+}
+
 __device__ __forceinline__ bool is_nan_bits(uint64_t x, int e, int m)
 {
     const uint64_t all = (1ull << e) - 1ull;
