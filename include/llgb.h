@@ -211,14 +211,23 @@ llgb_status llgb_copy(const llgb_view* src, llgb_view* dst, void* stream);
 llgb_status llgb_pack(const llgb_view* plain, llgb_view* packed, void* stream);
 llgb_status llgb_unpack(const llgb_view* packed, llgb_view* plain, void* stream);
 
+/* Which tile engine a copy runs.  Both move the same bytes.
+ *   AUTO:   the library's choice -- gather programs for jobs made only of
+ *           byte moves with more than two tiles per CTA, else value loops;
+ *   VALUE:  the value loops (per-item loops over each warp's share);
+ *   GATHER: per-thread gather programs where the job allows (only byte
+ *           moves, within the CTA's program capacity), else value loops. */
+typedef enum llgb_engine { LLGB_ENGINE_AUTO = 0, LLGB_ENGINE_VALUE = 1, LLGB_ENGINE_GATHER = 2 } llgb_engine;
+
 /* Launch shape of the copy kernel.  All zero = the library's choice. */
 typedef struct llgb_launch_config {
     int32_t tile_records;   /* records per tile; multiple of 128 and of lanes */
     int32_t src_stages;     /* source tiles in flight per CTA (1..8)           */
     int32_t dst_stages;     /* destination tiles in flight per CTA (1..4)      */
-    int32_t threads;        /* threads per CTA: 128, 256, 512 or 1024          */
+    int32_t threads;        /* threads per CTA: 128, 256 or 512                */
     int32_t ctas_per_sm;    /* resident CTAs per SM (1..8)                      */
-    int32_t reserved[3];    /* must be 0                                       */
+    int32_t engine;         /* llgb_engine                                     */
+    int32_t reserved[2];    /* must be 0                                       */
 } llgb_launch_config;
 
 /* The launch shape llgb_copy uses for this pair (after autotuning, if any). */

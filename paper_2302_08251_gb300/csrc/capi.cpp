@@ -220,7 +220,11 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
 // source and destination images each stay within a quarter of a CTA's
 // shared memory: a batch kernel sizes every stage for the largest image of
 // its group, and two source plus two destination stages of any mix of such
-// jobs then fit.
+// jobs then fit.  Jobs of at most kFewTiles tiles run the value loops: every
+// CTA that meets a gather job builds its program, which short jobs do not
+// repay.
+constexpr uint32_t kFewTiles = 4;
+
 llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads)
 {
     llgb_launch_config c{};
@@ -240,7 +244,7 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
         if ((job->src.img_bytes <= side_cap && job->dst.img_bytes <= side_cap) || tile <= q) break;
         tile -= q;
     }
-    *mode = job_mode(*job, threads);
+    *mode = job->ntiles <= kFewTiles ? 0 : job_mode(*job, threads);
     return LLGB_OK;
 }
 
@@ -288,7 +292,11 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     args.dst_stages = (uint16_t)c.dst_stages;
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
-    const int mode = job_mode(args.job, c.threads);
+    int mode = c.engine == LLGB_ENGINE_VALUE ? 0 : job_mode(args.job, c.threads);
+    // a gather program is built once per job by every CTA: with at most two
+    // tiles per CTA that costs more than it saves, and the value loops
+    // (whole-element moves) need no program
+    if (c.engine == LLGB_ENGINE_AUTO && mode != 0 && args.total_tiles <= 2u * (uint32_t)grid) mode = 0;
     if (c.threads / 32 <= (int)producer_warps(mode))
         return fail(LLGB_ERR_INVALID_ARG, "launch config leaves no consumer warp");
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
@@ -566,8 +574,10 @@ llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst, const llgb_laun
 {
     try {
         if (!cfg) return fail(LLGB_ERR_INVALID_ARG, "null launch config");
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 2; ++k)
             if (cfg->reserved[k]) return fail(LLGB_ERR_INVALID_ARG, "reserved fields must be 0");
+        if (cfg->engine < LLGB_ENGINE_AUTO || cfg->engine > LLGB_ENGINE_GATHER)
+            return fail(LLGB_ERR_INVALID_ARG, "unknown engine");
         if (cfg->tile_records <= 0) return fail(LLGB_ERR_INVALID_ARG, "tile_records must be positive");
         return run_copy(src, dst, cfg, stream);
     } catch (...) {

@@ -64,10 +64,14 @@ MappingDesc._fields_ = [
 ]
 
 
+ENGINES = {"auto": 0, "value": 1, "gather": 2}
+
+
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("tile_records", ctypes.c_int32), ("src_stages", ctypes.c_int32),
                 ("dst_stages", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("ctas_per_sm", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k in
@@ -293,9 +297,11 @@ def llgb_copy_config(src: View, dst: View) -> dict:
 
 
 def llgb_copy_with(src: View, dst: View, cfg: dict, stream=None) -> None:
+    """llgb_copy with an explicit launch shape; cfg may also hold
+    "engine": "auto" | "value" | "gather"."""
     c = LaunchConfig()
     for k, v in cfg.items():
-        setattr(c, k, int(v))
+        setattr(c, k, ENGINES[v] if k == "engine" else int(v))
     check(lib().llgb_copy_with(src.handle, dst.handle, ctypes.byref(c), _stream_ptr(stream)))
 
 

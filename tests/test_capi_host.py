@@ -202,3 +202,23 @@ def test_default_launch_shape_fits_the_tile_rules():
     assert c.threads in (128, 256, 512, 1024)
     for h in hs:
         L.llgb_view_destroy(h)
+
+
+def test_copy_with_rejects_an_unknown_engine():
+    L = llgb.lib()
+    rec = llgb.Record(synth.PARTICLE)
+    hs = []
+    for mp in ({"kind": "aos"}, {"kind": "soa_mb"}):
+        keep = []
+        e = llgb.extents_desc((1000,))
+        m = llgb.mapping_desc(mp, keep)
+        h = ctypes.c_void_p()
+        llgb.check(L.llgb_view_create(rec.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(h)))
+        hs.append(h)
+    c = llgb.LaunchConfig(tile_records=128, src_stages=2, dst_stages=2, threads=256, ctas_per_sm=1, engine=7)
+    assert L.llgb_copy_with(hs[0], hs[1], ctypes.byref(c), None) == llgb.ERR_INVALID_ARG
+    c.engine = 1
+    c.reserved[1] = 5
+    assert L.llgb_copy_with(hs[0], hs[1], ctypes.byref(c), None) == llgb.ERR_INVALID_ARG
+    for h in hs:
+        L.llgb_view_destroy(h)

@@ -46,17 +46,26 @@ def run_pair(record, fields, src_map, dst_map, cfg=None):
 PAIRS = list(itertools.product(range(len(AFFINE)), repeat=2))
 
 
+ENGINE_SHAPE = {"tile_records": 384, "src_stages": 4, "dst_stages": 3, "threads": 256, "ctas_per_sm": 2}
+
+
+@pytest.mark.parametrize("engine", ["auto", "gather", "value"])
 @pytest.mark.parametrize("pair", PAIRS, ids=lambda p: f"{p[0]}-{p[1]}")
 @pytest.mark.parametrize("name", ["cfd", "padded"])
-def test_affine_pairs(pair, name):
+def test_affine_pairs(pair, name, engine):
+    # both tile engines (gather programs, value loops) on every mapping pair;
+    # "auto" takes the library's shape and engine choice
     rec = RECORDS[name]
-    n = 3001  # several 128-record tiles and a ragged tail
-    run_pair(rec, synth.uniform_fields(rec, n, 7), AFFINE[pair[0]], AFFINE[pair[1]])
+    n = 3001  # several tiles and a ragged tail
+    cfg = None if engine == "auto" else dict(ENGINE_SHAPE, engine=engine)
+    run_pair(rec, synth.uniform_fields(rec, n, 7), AFFINE[pair[0]], AFFINE[pair[1]], cfg)
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 127, 128, 129, 1000, 4096, 65536, 65537])
 def test_particle_aos_to_soa_sizes(n):
     run_pair(synth.PARTICLE, synth.particles(n, n), {"kind": "aos"}, {"kind": "soa_mb"})
+    run_pair(synth.PARTICLE, synth.particles(n, n), {"kind": "aos"}, {"kind": "soa_mb"},
+             dict(ENGINE_SHAPE, tile_records=128, engine="gather"))
 
 
 @pytest.mark.parametrize("b", [1, 3, 7, 12, 17, 31, 32])
@@ -111,15 +120,19 @@ def test_bitpack_float_to_bitpack_float():
              {"kind": "bitpack_float", "exp": 5, "man": 2})
 
 
+@pytest.mark.parametrize("engine", ["auto", "gather"])
 @pytest.mark.parametrize("inner", [{"kind": "soa_mb"}, {"kind": "aos", "packed": 1},
                                    {"kind": "aosoa", "lanes": 32}, {"kind": "soa_sb"}], ids=str)
-def test_bytesplit(inner):
+def test_bytesplit(inner, engine):
+    # "gather": the byte-move form (one move per byte plane) where a leaf
+    # does not take the transpose loops
     n = 2500
+    cfg = None if engine == "auto" else dict(ENGINE_SHAPE, tile_records=128, engine=engine)
     fields = synth.mixed_f(n, seed=4)
     bs = {"kind": "bytesplit", "inner": inner}
-    run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, bs)
-    run_pair(synth.MIXED_F, fields, bs, {"kind": "aos"})
-    run_pair(synth.CFD, synth.cfd(n, 2), {"kind": "aos"}, bs)
+    run_pair(synth.MIXED_F, fields, {"kind": "soa_mb"}, bs, cfg)
+    run_pair(synth.MIXED_F, fields, bs, {"kind": "aos"}, cfg)
+    run_pair(synth.CFD, synth.cfd(n, 2), {"kind": "aos"}, bs, cfg)
 
 
 @pytest.mark.parametrize("inner", [{"kind": "soa_mb"}, {"kind": "aos"},
@@ -170,13 +183,14 @@ CONFIGS = [
                                   ({"kind": "aosoa", "lanes": 8}, {"kind": "aosoa", "lanes": 32}),
                                   ({"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12})],
                          ids=["aos-soa", "soa-aosoa32", "aosoa8-aosoa32", "pack12"])
-def test_launch_shapes(cfg, maps):
+@pytest.mark.parametrize("engine", ["auto", "gather"])
+def test_launch_shapes(cfg, maps, engine):
     n = 40000 + 77
     if maps[1]["kind"] == "bitpack_int":
         rec, fields = synth.INT6, synth.int6(n, 12, 5)
     else:
         rec, fields = synth.CFD, synth.cfd(n, 5)
-    run_pair(rec, fields, maps[0], maps[1], cfg)
+    run_pair(rec, fields, maps[0], maps[1], dict(cfg, engine=engine))
 
 
 def test_single_blob_with_wide_subarray_alignment_zeroes_the_gaps():
