@@ -102,6 +102,8 @@ def _load():
         lib.orc_convert_n.argtypes = [p, p, u64, i32, i32, i32, i32]
         lib.orc_nbody_step.argtypes = [PM, u64, PB, ctypes.c_double,
                                        ctypes.c_double, u64, u64, p, p]
+        lib.orc_nbody_access_counts.argtypes = [u64, u64, p]
+        lib.orc_nbody_heatmap.argtypes = [PM, u64, u64, u64, p]
         _lib = lib
     return _lib
 
@@ -226,6 +228,26 @@ class OracleView:
                                  float(eps), float(dt), i0, i1,
                                  pos.ctypes.data, vel.ctypes.data)
         return pos, vel
+
+
+def nbody_access_counts(n: int, block: int = 64) -> np.ndarray:
+    """FieldAccessCount of one tiled n-body step (Sec. 4): 7 read counters,
+    then 7 write counters, for the particle record."""
+    out = np.zeros(14, dtype=np.uint64)
+    _load().orc_nbody_access_counts(n, block, out.ctypes.data)
+    return out
+
+
+def nbody_heatmap(mapping: dict, n: int, g: int, block: int = 64) -> np.ndarray:
+    """Heatmap of one tiled n-body step at granularity g bytes (Sec. 4):
+    per-granule access counts, blob after blob."""
+    particle = [(f"leaf{k}", "f32") for k in range(7)]
+    keep: list = []
+    m = _to_c_mapping(mapping, keep)
+    total = sum((s + g - 1) // g for s in blob_sizes(particle, mapping, n))
+    out = np.zeros(max(1, total), dtype=np.uint64)
+    _load().orc_nbody_heatmap(ctypes.byref(m), n, block, g, out.ctypes.data)
+    return out[:total]
 
 
 def blob_sizes(record, mapping: dict, n: int) -> list:

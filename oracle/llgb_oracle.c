@@ -637,3 +637,40 @@ void orc_nbody_step(const orc_mapping* m, uint64_t n, uint8_t* const* blobs,
     free(pos);
     free(mass);
 }
+
+/* ------------------------------------------- access instrumentation -- */
+
+void orc_nbody_access_counts(uint64_t n, uint64_t block, uint64_t* counts)
+{
+    const uint64_t blocks = n == 0 ? 0 : (n + block - 1) / block;
+    for (int k = 0; k < 14; ++k) counts[k] = 0;
+    /* reads: own positions (update), every record's position and mass once
+     * per block (update), positions again (move) */
+    for (int f = 0; f < 3; ++f) counts[f] = n + blocks * n + n;
+    /* velocities: read in the update and in the move */
+    for (int f = 3; f < 6; ++f) counts[f] = 2 * n;
+    counts[6] = blocks * n;
+    /* writes: velocities (update), positions (move) */
+    for (int f = 0; f < 6; ++f) counts[7 + f] = n;
+}
+
+void orc_nbody_heatmap(const orc_mapping* m, uint64_t n, uint64_t block, uint64_t g, uint64_t* heat)
+{
+    static const int32_t types[7] = {ORC_F32, ORC_F32, ORC_F32, ORC_F32,
+                                     ORC_F32, ORC_F32, ORC_F32};
+    uint64_t counts[14], start[8] = {0};
+    orc_nbody_access_counts(n, block, counts);
+    const int32_t nb = orc_blob_count(types, 7, m);
+    for (int32_t b = 0; b < nb; ++b) start[b + 1] = start[b] + (orc_blob_size(types, 7, m, n, b) + g - 1) / g;
+    for (uint64_t k = 0; k < start[nb]; ++k) heat[k] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        for (int32_t f = 0; f < 7; ++f) {
+            uint64_t off = 0;
+            const int b = affine_locate(types, 7, m, n, i, f, &off);
+            if (b < 0) return;
+            const uint64_t acc = counts[f] / n + counts[7 + f] / n; /* per element */
+            for (uint64_t k = off / g; k <= (off + 3) / g; ++k) heat[start[b] + k] += acc;
+        }
+    }
+}
+

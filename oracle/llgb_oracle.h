@@ -126,6 +126,27 @@ void orc_nbody_step(const orc_mapping* m, uint64_t n, uint8_t* const* blobs,
                     double eps, double dt, uint64_t i0, uint64_t i1,
                     double* pos_out, double* vel_out);
 
+/* Access instrumentation (Sec. 4, "Memory access instrumentation"):
+ * FieldAccessCount counts the accesses per record field (reads and writes
+ * apart: 2 counters per field), Heatmap the accesses touching each granule
+ * of g bytes of every blob.  What is counted is the access schedule of the
+ * tiled n-body step the CUDA library runs on the particle record, with
+ * blocks of `block` particles (B = ceil(n / block) blocks) -- one step:
+ *   update: each block reads pos.x/y/z of its own particles once, pos.x/y/z
+ *           and mass of every record once, and reads and writes vel.x/y/z
+ *           of its own particles once;
+ *   move:   every particle's pos and vel are read once and pos written once.
+ * orc_nbody_access_counts writes the 14 field counters of one step (reads of
+ * leaves 0..6, then writes of leaves 0..6). */
+void orc_nbody_access_counts(uint64_t n, uint64_t block, uint64_t* counts);
+
+/* Heatmap of one such step at granularity g: for every record i and leaf f,
+ * the accesses of that element in the step (reads + writes) are added to the
+ * counter of every granule its 4 bytes touch.  Counters of blob b follow
+ * those of blobs 0 .. b-1 (ceil(blob size / g) each).  `heat` is zeroed
+ * first. */
+void orc_nbody_heatmap(const orc_mapping* m, uint64_t n, uint64_t block, uint64_t g, uint64_t* heat);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ the mapping the particles are read through.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2302_08251_gb300 import synth
 from helpers import AFFINE, oracle_view
 
@@ -112,3 +113,78 @@ def test_partial_range_equals_the_slice_of_the_full_step():
     part = v.nbody_step(EPS, DT, 10, 20)
     assert np.array_equal(full[0][10:20], part[0])
     assert np.array_equal(full[1][10:20], part[1])
+
+
+# ---- access instrumentation of the tiled step (Sec. 4: FieldAccessCount,
+# Heatmap): pinned against a direct enumeration of the access events and
+# against what every mapping must agree on ----
+
+def enumerate_accesses(n, block=64):
+    """Every access of one tiled step as (record, leaf, is_write), listed
+    event by event from the schedule: blocks of `block` particles each read
+    their own positions, every record's position and mass, then read and
+    write their velocities; the move reads pos and vel and writes pos."""
+    ev = []
+    for b in range(0, n, block):
+        mine = range(b, min(n, b + block))
+        for i in mine:
+            ev += [(i, f, False) for f in (0, 1, 2)]
+        for j in range(n):
+            ev += [(j, f, False) for f in (0, 1, 2, 6)]
+        for i in mine:
+            ev += [(i, f, False) for f in (3, 4, 5)] + [(i, f, True) for f in (3, 4, 5)]
+    for i in range(n):
+        ev += [(i, f, False) for f in range(6)] + [(i, f, True) for f in (0, 1, 2)]
+    return ev
+
+
+@pytest.mark.parametrize("n", [0, 1, 63, 64, 65, 200])
+def test_access_counts_match_the_enumerated_schedule(n):
+    want = np.zeros(14, dtype=np.uint64)
+    for _, f, w in enumerate_accesses(n):
+        want[f + (7 if w else 0)] += 1
+    assert np.array_equal(oracle.nbody_access_counts(n), want)
+
+
+def element_offset(mapping, n, i, f):
+    """(blob, byte) of leaf f of record i for the particle record, from the
+    mapping formulas (28-byte record of 7 f32 leaves)."""
+    k = mapping["kind"]
+    if k == "aos":
+        return 0, 28 * i + 4 * f
+    if k == "soa_mb":
+        return f, 4 * i
+    if k == "soa_sb":
+        return 0, 4 * n * f + 4 * i
+    L = mapping["lanes"]
+    return 0, (i // L) * 28 * L + 4 * L * f + 4 * (i % L)
+
+
+MAPS = [{"kind": "aos"}, {"kind": "soa_mb"}, {"kind": "soa_sb"}, {"kind": "aosoa", "lanes": 8},
+        {"kind": "aosoa", "lanes": 32}]
+
+
+@pytest.mark.parametrize("mapping", MAPS, ids=lambda m: m["kind"] + str(m.get("lanes", "")))
+@pytest.mark.parametrize("g", [1, 2, 4, 8, 64])
+def test_heatmap_matches_the_enumerated_accesses(mapping, g):
+    n = 70
+    sizes = oracle.blob_sizes(synth.PARTICLE, mapping, n)
+    start = np.cumsum([0] + [(s + g - 1) // g for s in sizes])
+    want = np.zeros(start[-1], dtype=np.uint64)
+    for i, f, _ in enumerate_accesses(n):
+        b, off = element_offset(mapping, n, i, f)
+        for k in range(off // g, (off + 3) // g + 1):
+            want[start[b] + k] += 1
+    got = oracle.nbody_heatmap(mapping, n, g)
+    assert np.array_equal(got, want)
+    # every access of a 4-byte element touches 4 byte counters
+    if g == 1:
+        assert int(got.sum()) == 4 * int(oracle.nbody_access_counts(n).sum())
+
+
+def test_heatmap_per_element_counts_agree_across_mappings():
+    n = 100
+    per = [np.sort(oracle.nbody_heatmap(m, n, 4)[np.nonzero(oracle.nbody_heatmap(m, n, 4))])
+           for m in MAPS]
+    for p in per[1:]:
+        assert np.array_equal(p, per[0])
