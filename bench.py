@@ -465,10 +465,56 @@ def nbody_bench(device, args):
     # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop x clock (2.07 GHz max)
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
     best = max(x["TFLOP/s"] for x in out.values())
-    return {"n": n, "flop_per_interaction": 20, "views": out,
+    instrumented = nbody_instrumentation_bench(device, base, rec, n, args)
+    return {"n": n, "flop_per_interaction": 20, "views": out, "instrumented": instrumented,
             "roofline": {"bound": "alu", "achieved": best, "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(best / peak, 4),
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz (nominal)"}}
+
+
+def nbody_instrumentation_bench(device, base, rec, n, args):
+    """FieldAccessCount / Heatmap (Sec. 4) on the SoA n-body step: step time
+    with each instrumentation against the plain step, and counter memory
+    against the view's bytes."""
+    import torch
+    from paper_2302_08251_gb300 import llgb
+    v = llgb.View(rec, {"kind": "soa_mb"}, (n,))
+    llgb.llgb_copy(base, v)
+    counts = torch.zeros(14, dtype=torch.int64, device=device)
+    heats = {g: torch.zeros(llgb.llgb_heatmap_counters(v, g), dtype=torch.int64, device=device)
+             for g in (1, 64)}
+    variants = {
+        "plain": lambda: llgb.llgb_nbody_step(v, 0.01, 1e-4),
+        "FieldAccessCount, atomic per access": lambda: llgb.llgb_nbody_step_instrumented(
+            v, 0.01, 1e-4, field_counts=counts, count_mode="atomic"),
+        "FieldAccessCount, per-CTA counters": lambda: llgb.llgb_nbody_step_instrumented(
+            v, 0.01, 1e-4, field_counts=counts, count_mode="block"),
+        "Heatmap, 64-byte granules": lambda: llgb.llgb_nbody_step_instrumented(
+            v, 0.01, 1e-4, heat=heats[64], granularity=64),
+        "Heatmap, bytes": lambda: llgb.llgb_nbody_step_instrumented(v, 0.01, 1e-4, heat=heats[1], granularity=1),
+    }
+    out = {}
+    for name, fn in variants.items():
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_step": round(a.elapsed_time(b) / reps, 4)}
+    plain = out["plain"]["ms_per_step"]
+    view_bytes = sum(llgb.blob_sizes(rec, {"kind": "soa_mb"}, (n,)))
+    for name in out:
+        out[name]["slowdown"] = round(out[name]["ms_per_step"] / plain, 3)
+    out["FieldAccessCount, atomic per access"]["counter_bytes"] = 14 * 8
+    out["FieldAccessCount, per-CTA counters"]["counter_bytes"] = 14 * 8
+    for g, key in ((64, "Heatmap, 64-byte granules"), (1, "Heatmap, bytes")):
+        out[key]["counter_bytes"] = heats[g].numel() * 8
+        out[key]["memory_overhead"] = round(heats[g].numel() * 8 / view_bytes, 3)
+    return out
 
 
 def time_copy(src, dst, reps=10):

@@ -311,6 +311,41 @@ llgb_status llgb_autotune_clear(void);
  * kernels).  Errors: INVALID_ARG, UNBOUND, UNSUPPORTED, CUDA. */
 llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream);
 
+/* --------------------------------------------- access instrumentation -- */
+
+/* FieldAccessCount and Heatmap (Sec. 4, "Memory access instrumentation") of
+ * the n-body consumer: llgb_nbody_step, with every access it makes through
+ * the view counted as a side effect.  The result bits are those of
+ * llgb_nbody_step.
+ *   field_counts: NULL, or 14 device uint64 counters, 8-byte aligned,
+ *       incremented (not zeroed): reads of leaves 0..6, then writes of
+ *       leaves 0..6 (FieldAccessCount: two counters per record field).
+ *   count_mode: how field_counts are incremented --
+ *       LLGB_COUNT_ATOMIC: one global atomic increment per access (the
+ *           paper's scheme);
+ *       LLGB_COUNT_BLOCK: per-CTA shared-memory counters added to the global
+ *           ones once per CTA (the same counts).
+ *   heat, granularity: NULL, or llgb_heatmap_counters(particles, g) device
+ *       uint64 counters, 8-byte aligned, incremented: counter k of blob b
+ *       (after the counters of blobs 0 .. b-1) counts the accesses touching
+ *       bytes [k g, (k+1) g) of blob b; an access of a 4-byte leaf touches
+ *       every granule its bytes overlap.  g: a power of two (1 = bytes,
+ *       64 = cache lines).  One global atomic increment per touched granule.
+ * Accesses of one step: the update reads each particle's pos once, the pos
+ * and mass of every particle once per 64-particle block of the update
+ * (B = ceil(n / 64) blocks), and reads and writes each vel once; the move
+ * reads each pos and vel once and writes each pos once.
+ * Errors: as llgb_nbody_step, plus INVALID_ARG (count mode, granularity,
+ * alignment). */
+typedef enum llgb_count_mode { LLGB_COUNT_ATOMIC = 1, LLGB_COUNT_BLOCK = 2 } llgb_count_mode;
+
+llgb_status llgb_nbody_step_instrumented(llgb_view* particles, float eps, float dt, uint64_t* field_counts,
+                                         int32_t count_mode, uint64_t* heat, uint64_t granularity, void* stream);
+
+/* Number of Heatmap counters of `view` at `granularity` bytes (a power of
+ * two): the sum over its blobs of ceil(blob bytes / granularity). */
+llgb_status llgb_heatmap_counters(const llgb_view* view, uint64_t granularity, uint64_t* counters);
+
 /* -------------------------------------------------------------- status -- */
 
 /* Read the device status word that kernels set when a bounded wait gives up

@@ -608,7 +608,13 @@ llgb_status llgb_unpack(const llgb_view* packed, llgb_view* plain, void* stream)
     return llgb_copy(packed, plain, stream);
 }
 
-llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream)
+}  // extern "C"
+
+namespace {
+
+// The particle view the n-body kernels read, plus for each leaf its blob and
+// the byte offset of its base in that blob (for heatmap counters).
+llgb_status particle_view(llgb_view* particles, ParticleView* v, int* kind, int* blob, uint64_t* boff)
 {
     if (!particles) return fail(LLGB_ERR_INVALID_ARG, "null view");
     const ViewPlan& p = particles->plan;
@@ -618,37 +624,107 @@ llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* str
         return fail(LLGB_ERR_UNSUPPORTED, "n-body reads AoS, SoA or AoSoA views");
     if (!particles->bound) return fail(LLGB_ERR_UNBOUND, "view used before llgb_view_bind");
     if (p.n > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs n < 2^32");
-    ParticleView v{};
-    v.n = (uint32_t)p.n;
-    int kind = PV_GENERIC;
+    *v = ParticleView{};
+    v->n = (uint32_t)p.n;
+    *kind = PV_GENERIC;
+    for (int f = 0; f < 7; ++f) blob[f] = 0;
     switch (p.base) {
     case BASE_AOS:  // 28-byte record, aligned and packed alike
-        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[0]) + 4 * f;
-        v.bstride = 28;
-        kind = PV_AOS;
+        for (int f = 0; f < 7; ++f) boff[f] = 4u * f;
+        v->bstride = 28;
+        *kind = PV_AOS;
         break;
     case BASE_SOA_MB:
-        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[f]);
-        v.bstride = 4;
-        kind = PV_SOA;
+        for (int f = 0; f < 7; ++f) {
+            blob[f] = f;
+            boff[f] = 0;
+        }
+        v->bstride = 4;
+        *kind = PV_SOA;
         break;
     case BASE_SOA_SB:
-        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[0]) + p.sb_base[f];
-        v.bstride = 4;
-        kind = PV_SOA;
+        for (int f = 0; f < 7; ++f) boff[f] = p.sb_base[f];
+        v->bstride = 4;
+        *kind = PV_SOA;
         break;
     default: {  // AoSoA
         const uint64_t L = p.lanes;
         if (L & (L - 1)) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs a power-of-two AoSoA lane count");
-        for (int f = 0; f < 7; ++f) v.base[f] = static_cast<uint8_t*>(particles->ptrs[0]) + L * 4 * f;
-        v.bstride = (uint32_t)(28 * L);
-        v.lmask = (uint32_t)(L - 1);
-        while ((1ull << v.lshift) < L) ++v.lshift;
-        kind = L == 32 ? PV_AOSOA32 : PV_GENERIC;
+        for (int f = 0; f < 7; ++f) boff[f] = L * 4 * f;
+        v->bstride = (uint32_t)(28 * L);
+        v->lmask = (uint32_t)(L - 1);
+        while ((1ull << v->lshift) < L) ++v->lshift;
+        *kind = L == 32 ? PV_AOSOA32 : PV_GENERIC;
         break;
     }
     }
+    for (int f = 0; f < 7; ++f) v->base[f] = static_cast<uint8_t*>(particles->ptrs[blob[f]]) + boff[f];
+    return LLGB_OK;
+}
+
+// Heatmap counters of a view at granularity g: ceil(blob bytes / g) per blob;
+// start[b] = counters of the blobs before b.
+uint64_t heat_layout(const llgb_view* v, uint64_t g, std::vector<uint64_t>* start)
+{
+    start->assign(1, 0);
+    for (uint64_t s : v->plan.blob_sizes) start->push_back(start->back() + (s + g - 1) / g);
+    return start->back();
+}
+
+}  // namespace
+
+extern "C" {
+
+llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream)
+{
+    ParticleView v;
+    int kind = 0, blob[7];
+    uint64_t boff[7];
+    const llgb_status st = particle_view(particles, &v, &kind, blob, boff);
+    if (st != LLGB_OK) return st;
     const cudaError_t e = launch_nbody(v, kind, eps, dt, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
+    return LLGB_OK;
+}
+
+llgb_status llgb_heatmap_counters(const llgb_view* view, uint64_t granularity, uint64_t* counters)
+{
+    if (!view || !counters) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+    if (granularity == 0 || (granularity & (granularity - 1)))
+        return fail(LLGB_ERR_INVALID_ARG, "granularity must be a power of two");
+    std::vector<uint64_t> start;
+    *counters = heat_layout(view, granularity, &start);
+    return LLGB_OK;
+}
+
+llgb_status llgb_nbody_step_instrumented(llgb_view* particles, float eps, float dt, uint64_t* field_counts,
+                                         int32_t count_mode, uint64_t* heat, uint64_t granularity, void* stream)
+{
+    ParticleView v;
+    int kind = 0, blob[7];
+    uint64_t boff[7];
+    llgb_status st = particle_view(particles, &v, &kind, blob, boff);
+    if (st != LLGB_OK) return st;
+    if (field_counts && count_mode != LLGB_COUNT_ATOMIC && count_mode != LLGB_COUNT_BLOCK)
+        return fail(LLGB_ERR_INVALID_ARG, "unknown count mode");
+    if ((reinterpret_cast<uintptr_t>(field_counts) | reinterpret_cast<uintptr_t>(heat)) & 7u)
+        return fail(LLGB_ERR_INVALID_ARG, "counters must be 8-byte aligned");
+    NbodyInstr in{};
+    in.counts = reinterpret_cast<unsigned long long*>(field_counts);
+    in.count_mode = count_mode;
+    if (heat) {
+        if (granularity == 0 || (granularity & (granularity - 1)))
+            return fail(LLGB_ERR_INVALID_ARG, "granularity must be a power of two");
+        std::vector<uint64_t> start;
+        heat_layout(particles, granularity, &start);
+        in.heat = reinterpret_cast<unsigned long long*>(heat);
+        while ((1ull << in.gshift) < granularity) ++in.gshift;
+        for (int f = 0; f < 7; ++f) {
+            in.boff[f] = boff[f];
+            in.hstart[f] = start[blob[f]];
+        }
+    }
+    const cudaError_t e = launch_nbody_instrumented(v, in, eps, dt, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
     return LLGB_OK;
 }

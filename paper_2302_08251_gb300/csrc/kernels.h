@@ -33,6 +33,21 @@ struct ParticleView {
 
 enum { PV_AOS = 0, PV_SOA = 1, PV_AOSOA32 = 2, PV_GENERIC = 3 };
 
+// Access instrumentation of the n-body kernels (Sec. 4): FieldAccessCount
+// counters (reads of leaves 0..6, then writes) and Heatmap counters (per
+// granule of 2^gshift bytes; leaf f's element of record i is at byte
+// boff[f] + offset(i) of its blob, whose counters start at hstart[f]).
+struct NbodyInstr {
+    unsigned long long* counts;  // 14 counters, or nullptr
+    unsigned long long* heat;    // heatmap counters, or nullptr
+    uint64_t boff[7];
+    uint64_t hstart[7];
+    uint32_t gshift;
+    int count_mode;              // 1: global atomic per access; 2: per-block counters
+};
+
 cudaError_t launch_nbody(const ParticleView& v, int kind, float eps, float dt, cudaStream_t stream);
+cudaError_t launch_nbody_instrumented(const ParticleView& v, const NbodyInstr& ins, float eps, float dt,
+                                      cudaStream_t stream);
 
 }  // namespace llgb

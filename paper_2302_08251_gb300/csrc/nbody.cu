@@ -46,6 +46,53 @@ __device__ __forceinline__ void st_leaf(const ParticleView& v, int f, uint32_t i
     *reinterpret_cast<float*>(v.base[f] + Addr<KIND>::off(v, i)) = x;
 }
 
+// Access instrumentation (Sec. 4).  CM = 1: one global atomic increment per
+// access (the paper's scheme); CM = 2: per-block shared-memory counters,
+// added to the global ones once per block (same counts, far fewer global
+// atomics).  HEAT: one global atomic per granule an access touches.
+template <int KIND, int CM, bool HEAT>
+__device__ __forceinline__ void note(const ParticleView& v, const NbodyInstr& in, unsigned long long* block_counts,
+                                     int f, uint32_t i, bool write)
+{
+    const int c = f + (write ? 7 : 0);
+    if (CM == 1) atomicAdd(&in.counts[c], 1ull);
+    if (CM == 2) atomicAdd(&block_counts[c], 1ull);
+    if (HEAT) {
+        const uint64_t off = in.boff[f] + Addr<KIND>::off(v, i);
+        for (uint64_t k = off >> in.gshift; k <= (off + 3u) >> in.gshift; ++k)
+            atomicAdd(&in.heat[in.hstart[f] + k], 1ull);
+    }
+}
+
+template <int KIND, int CM, bool HEAT>
+__device__ __forceinline__ float ld_i(const ParticleView& v, const NbodyInstr& in, unsigned long long* bc, int f,
+                                      uint32_t i)
+{
+    if (CM != 0 || HEAT) note<KIND, CM, HEAT>(v, in, bc, f, i, false);
+    return ld_leaf<KIND>(v, f, i);
+}
+
+template <int KIND, int CM, bool HEAT>
+__device__ __forceinline__ void st_i(const ParticleView& v, const NbodyInstr& in, unsigned long long* bc, int f,
+                                     uint32_t i, float x)
+{
+    if (CM != 0 || HEAT) note<KIND, CM, HEAT>(v, in, bc, f, i, true);
+    st_leaf<KIND>(v, f, i, x);
+}
+
+template <int CM>
+__device__ __forceinline__ void block_counts_init(unsigned long long* bc)
+{
+    if (CM == 2 && threadIdx.x < 14) bc[threadIdx.x] = 0ull;
+}
+
+// After a __syncthreads: add the block's counters to the global ones.
+template <int CM>
+__device__ __forceinline__ void block_counts_flush(const NbodyInstr& in, const unsigned long long* bc)
+{
+    if (CM == 2 && threadIdx.x < 14 && bc[threadIdx.x] != 0ull) atomicAdd(&in.counts[threadIdx.x], bc[threadIdx.x]);
+}
+
 // A shared-memory view with compile-time extent N of the record {x, y, z, m}:
 // no extents or mapping state are stored, only the records.
 template <int N>
@@ -76,28 +123,43 @@ __device__ __forceinline__ void interact(const float4 b, float px, float py, flo
 // One warp per j slice: it stages kJ-record tiles of its slice with warp-
 // level synchronisation only, and every lane interacts two particles (i and
 // i + 32) with each staged record.
-template <int KIND>
+template <int KIND, int CM = 0, bool HEAT = false>
 __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v, float eps2, float dt,
-                                                            uint32_t chunk)
+                                                            uint32_t chunk, const NbodyInstr in)
 {
     __shared__ StaticBodyTile<kJ> tile[kParts];
     __shared__ float3 partial[kParts][kI];
+    __shared__ unsigned long long bc[14];
     const uint32_t lane = threadIdx.x % kW;
     const uint32_t part = threadIdx.x / kW;
     const uint32_t i0 = blockIdx.x * kI + lane, i1 = i0 + kW;
     const uint32_t n = v.n;
+    block_counts_init<CM>(bc);
+    if (CM == 2) __syncthreads();
 
+    // the block's own particles are read by slice 0 only (once each)
     float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
-    if (i0 < n) {
-        p0x = ld_leaf<KIND>(v, 0, i0);
-        p0y = ld_leaf<KIND>(v, 1, i0);
-        p0z = ld_leaf<KIND>(v, 2, i0);
+    if (part == 0) {
+        if (i0 < n) {
+            p0x = ld_i<KIND, CM, HEAT>(v, in, bc, 0, i0);
+            p0y = ld_i<KIND, CM, HEAT>(v, in, bc, 1, i0);
+            p0z = ld_i<KIND, CM, HEAT>(v, in, bc, 2, i0);
+        }
+        if (i1 < n) {
+            p1x = ld_i<KIND, CM, HEAT>(v, in, bc, 0, i1);
+            p1y = ld_i<KIND, CM, HEAT>(v, in, bc, 1, i1);
+            p1z = ld_i<KIND, CM, HEAT>(v, in, bc, 2, i1);
+        }
+        partial[0][lane] = make_float3(p0x, p0y, p0z);
+        partial[0][lane + kW] = make_float3(p1x, p1y, p1z);
     }
-    if (i1 < n) {
-        p1x = ld_leaf<KIND>(v, 0, i1);
-        p1y = ld_leaf<KIND>(v, 1, i1);
-        p1z = ld_leaf<KIND>(v, 2, i1);
+    __syncthreads();
+    if (part != 0) {
+        const float3 q0 = partial[0][lane], q1 = partial[0][lane + kW];
+        p0x = q0.x; p0y = q0.y; p0z = q0.z;
+        p1x = q1.x; p1y = q1.y; p1z = q1.z;
     }
+    __syncthreads();
     float a0x = 0.f, a0y = 0.f, a0z = 0.f, a1x = 0.f, a1y = 0.f, a1z = 0.f;
     const uint32_t j0 = part * chunk;
     for (uint32_t jt = 0; jt < chunk; jt += kJ) {
@@ -107,8 +169,8 @@ __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v
             const uint32_t j = j0 + jl;
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);  // zero mass beyond n
             if (j < n && jl < chunk)
-                q = make_float4(ld_leaf<KIND>(v, 0, j), ld_leaf<KIND>(v, 1, j), ld_leaf<KIND>(v, 2, j),
-                                ld_leaf<KIND>(v, 6, j));
+                q = make_float4(ld_i<KIND, CM, HEAT>(v, in, bc, 0, j), ld_i<KIND, CM, HEAT>(v, in, bc, 1, j),
+                                ld_i<KIND, CM, HEAT>(v, in, bc, 2, j), ld_i<KIND, CM, HEAT>(v, in, bc, 6, j));
             tile[part](lane + r * kW) = q;
         }
         __syncwarp();
@@ -144,33 +206,66 @@ __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v
                 sy += partial[p][li].y;
                 sz += partial[p][li].z;
             }
-            st_leaf<KIND>(v, 3, i, fmaf(dt, sx, ld_leaf<KIND>(v, 3, i)));
-            st_leaf<KIND>(v, 4, i, fmaf(dt, sy, ld_leaf<KIND>(v, 4, i)));
-            st_leaf<KIND>(v, 5, i, fmaf(dt, sz, ld_leaf<KIND>(v, 5, i)));
+            st_i<KIND, CM, HEAT>(v, in, bc, 3, i, fmaf(dt, sx, ld_i<KIND, CM, HEAT>(v, in, bc, 3, i)));
+            st_i<KIND, CM, HEAT>(v, in, bc, 4, i, fmaf(dt, sy, ld_i<KIND, CM, HEAT>(v, in, bc, 4, i)));
+            st_i<KIND, CM, HEAT>(v, in, bc, 5, i, fmaf(dt, sz, ld_i<KIND, CM, HEAT>(v, in, bc, 5, i)));
         }
+    }
+    if (CM == 2) {
+        __syncthreads();
+        block_counts_flush<CM>(in, bc);
     }
 }
 
-template <int KIND>
-__global__ void nbody_move(const ParticleView v, float dt)
+template <int KIND, int CM = 0, bool HEAT = false>
+__global__ void nbody_move(const ParticleView v, float dt, const NbodyInstr in)
 {
+    __shared__ unsigned long long bc[14];
+    block_counts_init<CM>(bc);
+    if (CM == 2) __syncthreads();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.n) return;
-    for (int k = 0; k < 3; ++k) st_leaf<KIND>(v, k, i, fmaf(dt, ld_leaf<KIND>(v, 3 + k, i), ld_leaf<KIND>(v, k, i)));
+    if (i < v.n) {
+        for (int k = 0; k < 3; ++k) {
+            const float vel = ld_i<KIND, CM, HEAT>(v, in, bc, 3 + k, i);
+            const float pos = ld_i<KIND, CM, HEAT>(v, in, bc, k, i);
+            st_i<KIND, CM, HEAT>(v, in, bc, k, i, fmaf(dt, vel, pos));
+        }
+    }
+    if (CM == 2) {
+        __syncthreads();
+        block_counts_flush<CM>(in, bc);
+    }
 }
 
-template <int KIND>
-static cudaError_t launch_kind(const ParticleView& v, float eps, float dt, cudaStream_t stream)
+template <int KIND, int CM = 0, bool HEAT = false>
+static cudaError_t launch_kind(const ParticleView& v, float eps, float dt, cudaStream_t stream,
+                               const NbodyInstr& in = NbodyInstr{})
 {
     const uint32_t n = v.n;
     uint32_t chunk = (n + kParts - 1) / kParts;
     chunk = (chunk + kJ - 1) / kJ * kJ;
     const uint32_t blocks = (n + kI - 1) / kI;
-    nbody_update<KIND><<<blocks, kW * kParts, 0, stream>>>(v, eps * eps, dt, chunk);
+    nbody_update<KIND, CM, HEAT><<<blocks, kW * kParts, 0, stream>>>(v, eps * eps, dt, chunk, in);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    nbody_move<KIND><<<(n + 255) / 256, 256, 0, stream>>>(v, dt);
+    nbody_move<KIND, CM, HEAT><<<(n + 255) / 256, 256, 0, stream>>>(v, dt, in);
     return cudaGetLastError();
+}
+
+// Instrumented steps use the runtime address function; the arithmetic, and
+// so every result bit, is the plain step's.
+cudaError_t launch_nbody_instrumented(const ParticleView& v, const NbodyInstr& in, float eps, float dt,
+                                      cudaStream_t stream)
+{
+    if (v.n == 0) return cudaSuccess;
+    const bool heat = in.heat != nullptr;
+    const int cm = in.counts ? in.count_mode : 0;
+    if (cm == 1) return heat ? launch_kind<PV_GENERIC, 1, true>(v, eps, dt, stream, in)
+                             : launch_kind<PV_GENERIC, 1, false>(v, eps, dt, stream, in);
+    if (cm == 2) return heat ? launch_kind<PV_GENERIC, 2, true>(v, eps, dt, stream, in)
+                             : launch_kind<PV_GENERIC, 2, false>(v, eps, dt, stream, in);
+    return heat ? launch_kind<PV_GENERIC, 0, true>(v, eps, dt, stream, in)
+                : launch_kind<PV_GENERIC, 0, false>(v, eps, dt, stream, in);
 }
 
 cudaError_t launch_nbody(const ParticleView& v, int kind, float eps, float dt, cudaStream_t stream)

@@ -81,6 +81,7 @@ class LaunchConfig(ctypes.Structure):
 EXPORTS = [
     "llgb_last_error", "llgb_version", "llgb_record_create", "llgb_record_destroy",
     "llgb_record_leaf_count", "llgb_record_size", "llgb_view_create", "llgb_view_destroy",
+    "llgb_nbody_step_instrumented", "llgb_heatmap_counters",
     "llgb_view_blob_count", "llgb_view_blob_size", "llgb_view_record_count",
     "llgb_view_bind", "llgb_copy", "llgb_pack", "llgb_unpack", "llgb_copy_config",
     "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
@@ -125,6 +126,8 @@ def lib():
         L.llgb_copy_config.argtypes = [p, p, ctypes.POINTER(LaunchConfig)]
         L.llgb_copy_with.argtypes = [p, p, ctypes.POINTER(LaunchConfig), p]
         L.llgb_nbody_step.argtypes = [p, ctypes.c_float, ctypes.c_float, p]
+        L.llgb_nbody_step_instrumented.argtypes = [p, ctypes.c_float, ctypes.c_float, p, i32, p, u64, p]
+        L.llgb_heatmap_counters.argtypes = [p, u64, ctypes.POINTER(u64)]
         L.llgb_device_status.argtypes = [ctypes.POINTER(i32), i32]
         L.llgb_batch_create.argtypes = [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)]
         L.llgb_batch_launch.argtypes = [p, p, i32]
@@ -307,6 +310,26 @@ def llgb_copy_with(src: View, dst: View, cfg: dict, stream=None) -> None:
 
 def llgb_nbody_step(view: View, eps: float, dt: float, stream=None) -> None:
     check(lib().llgb_nbody_step(view.handle, float(eps), float(dt), _stream_ptr(stream)))
+
+
+COUNT_MODES = {"atomic": 1, "block": 2}
+
+
+def llgb_heatmap_counters(view: View, granularity: int) -> int:
+    out = ctypes.c_uint64()
+    check(lib().llgb_heatmap_counters(view.handle, int(granularity), ctypes.byref(out)))
+    return out.value
+
+
+def llgb_nbody_step_instrumented(view: View, eps: float, dt: float, field_counts=None, count_mode="atomic",
+                                 heat=None, granularity: int = 1, stream=None) -> None:
+    """llgb_nbody_step counting its accesses: field_counts (14 uint64 device
+    counters) and/or heat (llgb_heatmap_counters(view, granularity) uint64
+    device counters), both incremented."""
+    fc = ctypes.c_void_p(field_counts.data_ptr()) if field_counts is not None else None
+    ht = ctypes.c_void_p(heat.data_ptr()) if heat is not None else None
+    check(lib().llgb_nbody_step_instrumented(view.handle, float(eps), float(dt), fc, COUNT_MODES[count_mode],
+                                             ht, int(granularity), _stream_ptr(stream)))
 
 
 def llgb_device_status(reset: bool = False) -> int:
