@@ -33,7 +33,7 @@ TYPE_ID = {t: k for k, t in enumerate(TYPES)}
 TYPE_SIZE = {"u8": 1, "u16": 2, "u32": 4, "u64": 8, "i8": 1, "i16": 2,
              "i32": 4, "i64": 8, "f16": 2, "bf16": 2, "f32": 4, "f64": 8}
 KINDS = ["aos", "soa_sb", "soa_mb", "aosoa", "bitpack_int", "bitpack_float",
-         "bytesplit", "changetype"]
+         "bytesplit", "changetype", "null", "split"]
 KIND_ID = {k: n for n, k in enumerate(KINDS)}
 MAX_CT = 4
 
@@ -71,6 +71,8 @@ _Mapping._fields_ = [
     ("field_exp", ctypes.POINTER(ctypes.c_int32)),
     ("field_man", ctypes.POINTER(ctypes.c_int32)),
     ("inner", ctypes.POINTER(_Mapping)),
+    ("split_mask", ctypes.c_uint64),
+    ("inner2", ctypes.POINTER(_Mapping)),
 ]
 
 _lib = None
@@ -132,6 +134,12 @@ def _to_c_mapping(m: dict, keep: list) -> _Mapping:
         inner = _to_c_mapping(m["inner"], keep)
         keep.append(inner)
         c.inner = ctypes.pointer(inner)
+    if m["kind"] == "split":
+        # {"kind": "split", "fields": [leaf indices -> "inner"], "rest": mapping of the others}
+        c.split_mask = sum(1 << f for f in m["fields"])
+        rest = _to_c_mapping(m["rest"], keep)
+        keep.append(rest)
+        c.inner2 = ctypes.pointer(rest)
     return c
 
 

@@ -96,6 +96,30 @@ static int inner_types(const int32_t* types, int32_t nf, const orc_mapping* m,
     return -1;
 }
 
+/* Split (with Null, Sec. 3): the leaves whose bit is set in split_mask form,
+ * in leaf order, the record of `inner`; the others that of `inner2`.  The
+ * blobs of `inner` come first, then those of `inner2`. */
+static void split_types(const int32_t* types, int32_t nf, const orc_mapping* m, int32_t* t0, int* n0,
+                        int32_t* t1, int* n1)
+{
+    *n0 = *n1 = 0;
+    for (int f = 0; f < nf; ++f) {
+        if ((m->split_mask >> f) & 1u) t0[(*n0)++] = types[f];
+        else t1[(*n1)++] = types[f];
+    }
+}
+
+/* Part (0: inner, 1: inner2) of leaf f and its index in that part's record. */
+static int split_index(const orc_mapping* m, int32_t f, int* part)
+{
+    const int sel = (int)((m->split_mask >> f) & 1u);
+    int idx = 0;
+    for (int g = 0; g < f; ++g)
+        if ((int)((m->split_mask >> g) & 1u) == sel) ++idx;
+    *part = sel ? 0 : 1;
+    return idx;
+}
+
 /* Index of the first inner leaf that Bytesplit makes from leaf f. */
 static int bytesplit_first(const int32_t* types, int32_t f)
 {
@@ -162,6 +186,18 @@ int orc_check(const int32_t* types, int32_t nf, const orc_mapping* m)
         int n = inner_types(types, nf, m, it);
         if (n < 0) return 8;
         return orc_check(it, n, m->inner);
+    }
+    case ORC_NULL:
+        return 0;
+    case ORC_SPLIT: {
+        int32_t t0[MAX_LEAVES], t1[MAX_LEAVES];
+        int n0, n1, r;
+        if (!m->inner || !m->inner2) return 6;
+        if (nf < 64 && (m->split_mask >> nf) != 0) return 10;  /* selects no leaf beyond the record */
+        split_types(types, nf, m, t0, &n0, t1, &n1);
+        if (n0 == 0 || n1 == 0) return 10;                      /* both parts hold leaves */
+        r = orc_check(t0, n0, m->inner);
+        return r ? r : orc_check(t1, n1, m->inner2);
     }
     default:
         return 9;
@@ -292,6 +328,14 @@ int32_t orc_blob_count(const int32_t* types, int32_t nf, const orc_mapping* m)
         int ni = inner_types(types, nf, m, it);
         return ni < 0 ? 0 : orc_blob_count(it, ni, m->inner);
     }
+    case ORC_NULL:
+        return 0;
+    case ORC_SPLIT: {
+        int32_t t0[MAX_LEAVES], t1[MAX_LEAVES];
+        int n0, n1;
+        split_types(types, nf, m, t0, &n0, t1, &n1);
+        return orc_blob_count(t0, n0, m->inner) + orc_blob_count(t1, n1, m->inner2);
+    }
     default:
         return 0;
     }
@@ -328,6 +372,13 @@ uint64_t orc_blob_size(const int32_t* types, int32_t nf, const orc_mapping* m,
         int32_t it[MAX_LEAVES];
         int ni = inner_types(types, nf, m, it);
         return orc_blob_size(it, ni, m->inner, n, k);
+    }
+    case ORC_SPLIT: {
+        int32_t t0[MAX_LEAVES], t1[MAX_LEAVES];
+        int n0, n1;
+        split_types(types, nf, m, t0, &n0, t1, &n1);
+        const int32_t b0 = orc_blob_count(t0, n0, m->inner);
+        return k < b0 ? orc_blob_size(t0, n0, m->inner, n, k) : orc_blob_size(t1, n1, m->inner2, n, k - b0);
     }
     default:
         return 0;
@@ -482,6 +533,16 @@ uint64_t orc_load(const int32_t* types, int32_t nf, const orc_mapping* m, uint64
         float_format(t, &te, &tm);
         return orc_convert(u, ue, um, te, tm);
     }
+    case ORC_NULL:
+        return 0;  /* Sec. 3: a default-constructed value */
+    case ORC_SPLIT: {
+        int32_t t0[MAX_LEAVES], t1[MAX_LEAVES];
+        int n0, n1, part;
+        split_types(types, nf, m, t0, &n0, t1, &n1);
+        const int idx = split_index(m, f, &part);
+        if (part == 0) return orc_load(t0, n0, m->inner, n, blobs, i, idx);
+        return orc_load(t1, n1, m->inner2, n, blobs + orc_blob_count(t0, n0, m->inner), i, idx);
+    }
     default:
         return 0;
     }
@@ -533,6 +594,17 @@ void orc_store(const int32_t* types, int32_t nf, const orc_mapping* m, uint64_t 
             u = orc_convert(v, te, tm, ue, um);
         }
         orc_store(it, ni, m->inner, n, blobs, i, f, u);
+        return;
+    }
+    case ORC_NULL:
+        return;  /* Sec. 3: writes are discarded */
+    case ORC_SPLIT: {
+        int32_t t0[MAX_LEAVES], t1[MAX_LEAVES];
+        int n0, n1, part;
+        split_types(types, nf, m, t0, &n0, t1, &n1);
+        const int idx = split_index(m, f, &part);
+        if (part == 0) orc_store(t0, n0, m->inner, n, blobs, i, idx, v);
+        else orc_store(t1, n1, m->inner2, n, blobs + orc_blob_count(t0, n0, m->inner), i, idx, v);
         return;
     }
     default:

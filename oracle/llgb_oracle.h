@@ -48,7 +48,9 @@ enum {
     ORC_BITPACK_INT,      /* b-bit integers, one bit stream per leaf               */
     ORC_BITPACK_FLOAT,    /* (1+E+M)-bit floats, one bit stream per leaf           */
     ORC_BYTESPLIT,        /* each leaf split into bytes, forwarded to `inner`      */
-    ORC_CHANGETYPE        /* leaves of type from[k] stored as to[k] via `inner`    */
+    ORC_CHANGETYPE,       /* leaves of type from[k] stored as to[k] via `inner`    */
+    ORC_NULL,             /* no storage: loads give 0, stores are discarded        */
+    ORC_SPLIT             /* leaves in split_mask via `inner`, the rest via `inner2` */
 };
 
 #define ORC_MAX_CT 4
@@ -67,7 +69,10 @@ typedef struct orc_mapping {
     const int32_t* field_bits;   /* optional per-leaf override of `bits`           */
     const int32_t* field_exp;    /* optional per-leaf override of `exp_bits`       */
     const int32_t* field_man;    /* optional per-leaf override of `man_bits`       */
-    const struct orc_mapping* inner; /* Bytesplit / ChangeType inner mapping       */
+    const struct orc_mapping* inner; /* Bytesplit / ChangeType inner mapping; Split:
+                                        mapping of the selected leaves            */
+    uint64_t split_mask;         /* Split: bit f set = leaf f is selected          */
+    const struct orc_mapping* inner2; /* Split: mapping of the other leaves        */
 } orc_mapping;
 
 /* Size in bytes of a leaf type; 0 for an unknown type. */
