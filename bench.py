@@ -534,11 +534,48 @@ def time_copy(src, dst, reps=10):
     return statistics.median(ts)
 
 
+SPLIT_ROWS = [
+    # (row name, record kind, source mapping, destination mapping)
+    ("2^26 INT6 AoS -> Split{a,b,c,d: BitpackInt b=12 | e,f: SoA-MB}", "int6", {"kind": "aos"},
+     {"kind": "split", "fields": [0, 1, 2, 3], "inner": {"kind": "bitpack_int", "bits": 12},
+      "rest": {"kind": "soa_mb"}}),
+    ("2^26 particles AoS -> Split{pos: SoA-MB | vel, mass: AoSoA32}", "particle", {"kind": "aos"},
+     {"kind": "split", "fields": [0, 1, 2], "inner": {"kind": "soa_mb"},
+      "rest": {"kind": "aosoa", "lanes": 32}}),
+    ("2^26 particles AoS -> Split{mass: Null | rest: SoA-MB}", "particle", {"kind": "aos"},
+     {"kind": "split", "fields": [6], "inner": {"kind": "null"}, "rest": {"kind": "soa_mb"}}),
+]
+
+
+def split_rows(device, entry):
+    """Copies into and out of Split views (Sec. 3): each row's forward copy
+    and the copy back into the source's mapping, algorithmic bytes = source
+    blobs + destination blobs."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, synth
+    n = 1 << 26
+    rows = {}
+    for name, kind, src_map, dst_map in SPLIT_ROWS:
+        leaves = {"int6": synth.INT6, "particle": synth.PARTICLE}[kind]
+        rec = llgb.Record(leaves)
+        fields = synth.device_fields(kind, n, 23, device=device)
+        soa = llgb.View(rec, {"kind": "soa_mb"}, (n,), blobs=[f.view(torch.uint8) for f in fields])
+        src = llgb.View(rec, src_map, (n,))
+        llgb.llgb_copy(soa, src)
+        del soa, fields
+        dst = llgb.View(rec, dst_map, (n,))
+        nbytes = sum(llgb.blob_sizes(rec, src_map, (n,))) + sum(llgb.blob_sizes(rec, dst_map, (n,)))
+        rows[name] = {"forward": entry(nbytes, time_copy(src, dst)), "back": entry(nbytes, time_copy(dst, src))}
+        del src, dst
+        torch.cuda.empty_cache()
+    return rows
+
+
 def sweeps_bench(device):
     """The configurations the suite's step holds one point of: BitpackInt at
     b in {1, 3, 7, 12, 17, 31} (2^26 INT6 records), BitpackFloat at the 12
     (E, M) formats (2^25 MIXED_F records), both from / to SoA multi-blob;
-    and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose
+    copies into and out of Split / Null views (2^26 records); and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose
     3.7 MB fit L2: its latency is reported warm and with L2 flushed."""
     import torch
     from paper_2302_08251_gb300 import llgb, synth
@@ -584,6 +621,8 @@ def sweeps_bench(device):
     out["C2 BitpackFloat, 2^25 MIXED_F records, SoA-MB <-> BitpackFloatSoA"] = c2
     del fields, base, plain
     torch.cuda.empty_cache()
+
+    out["F2 Split / Null"] = split_rows(device, entry)
 
     n = 65536
     rec = llgb.Record(synth.PARTICLE)

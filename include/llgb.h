@@ -126,7 +126,10 @@ enum {
     LLGB_MAP_BITPACK_INT,      /* BitpackIntSoA: b-bit integers (Sec. 3)       */
     LLGB_MAP_BITPACK_FLOAT,    /* BitpackFloatSoA: (1+E+M)-bit floats (Sec. 3)  */
     LLGB_MAP_BYTESPLIT,        /* Bytesplit over `inner` (Sec. 3)              */
-    LLGB_MAP_CHANGETYPE        /* ChangeType over `inner` (Sec. 3)             */
+    LLGB_MAP_CHANGETYPE,       /* ChangeType over `inner` (Sec. 3)             */
+    LLGB_MAP_NULL,             /* no storage (Sec. 3)                          */
+    LLGB_MAP_SPLIT             /* leaves in split_mask via `inner`, the others
+                                  via `inner2` (Sec. 3, with Null)              */
 };
 
 #define LLGB_MAX_CT 4
@@ -153,7 +156,14 @@ enum {
  *  CHANGETYPE:    leaves of type ct_from[k] are stored as ct_to[k] (floating
  *                 point types) through `inner`; round to nearest even on store,
  *                 exact or RNE conversion back on load.
- * `inner` must be an AOS, SOA_* or AOSOA mapping. */
+ *  NULL:          no blobs: loads give a zero value, stores are discarded.
+ *  SPLIT:         the leaves whose bit is set in split_mask form (in leaf
+ *                 order) the record of `inner`, the other leaves that of
+ *                 `inner2`; the view's blobs are inner's, then inner2's.  Both
+ *                 sides hold at least one leaf; any kind may be nested,
+ *                 including SPLIT and NULL.
+ * The `inner` of BYTESPLIT and CHANGETYPE must be an AOS, SOA_* or AOSOA
+ * mapping. */
 typedef struct llgb_mapping_desc {
     int32_t kind;
     int32_t aos_packed;
@@ -169,6 +179,8 @@ typedef struct llgb_mapping_desc {
     const int32_t* field_exp;
     const int32_t* field_man;
     const struct llgb_mapping_desc* inner;
+    uint64_t split_mask;                     /* SPLIT: bit f = leaf f to `inner` */
+    const struct llgb_mapping_desc* inner2;  /* SPLIT: mapping of the others     */
 } llgb_mapping_desc;
 
 /* ---------------------------------------------------------------- view -- */

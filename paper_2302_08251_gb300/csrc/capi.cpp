@@ -304,7 +304,10 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     return LLGB_OK;
 }
 
-bool is_bitpacked(const llgb_view* v) { return v && v->plan.base >= BASE_BITS_INT; }
+bool is_bitpacked(const llgb_view* v)
+{
+    return v && (v->plan.base == BASE_BITS_INT || v->plan.base == BASE_BITS_FLOAT);
+}
 
 }  // namespace
 
@@ -620,7 +623,7 @@ llgb_status particle_view(llgb_view* particles, ParticleView* v, int* kind, int*
     const ViewPlan& p = particles->plan;
     if (p.types != std::vector<int32_t>(7, LLGB_F32))
         return fail(LLGB_ERR_INVALID_ARG, "n-body needs the 7-leaf f32 particle record");
-    if (p.wrap != WRAP_NONE || p.base >= BASE_BITS_INT)
+    if (p.wrap != WRAP_NONE || p.base == BASE_BITS_INT || p.base == BASE_BITS_FLOAT || p.base == BASE_SPLIT)
         return fail(LLGB_ERR_UNSUPPORTED, "n-body reads AoS, SoA or AoSoA views");
     if (!particles->bound) return fail(LLGB_ERR_UNBOUND, "view used before llgb_view_bind");
     if (p.n > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs n < 2^32");

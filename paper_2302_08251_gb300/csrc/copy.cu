@@ -305,6 +305,7 @@ __device__ __noinline__ void value_loop(const ItemDesc& I, const JobDesc& J, con
 
     auto load = [&](uint32_t r) -> uint64_t {
         if (r >= nvalid) return 0ull;
+        if (LOP == L_NULL) return 0ull;  // Null mapping: a zero value
         if (LOP == L_DIRECT) return ld_elem(simg + eoff(A, r), size, A.align);
         if (LOP == L_CT) return fconv(ld_elem(simg + eoff(A, r), I.s_size, A.align), I.s_e, I.s_m, I.l_e, I.l_m);
         if (is_bits_src) {
@@ -1038,6 +1039,7 @@ __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc&
         case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, sp, nvalid); break;
         case L_BITS_INT: value_dispatch<L_BITS_INT>(I, J, simg, dimg, sp, nvalid); break;
         case L_BITS_FLOAT: value_dispatch<L_BITS_FLOAT>(I, J, simg, dimg, sp, nvalid); break;
+        case L_NULL: value_dispatch<L_NULL>(I, J, simg, dimg, sp, nvalid); break;
         default: value_dispatch<L_SPLIT>(I, J, simg, dimg, sp, nvalid); break;
         }
     }

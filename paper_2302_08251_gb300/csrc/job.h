@@ -55,7 +55,8 @@ struct LeafDesc {
 };
 
 enum ItemOp : uint8_t { ITEM_MOVE = 0, ITEM_VALUE = 1 };
-enum LoadOp : uint8_t { L_DIRECT = 0, L_CT = 1, L_BITS_INT = 2, L_BITS_FLOAT = 3, L_SPLIT = 4 };
+// L_NULL: the leaf has no storage (Null mapping): it loads as 0.
+enum LoadOp : uint8_t { L_DIRECT = 0, L_CT = 1, L_BITS_INT = 2, L_BITS_FLOAT = 3, L_SPLIT = 4, L_NULL = 5 };
 enum StoreOp : uint8_t { S_DIRECT = 0, S_CT = 1, S_BITS_INT = 2, S_BITS_FLOAT = 3, S_SPLIT = 4 };
 
 // A unit of per-record work inside a tile.

@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 
 namespace llgb {
 
@@ -71,6 +72,91 @@ static bool is_affine_kind(int k)
     return k == LLGB_MAP_AOS || k == LLGB_MAP_SOA_SB || k == LLGB_MAP_SOA_MB || k == LLGB_MAP_AOSOA;
 }
 
+static bool is_bits_base(int b) { return b == BASE_BITS_INT || b == BASE_BITS_FLOAT; }
+
+// Split and Null (Sec. 3).  Null stores nothing: its leaves load as zero and
+// their stores are dropped.  Split plans the sub-record of the leaves in
+// split_mask (leaf order) with `inner` and that of the others with `inner2`,
+// each as an ordinary view (recursively), and lays their stored leaves and
+// blobs side by side, inner's first.
+static llgb_status plan_split(const llgb_record& rec, const llgb_extents& ext, const llgb_mapping_desc& map,
+                              ViewPlan& v, ViewPlan* out, std::string* why)
+{
+    const int nf = (int)rec.types.size();
+    v.base = BASE_SPLIT;
+    std::vector<std::vector<int>> fields;
+    std::vector<const llgb_mapping_desc*> maps;
+    if (map.kind == LLGB_MAP_NULL) {
+        fields.emplace_back();
+        for (int f = 0; f < nf; ++f) fields.back().push_back(f);
+        maps.push_back(nullptr);
+    } else {
+        if (!map.inner || !map.inner2) {
+            *why = "Split needs `inner` and `inner2`";
+            return LLGB_ERR_INVALID_ARG;
+        }
+        if (nf < 64 && (map.split_mask >> nf) != 0) {
+            *why = "Split selects a leaf beyond the record";
+            return LLGB_ERR_INVALID_ARG;
+        }
+        std::vector<int> sel, rest;
+        for (int f = 0; f < nf; ++f) ((map.split_mask >> f) & 1u ? sel : rest).push_back(f);
+        if (sel.empty() || rest.empty()) {
+            *why = "Split needs leaves on both sides";
+            return LLGB_ERR_INVALID_ARG;
+        }
+        fields = {sel, rest};
+        maps = {map.inner, map.inner2};
+    }
+    v.recipes.assign(nf, Recipe{L_NULL, 0, 0});
+    std::string sig = "split" + std::to_string(map.kind == LLGB_MAP_NULL ? 0ull : map.split_mask) + "{";
+    for (size_t k = 0; k < fields.size(); ++k) {
+        ViewPlan part;
+        const bool null = maps[k] == nullptr || maps[k]->kind == LLGB_MAP_NULL;
+        v.part_leaf0.push_back((int)v.stored.size());
+        v.part_blob0.push_back((int)v.blob_sizes.size());
+        if (!null) {
+            llgb_record sub;
+            for (int f : fields[k]) {
+                sub.paths.push_back(rec.paths[f]);
+                sub.types.push_back(rec.types[f]);
+            }
+            const llgb_status st = plan_view(sub, ext, *maps[k], &part, why);
+            if (st != LLGB_OK) return st;
+            const int leaf0 = v.part_leaf0.back(), blob0 = v.part_blob0.back();
+            for (size_t j = 0; j < fields[k].size(); ++j) {
+                Recipe r = part.recipes[j];
+                if (r.op != L_NULL) r.first += leaf0;
+                v.recipes[fields[k][j]] = r;
+            }
+            for (size_t g = 0; g < part.stored.size(); ++g) {
+                v.stored.push_back(part.stored[g]);
+                v.seg_end.push_back(part.seg_end[g]);
+                v.leaf_blob.push_back(part.leaf_blob[g] + blob0);
+                v.leaf_offset.push_back(part.leaf_offset[g]);
+                v.sb_base.push_back(part.sb_base[g]);
+            }
+            for (uint64_t b : part.blob_sizes) v.blob_sizes.push_back(b);
+            sig += part.sig;
+        }
+        sig += "|";
+        v.parts.push_back(std::move(part));
+        v.part_fields.push_back(fields[k]);
+        v.part_null.push_back(null);
+    }
+    if ((int)v.stored.size() > kMaxLeaves) {
+        *why = "more than 32 stored leaves";
+        return LLGB_ERR_UNSUPPORTED;
+    }
+    if ((int)v.blob_sizes.size() > kMaxBlobs) {
+        *why = "more than 32 blobs";
+        return LLGB_ERR_UNSUPPORTED;
+    }
+    v.sig = sig + "}";
+    *out = std::move(v);
+    return LLGB_OK;
+}
+
 llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llgb_mapping_desc& map,
                       ViewPlan* out, std::string* why)
 {
@@ -105,6 +191,7 @@ llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llg
         return LLGB_ERR_INDEX_OVERFLOW;
     }
     v.n = n;
+    if (map.kind == LLGB_MAP_SPLIT || map.kind == LLGB_MAP_NULL) return plan_split(rec, ext, map, v, out, why);
 
     // --- wrappers (Sec. 3: ChangeType, Bytesplit) ---
     const llgb_mapping_desc* base = &map;
@@ -330,11 +417,16 @@ static uint64_t gcd64(uint64_t a, uint64_t b)
     return a;
 }
 
+static uint64_t lane_quantum(const ViewPlan& v, uint64_t q)
+{
+    if (v.base == BASE_AOSOA) q = q / gcd64(q, v.lanes) * v.lanes;
+    for (const ViewPlan& p : v.parts) q = lane_quantum(p, q);
+    return q;
+}
+
 uint32_t tile_quantum(const ViewPlan& src, const ViewPlan& dst)
 {
-    uint64_t q = 128;
-    for (const ViewPlan* v : {&src, &dst})
-        if (v->base == BASE_AOSOA) q = q / gcd64(q, v->lanes) * v->lanes;
+    const uint64_t q = lane_quantum(dst, lane_quantum(src, 128));
     return q > (1u << 20) ? 0u : (uint32_t)q;
 }
 
@@ -343,9 +435,15 @@ static double image_bpr(const ViewPlan& v)
     switch (v.base) {
     case BASE_AOS:
     case BASE_AOSOA: return (double)v.record_bytes;
+    case BASE_SPLIT: {
+        double s = 0;
+        for (size_t k = 0; k < v.parts.size(); ++k)
+            if (!v.part_null[k]) s += image_bpr(v.parts[k]);
+        return s;
+    }
     default: {
         double s = 0;
-        for (const StoredLeaf& l : v.stored) s += (v.base >= BASE_BITS_INT) ? l.bits / 8.0 : l.size;
+        for (const StoredLeaf& l : v.stored) s += is_bits_base(v.base) ? l.bits / 8.0 : l.size;
         return s;
     }
     }
@@ -357,23 +455,30 @@ void bytes_per_record(const ViewPlan& src, const ViewPlan& dst, double* src_bpr,
     *src_bpr = image_bpr(src);
     *dst_bpr = image_bpr(dst);
     uint32_t c = 0;
-    if (dst.base >= BASE_BITS_INT)
+    if (is_bits_base(dst.base))
         for (const StoredLeaf& l : dst.stored) c += l.bits > 32 ? 8 : 4;
     *code_bpr = c;
 }
 
-// Fill one side's runs and leaf addressing for tiles of `tile` records.
-static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, uint32_t tile, uint32_t ntiles,
-                             SideDesc* S, std::string* why)
+// Append the runs and leaf addressing of plan v (its blobs and stored leaves
+// numbered from blob0 / leaf0 in the side) for tiles of `tile` records.
+static llgb_status plan_side_part(const ViewPlan& v, int blob0, int leaf0, uint32_t tile, uint32_t ntiles,
+                                  SideDesc* S, uint64_t& img, bool& bulk_ok, std::string* why)
 {
-    memset(S, 0, sizeof *S);
-    for (size_t k = 0; k < ptrs.size(); ++k) S->blobs[k] = static_cast<uint8_t*>(ptrs[k]);
-    uint64_t img = 0;
-    bool bulk_ok = true;
+    if (v.base == BASE_SPLIT) {
+        for (size_t k = 0; k < v.parts.size(); ++k) {
+            if (v.part_null[k]) continue;
+            const llgb_status st = plan_side_part(v.parts[k], blob0 + v.part_blob0[k], leaf0 + v.part_leaf0[k], tile,
+                                                  ntiles, S, img, bulk_ok, why);
+            if (st != LLGB_OK) return st;
+        }
+        return LLGB_OK;
+    }
+    const int segs0 = S->nsegs;
     auto add_seg = [&](uint32_t blob, uint64_t gbase, uint64_t tile_bytes, uint64_t end) -> int64_t {
         if (S->nsegs >= kMaxSegs || tile_bytes > 0xFFFFFFFFull) return -1;
         SegDesc& d = S->segs[S->nsegs++];
-        d.blob = blob;
+        d.blob = blob0 + blob;
         d.gbase = gbase;
         d.tile_bytes = (uint32_t)tile_bytes;
         d.sbase = (uint32_t)img;
@@ -389,9 +494,10 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
         return d.sbase;
     };
     const int ns = (int)v.stored.size();
-    S->nleaves = (uint16_t)ns;
+    S->nleaves = (uint16_t)std::max<int>(S->nleaves, leaf0 + ns);
+    LeafDesc* leaves = S->leaves + leaf0;
     for (int g = 0; g < ns; ++g) {
-        LeafDesc& L = S->leaves[g];
+        LeafDesc& L = leaves[g];
         L.size = (uint16_t)v.stored[g].size;
         L.lanes = 1;
         L.lshift = 0;
@@ -402,8 +508,8 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
         const int64_t sb = add_seg(0, 0, (uint64_t)tile * v.record_bytes, v.seg_end[0]);
         if (sb < 0) break;
         for (int g = 0; g < ns; ++g) {
-            S->leaves[g].sbase = (uint32_t)(sb + v.leaf_offset[g]);
-            S->leaves[g].bstride = (uint32_t)v.record_bytes;
+            leaves[g].sbase = (uint32_t)(sb + v.leaf_offset[g]);
+            leaves[g].bstride = (uint32_t)v.record_bytes;
         }
         break;
     }
@@ -415,10 +521,10 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
         for (uint8_t p = 0; p < 32; ++p)
             if ((1u << p) == L) shift = p;
         for (int g = 0; g < ns; ++g) {
-            S->leaves[g].sbase = (uint32_t)(sb + L * v.leaf_offset[g]);
-            S->leaves[g].bstride = (uint32_t)(L * v.record_bytes);
-            S->leaves[g].lanes = L;
-            S->leaves[g].lshift = shift;
+            leaves[g].sbase = (uint32_t)(sb + L * v.leaf_offset[g]);
+            leaves[g].bstride = (uint32_t)(L * v.record_bytes);
+            leaves[g].lanes = L;
+            leaves[g].lshift = shift;
         }
         break;
     }
@@ -428,8 +534,8 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
             const uint64_t s = v.stored[g].size;
             const int64_t sb = add_seg(v.leaf_blob[g], v.sb_base[g], (uint64_t)tile * s, v.seg_end[g]);
             if (sb < 0) break;
-            S->leaves[g].sbase = (uint32_t)sb;
-            S->leaves[g].bstride = (uint32_t)s;
+            leaves[g].sbase = (uint32_t)sb;
+            leaves[g].bstride = (uint32_t)s;
         }
         break;
     default:
@@ -437,23 +543,36 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
             const uint64_t w = v.stored[g].bits;
             const int64_t sb = add_seg(v.leaf_blob[g], 0, (uint64_t)tile * w / 8, v.seg_end[g]);
             if (sb < 0) break;
-            S->leaves[g].sbase = (uint32_t)sb;
-            S->leaves[g].kind = LEAF_BITS;
-            S->leaves[g].bits = (uint8_t)w;
+            leaves[g].sbase = (uint32_t)sb;
+            leaves[g].kind = LEAF_BITS;
+            leaves[g].bits = (uint8_t)w;
         }
         break;
     }
     const int expect_segs = (v.base == BASE_AOS || v.base == BASE_AOSOA) ? 1 : ns;
-    if (S->nsegs != expect_segs) {
+    if (S->nsegs - segs0 != expect_segs) {
         *why = "internal: a tile run does not fit its blob region";
         return LLGB_ERR_INVALID_ARG;
     }
     for (int g = 0; g < ns; ++g) {
-        LeafDesc& L = S->leaves[g];
+        LeafDesc& L = leaves[g];
         uint32_t p = 8;
         while (p > 1 && ((L.sbase % p) || (L.bstride % p) || (L.lanes > 1 && (L.size % p)))) p /= 2;
         L.align = (uint8_t)p;
     }
+    return LLGB_OK;
+}
+
+// Fill one side's runs and leaf addressing for tiles of `tile` records.
+static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, uint32_t tile, uint32_t ntiles,
+                             SideDesc* S, std::string* why)
+{
+    memset(S, 0, sizeof *S);
+    for (size_t k = 0; k < ptrs.size(); ++k) S->blobs[k] = static_cast<uint8_t*>(ptrs[k]);
+    uint64_t img = 0;
+    bool bulk_ok = true;
+    const llgb_status st = plan_side_part(v, 0, 0, tile, ntiles, S, img, bulk_ok, why);
+    if (st != LLGB_OK) return st;
     if (img > 0xFFFFFFFFull) {
         *why = "tile image too large";
         return LLGB_ERR_INVALID_ARG;
@@ -462,6 +581,8 @@ static llgb_status plan_side(const ViewPlan& v, const std::vector<void*>& ptrs, 
     S->bulk_ok = bulk_ok ? 1 : 0;
     return LLGB_OK;
 }
+
+
 
 static bool fmt_is(int e, int m, int fe, int fm) { return e == fe && m == fm; }
 
@@ -568,30 +689,42 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
     st = plan_side(dst, dst_ptrs, tile, job->ntiles, &job->dst, why);
     if (st != LLGB_OK) return st;
 
-    // Gaps between SoA single-blob sub-arrays belong to no leaf: zero them.
-    if (dst.base == BASE_SOA_SB) {
-        for (size_t g = 1; g < dst.stored.size(); ++g) {
-            const uint64_t from = dst.seg_end[g - 1], to = dst.sb_base[g];
+    // Gaps between SoA single-blob sub-arrays belong to no leaf: zero them
+    // (in every SoA single-blob part of a Split destination).
+    std::function<bool(const ViewPlan&, int)> add_gaps = [&](const ViewPlan& v, int blob0) -> bool {
+        if (v.base == BASE_SPLIT) {
+            for (size_t k = 0; k < v.parts.size(); ++k)
+                if (!v.part_null[k] && !add_gaps(v.parts[k], blob0 + v.part_blob0[k])) return false;
+            return true;
+        }
+        if (v.base != BASE_SOA_SB) return true;
+        for (size_t g = 1; g < v.stored.size(); ++g) {
+            const uint64_t from = v.seg_end[g - 1], to = v.sb_base[g];
             if (to <= from) continue;
-            if (job->nzeros >= kMaxZeros || to - from > 0xFFFFFFFFull) {
-                *why = "too many or too large sub-array gaps";
-                return LLGB_ERR_UNSUPPORTED;
-            }
+            if (job->nzeros >= kMaxZeros || to - from > 0xFFFFFFFFull) return false;
             ZeroRun& z = job->zeros[job->nzeros++];
             z.offset = from;
             z.bytes = (uint32_t)(to - from);
-            z.blob = 0;
+            z.blob = (uint32_t)blob0;
         }
+        return true;
+    };
+    if (!add_gaps(dst, 0)) {
+        *why = "too many or too large sub-array gaps";
+        return LLGB_ERR_UNSUPPORTED;
     }
 
     // Bit-stream destination leaves (whether a generic item ORs into one is
     // known once the items exist, below).
+    int8_t pack_of[kMaxLeaves];
+    for (int g = 0; g < kMaxLeaves; ++g) pack_of[g] = -1;
     for (int g = 0; g < (int)dst.stored.size(); ++g) {
-        if (dst.base < BASE_BITS_INT) break;
+        if (job->dst.leaves[g].kind != LEAF_BITS) continue;
         if (job->npacks >= kMaxPacks) {
             *why = "more than 16 bit-packed leaves";
             return LLGB_ERR_UNSUPPORTED;
         }
+        pack_of[g] = (int8_t)job->npacks;
         PackDesc& P = job->packs[job->npacks++];
         P.bits = (uint8_t)dst.stored[g].bits;
         P.dst_sbase = job->dst.leaves[g].sbase;
@@ -614,6 +747,7 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
     for (int f = 0; f < nf; ++f) {
         const Recipe a = src.recipes[f], b = dst.recipes[f];
         const int32_t t = src.types[f];
+        if (b.op == L_NULL) continue;  // the destination stores nothing (Null)
         const int size = type_size(t);
         const bool a_bytes = a.op == L_DIRECT || a.op == L_SPLIT;
         const bool b_bytes = b.op == L_DIRECT || b.op == L_SPLIT;
@@ -719,7 +853,7 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
     for (int k = 0; k < job->nitems; ++k) {
         const ItemDesc& it = job->items[k];
         if (it.op != ITEM_VALUE || (it.sop != S_BITS_INT && it.sop != S_BITS_FLOAT)) continue;
-        PackDesc& P = job->packs[it.dst_leaf];
+        PackDesc& P = job->packs[pack_of[it.dst_leaf]];
         P.ored = (it.fast == FK_GENERIC && !P.aligned) ? 1 : 0;
         job->ored |= P.ored;
     }

@@ -20,7 +20,9 @@ struct llgb_record {
 
 namespace llgb {
 
-enum BaseKind { BASE_AOS, BASE_SOA_SB, BASE_SOA_MB, BASE_AOSOA, BASE_BITS_INT, BASE_BITS_FLOAT };
+// BASE_SPLIT: a Split (or Null) view made of parts, each an ordinary plan
+// (or no storage at all).
+enum BaseKind { BASE_AOS, BASE_SOA_SB, BASE_SOA_MB, BASE_AOSOA, BASE_BITS_INT, BASE_BITS_FLOAT, BASE_SPLIT };
 enum WrapKind { WRAP_NONE, WRAP_CHANGETYPE, WRAP_BYTESPLIT };
 
 // How a logical leaf reaches its stored leaves.
@@ -55,6 +57,13 @@ struct ViewPlan {
     std::vector<uint64_t> seg_end;     // per stored leaf: end of its run region
     std::vector<int> leaf_blob;        // per stored leaf: blob index
     std::string sig;                   // mapping signature (record, wrapper, layout), no sizes
+    // BASE_SPLIT: the parts, each over the sub-record of part_fields[k] (in
+    // leaf order); a null part stores nothing.  Part k's stored leaves and
+    // blobs start at part_leaf0[k] / part_blob0[k] of this plan's.
+    std::vector<ViewPlan> parts;
+    std::vector<std::vector<int>> part_fields;
+    std::vector<bool> part_null;
+    std::vector<int> part_leaf0, part_blob0;
 };
 
 int type_size(int32_t t);

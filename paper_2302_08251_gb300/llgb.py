@@ -23,7 +23,7 @@ TYPE_SIZE = {"u8": 1, "u16": 2, "u32": 4, "u64": 8, "i8": 1, "i16": 2, "i32": 4,
              "i64": 8, "f16": 2, "bf16": 2, "f32": 4, "f64": 8}
 INDEX_TYPES = {"i16": 0, "u16": 1, "i32": 2, "u32": 3, "i64": 4, "u64": 5}
 KIND_ID = {"aos": 0, "soa_sb": 1, "soa_mb": 2, "aosoa": 3, "bitpack_int": 4,
-           "bitpack_float": 5, "bytesplit": 6, "changetype": 7}
+           "bitpack_float": 5, "bytesplit": 6, "changetype": 7, "null": 8, "split": 9}
 MAX_CT = 4
 
 OK = 0
@@ -61,6 +61,8 @@ MappingDesc._fields_ = [
     ("field_exp", ctypes.POINTER(ctypes.c_int32)),
     ("field_man", ctypes.POINTER(ctypes.c_int32)),
     ("inner", ctypes.POINTER(MappingDesc)),
+    ("split_mask", ctypes.c_uint64),
+    ("inner2", ctypes.POINTER(MappingDesc)),
 ]
 
 
@@ -177,6 +179,12 @@ def mapping_desc(m: dict, keep: list) -> MappingDesc:
         inner = mapping_desc(m["inner"], keep)
         keep.append(inner)
         c.inner = ctypes.pointer(inner)
+    if m["kind"] == "split":
+        # {"kind": "split", "fields": [leaf indices -> "inner"], "rest": mapping of the others}
+        c.split_mask = sum(1 << f for f in m["fields"])
+        rest = mapping_desc(m["rest"], keep)
+        keep.append(rest)
+        c.inner2 = ctypes.pointer(rest)
     return c
 
 

@@ -80,6 +80,11 @@ MAPPINGS = [
     {"kind": "bytesplit", "inner": {"kind": "aos", "packed": 1}},
     {"kind": "changetype", "ct": [("f64", "f32")], "inner": {"kind": "soa_mb"}},
     {"kind": "changetype", "ct": [("f64", "f32")], "inner": {"kind": "aos"}},
+    {"kind": "null"},
+    {"kind": "split", "fields": [0], "inner": {"kind": "soa_mb"}, "rest": {"kind": "aos"}},
+    {"kind": "split", "fields": [1, 2], "inner": {"kind": "null"}, "rest": {"kind": "aosoa", "lanes": 8}},
+    {"kind": "split", "fields": [0, 2], "inner": {"kind": "bytesplit", "inner": {"kind": "soa_mb"}},
+     "rest": {"kind": "split", "fields": [0], "inner": {"kind": "soa_sb"}, "rest": {"kind": "aos", "packed": 1}}},
 ]
 
 
@@ -222,3 +227,24 @@ def test_copy_with_rejects_an_unknown_engine():
     assert L.llgb_copy_with(hs[0], hs[1], ctypes.byref(c), None) == llgb.ERR_INVALID_ARG
     for h in hs:
         L.llgb_view_destroy(h)
+
+
+@pytest.mark.parametrize("bad", [
+    {"kind": "split", "fields": [], "inner": {"kind": "aos"}, "rest": {"kind": "aos"}},
+    {"kind": "split", "fields": [0, 1, 2, 3], "inner": {"kind": "aos"}, "rest": {"kind": "aos"}},
+    {"kind": "split", "fields": [9], "inner": {"kind": "aos"}, "rest": {"kind": "aos"}},
+])
+def test_split_needs_leaves_on_both_sides(bad):
+    with pytest.raises(llgb.LlgbError) as err:
+        host_view(synth.MIXED_F, bad, 10)
+    assert err.value.status == llgb.ERR_INVALID_ARG
+
+
+def test_split_of_bitpacked_integers_and_plain_floats_plans():
+    # reading (15)'s alternative: integer leaves bit-packed, float leaves SoA
+    rec = [("x", "f32"), ("n", "u32"), ("y", "f32"), ("k", "i32")]
+    m = {"kind": "split", "fields": [1, 3], "inner": {"kind": "bitpack_int", "bits": 12},
+         "rest": {"kind": "soa_mb"}}
+    _, sizes = host_view(rec, m, 1000)
+    assert sizes == oracle.OracleView(rec, m, 1000).blob_sizes == [1500, 1500, 4000, 4000]
+
