@@ -104,6 +104,7 @@ def _load():
         lib.orc_convert_n.argtypes = [p, p, u64, i32, i32, i32, i32]
         lib.orc_nbody_step.argtypes = [PM, u64, PB, ctypes.c_double,
                                        ctypes.c_double, u64, u64, p, p]
+        lib.orc_nbody_move.argtypes = [PM, u64, PB, ctypes.c_double, u64, u64, p]
         lib.orc_nbody_access_counts.argtypes = [u64, u64, p]
         lib.orc_nbody_heatmap.argtypes = [PM, u64, u64, u64, p]
         _lib = lib
@@ -236,6 +237,17 @@ class OracleView:
                                  float(eps), float(dt), i0, i1,
                                  pos.ctypes.data, vel.ctypes.data)
         return pos, vel
+
+    def nbody_move(self, dt: float, i0: int = 0, i1: int | None = None):
+        """FP64 move phase alone (p + dt v); returns pos of shape (i1-i0, 3)."""
+        if self.types != ["f32"] * 7:
+            raise ValueError("n-body needs the 7-leaf f32 particle record")
+        if i1 is None:
+            i1 = self.n
+        pos = np.zeros((i1 - i0, 3), dtype=np.float64)
+        self._lib.orc_nbody_move(ctypes.byref(self._map_c), self.n, self._ptrs, float(dt), i0, i1,
+                                 pos.ctypes.data)
+        return pos
 
 
 def nbody_access_counts(n: int, block: int = 64) -> np.ndarray:

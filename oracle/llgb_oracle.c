@@ -710,6 +710,19 @@ void orc_nbody_step(const orc_mapping* m, uint64_t n, uint8_t* const* blobs,
     free(mass);
 }
 
+void orc_nbody_move(const orc_mapping* m, uint64_t n, uint8_t* const* blobs,
+                    double dt, uint64_t i0, uint64_t i1, double* pos_out)
+{
+    static const int32_t types[7] = {ORC_F32, ORC_F32, ORC_F32, ORC_F32,
+                                     ORC_F32, ORC_F32, ORC_F32};
+    for (uint64_t i = i0; i < i1; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const double p = f32_bits_to_double(orc_load(types, 7, m, n, blobs, i, k));
+            const double v = f32_bits_to_double(orc_load(types, 7, m, n, blobs, i, 3 + k));
+            pos_out[3 * (i - i0) + k] = p + dt * v;
+        }
+}
+
 /* ------------------------------------------- access instrumentation -- */
 
 void orc_nbody_access_counts(uint64_t n, uint64_t block, uint64_t* counts)

@@ -17,7 +17,7 @@
  *     through the source mapping and stored through the destination mapping;
  *     every destination byte that no field owns is zero;
  *   - one all-pairs n-body step (Sec. 5, Fig. 2) in double precision, reading
- *     the particle records through a mapping.
+ *     the particle records through a mapping, and its move phase alone.
  *
  * Values cross the API as uint64_t holding the little-endian bit pattern of
  * the field's own type, zero-extended to 64 bits.
@@ -130,6 +130,13 @@ uint64_t orc_convert(uint64_t bits, int32_t src_e, int32_t src_m,
 void orc_nbody_step(const orc_mapping* m, uint64_t n, uint8_t* const* blobs,
                     double eps, double dt, uint64_t i0, uint64_t i1,
                     double* pos_out, double* vel_out);
+
+/* The move phase alone (Sec. 5): p_i + dt v_i in double precision for the
+ * records [i0, i1), from the f32 pos and vel leaves the view holds; written
+ * as doubles (3 per record, record-major) to pos_out.  The view is not
+ * modified. */
+void orc_nbody_move(const orc_mapping* m, uint64_t n, uint8_t* const* blobs,
+                    double dt, uint64_t i0, uint64_t i1, double* pos_out);
 
 /* Access instrumentation (Sec. 4, "Memory access instrumentation"):
  * FieldAccessCount counts the accesses per record field (reads and writes

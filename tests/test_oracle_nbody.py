@@ -188,3 +188,35 @@ def test_heatmap_per_element_counts_agree_across_mappings():
            for m in MAPS]
     for p in per[1:]:
         assert np.array_equal(p, per[0])
+
+
+# ---- the move phase alone (Sec. 5): p + dt v ----
+
+def test_move_worked_example_uses_leaves_0_to_5():
+    # distinct values in every leaf: a wrong leaf index or sign shows
+    f = particles_from([1.0, 2.0, 3.0], [0.5, -1.0, 4.0], [7.0])
+    v = oracle_view(synth.PARTICLE, {"kind": "aos"}, f)
+    assert np.array_equal(v.nbody_move(0.25), [[1.125, 1.75, 4.0]])
+    assert np.array_equal(v.nbody_move(0.0), [[1.0, 2.0, 3.0]])
+
+
+def test_move_is_the_step_when_no_mass_pulls():
+    # massless particles feel no force, so the step's move is the move alone
+    n = 40
+    f = synth.particles(n, seed=31)
+    f[6] = np.zeros(n, np.float32)
+    v = oracle_view(synth.PARTICLE, {"kind": "soa_mb"}, f)
+    pos, vel = v.nbody_step(EPS, DT)
+    assert np.array_equal(vel, np.stack(f[3:6], axis=1).astype(np.float64))
+    assert np.array_equal(pos, v.nbody_move(DT))
+
+
+@pytest.mark.parametrize("mapping", AFFINE + [{"kind": "aosoa", "lanes": 3}, {"kind": "aosoa", "lanes": 48}],
+                         ids=str)
+def test_move_does_not_depend_on_the_mapping(mapping):
+    n = 101
+    f = synth.particles(n, seed=4)
+    ref = oracle_view(synth.PARTICLE, {"kind": "soa_mb"}, f).nbody_move(DT)
+    v = oracle_view(synth.PARTICLE, mapping, f)
+    assert np.array_equal(v.nbody_move(DT), ref)
+    assert np.array_equal(v.nbody_move(DT, 50, 99), ref[50:99])
