@@ -466,10 +466,66 @@ def nbody_bench(device, args):
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
     best = max(x["TFLOP/s"] for x in out.values())
     instrumented = nbody_instrumentation_bench(device, base, rec, n, args)
+    traversal = nbody_traversal_bench(device, base, rec, n)
     return {"n": n, "flop_per_interaction": 20, "views": out, "instrumented": instrumented,
+            "traversal": traversal,
             "roofline": {"bound": "alu", "achieved": best, "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(best / peak, 4),
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz (nominal)"}}
+
+
+TRAVERSAL_VIEWS = [("AoS", {"kind": "aos"}), ("SoA", {"kind": "soa_mb"}),
+                   ("AoSoA8", {"kind": "aosoa", "lanes": 8}), ("AoSoA32", {"kind": "aosoa", "lanes": 32}),
+                   ("AoSoA48", {"kind": "aosoa", "lanes": 48}), ("AoSoA3", {"kind": "aosoa", "lanes": 3})]
+
+
+def nbody_traversal_bench(device, base, rec, n_update, n_move=1 << 26):
+    """Index against blocks traversal (Sec. 5): the move phase alone on 2^26
+    particles (1.9 GB views, larger than L2; algorithmic bytes 36 per
+    particle: pos and vel read, pos written) and the update phase alone on
+    the 65,536-particle system, per mapping."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, synth
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    move = {}
+    fields = synth.device_fields("particle", n_move, 19, device=device)
+    big = llgb.View(rec, {"kind": "soa_mb"}, (n_move,), blobs=[f.view(torch.uint8) for f in fields])
+    for name, m in TRAVERSAL_VIEWS:
+        v = llgb.View(rec, m, (n_move,))
+        llgb.llgb_copy(big, v)
+        row = {}
+        for trav in ("index", "blocks"):
+            ms = timed(lambda: llgb.llgb_nbody_move(v, 1e-4, trav), 10)
+            g = 36.0 * n_move / (ms * 1e-3) / 1e9
+            row[trav] = {"ms": round(ms, 4), "GB/s": round(g, 1), "frac": round(g / hbm, 4)}
+        move[name] = row
+        del v
+        torch.cuda.empty_cache()
+    del big, fields
+    torch.cuda.empty_cache()
+    update = {}
+    for name, m in TRAVERSAL_VIEWS:
+        v = llgb.View(rec, m, (n_update,))
+        llgb.llgb_copy(base, v)
+        update[name] = {trav: {"ms": round(timed(lambda: llgb.llgb_nbody_update(v, 0.01, 1e-4, trav), 5), 4)}
+                        for trav in ("index", "blocks")}
+    return {"move": {"n": n_move, "bytes_per_particle": 36, "views": move},
+            "update": {"n": n_update, "views": update}}
 
 
 def nbody_instrumentation_bench(device, base, rec, n, args):

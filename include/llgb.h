@@ -316,12 +316,39 @@ llgb_status llgb_autotune_clear(void);
 
 /* One all-pairs n-body step (Sec. 5, Fig. 2) on a view whose record is the
  * particle {pos.x, pos.y, pos.z, vel.x, vel.y, vel.z, mass} (7 f32 leaves, in
- * this order) under an AOS, SOA_SB, SOA_MB or AOSOA mapping.  Update: for
+ * this order) under an AOS, SOA_SB, SOA_MB or AOSOA mapping (any lane
+ * count).  Update: for
  * every i, v_i += dt * sum_j m_j (p_j - p_i) / (|p_j - p_i|^2 + eps^2)^(3/2),
  * j over all particles; then move: p_i += dt * v_i.  FP32 arithmetic; the
  * result bits do not depend on the mapping.  Queued on `stream` (two
  * kernels).  Errors: INVALID_ARG, UNBOUND, UNSUPPORTED, CUDA. */
 llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream);
+
+/* The two phases of llgb_nbody_step apart, each with a chosen traversal of
+ * the records (Sec. 5: the single loop over the flat index that a mapping-
+ * agnostic consumer writes, against loops nested the way the mapping lays
+ * records out, which the paper leaves open for AoSoA):
+ *   LLGB_TRAVERSE_INDEX: one thread per record index i; every access maps i
+ *       through the mapping (for AoSoA with L lanes, i / L and i % L).
+ *   LLGB_TRAVERSE_BLOCKS: the walk follows the layout.  Move: for AoSoA, one
+ *       AoSoA block after another, the block's 3 L pos floats updated as one
+ *       contiguous run from the 3 L vel floats after them (16-byte accesses
+ *       when L is a multiple of 4); for SoA, 4 consecutive records of each
+ *       leaf per thread (16-byte accesses when the leaf arrays are 16-byte
+ *       aligned); an AoS record is its own block.  Update: addresses advance
+ *       as a (block, lane) cursor, one division per thread instead of one per
+ *       access.
+ * Both traversals give the same result bits, and llgb_nbody_update followed
+ * by llgb_nbody_move gives the bits of llgb_nbody_step.  AoSoA views may have
+ * any lane count.  Errors: as llgb_nbody_step, plus INVALID_ARG (unknown
+ * traversal). */
+typedef enum llgb_traversal { LLGB_TRAVERSE_INDEX = 0, LLGB_TRAVERSE_BLOCKS = 1 } llgb_traversal;
+
+/* Update only: v_i += dt * sum_j m_j (p_j - p_i) / (|p_j - p_i|^2 + eps^2)^(3/2). */
+llgb_status llgb_nbody_update(llgb_view* particles, float eps, float dt, int32_t traversal, void* stream);
+
+/* Move only: p_i += dt * v_i (one fused multiply-add per leaf). */
+llgb_status llgb_nbody_move(llgb_view* particles, float dt, int32_t traversal, void* stream);
 
 /* --------------------------------------------- access instrumentation -- */
 

@@ -616,8 +616,10 @@ llgb_status llgb_unpack(const llgb_view* packed, llgb_view* plain, void* stream)
 namespace {
 
 // The particle view the n-body kernels read, plus for each leaf its blob and
-// the byte offset of its base in that blob (for heatmap counters).
-llgb_status particle_view(llgb_view* particles, ParticleView* v, int* kind, int* blob, uint64_t* boff)
+// the byte offset of its base in that blob (for heatmap counters).  *layout:
+// 0 AoS, 1 SoA, 2 AoSoA.
+llgb_status particle_view(llgb_view* particles, ParticleView* v, int* kind, int* blob, uint64_t* boff,
+                          int* layout = nullptr)
 {
     if (!particles) return fail(LLGB_ERR_INVALID_ARG, "null view");
     const ViewPlan& p = particles->plan;
@@ -626,16 +628,19 @@ llgb_status particle_view(llgb_view* particles, ParticleView* v, int* kind, int*
     if (p.wrap != WRAP_NONE || p.base == BASE_BITS_INT || p.base == BASE_BITS_FLOAT || p.base == BASE_SPLIT)
         return fail(LLGB_ERR_UNSUPPORTED, "n-body reads AoS, SoA or AoSoA views");
     if (!particles->bound) return fail(LLGB_ERR_UNBOUND, "view used before llgb_view_bind");
-    if (p.n > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs n < 2^32");
+    if (p.n > 0x7FFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs n < 2^31");
     *v = ParticleView{};
     v->n = (uint32_t)p.n;
     *kind = PV_GENERIC;
+    int lay = 2;
     for (int f = 0; f < 7; ++f) blob[f] = 0;
     switch (p.base) {
     case BASE_AOS:  // 28-byte record, aligned and packed alike
         for (int f = 0; f < 7; ++f) boff[f] = 4u * f;
         v->bstride = 28;
+        v->lanes = 1;
         *kind = PV_AOS;
+        lay = 0;
         break;
     case BASE_SOA_MB:
         for (int f = 0; f < 7; ++f) {
@@ -643,25 +648,46 @@ llgb_status particle_view(llgb_view* particles, ParticleView* v, int* kind, int*
             boff[f] = 0;
         }
         v->bstride = 4;
+        v->lanes = 0xFFFFFFFFu;
         *kind = PV_SOA;
+        lay = 1;
         break;
     case BASE_SOA_SB:
         for (int f = 0; f < 7; ++f) boff[f] = p.sb_base[f];
         v->bstride = 4;
+        v->lanes = 0xFFFFFFFFu;
         *kind = PV_SOA;
+        lay = 1;
         break;
     default: {  // AoSoA
         const uint64_t L = p.lanes;
-        if (L & (L - 1)) return fail(LLGB_ERR_UNSUPPORTED, "n-body needs a power-of-two AoSoA lane count");
+        if (28 * L > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "AoSoA block too large for the n-body");
         for (int f = 0; f < 7; ++f) boff[f] = L * 4 * f;
         v->bstride = (uint32_t)(28 * L);
-        v->lmask = (uint32_t)(L - 1);
-        while ((1ull << v->lshift) < L) ++v->lshift;
-        *kind = L == 32 ? PV_AOSOA32 : PV_GENERIC;
+        v->lanes = (uint32_t)L;
+        if (L & (L - 1)) {
+            *kind = PV_DIV;
+        } else {
+            v->lmask = (uint32_t)(L - 1);
+            while ((1ull << v->lshift) < L) ++v->lshift;
+            *kind = L == 32 ? PV_AOSOA32 : PV_GENERIC;
+        }
         break;
     }
     }
+    // (block, lane) cursor steps of 32 records
+    if (lay == 1) {
+        v->step_lanes = 32;
+        v->step_off = 128;
+        v->wrap_off = 0;
+    } else {
+        const uint64_t L = v->lanes;
+        v->step_lanes = (uint32_t)(32 % L);
+        v->step_off = (32 / L) * v->bstride + (32 % L) * 4;
+        v->wrap_off = v->bstride - 4 * L;
+    }
     for (int f = 0; f < 7; ++f) v->base[f] = static_cast<uint8_t*>(particles->ptrs[blob[f]]) + boff[f];
+    if (layout) *layout = lay;
     return LLGB_OK;
 }
 
@@ -681,12 +707,40 @@ extern "C" {
 llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream)
 {
     ParticleView v;
+    int kind = 0, layout = 0, blob[7];
+    uint64_t boff[7];
+    const llgb_status st = particle_view(particles, &v, &kind, blob, boff, &layout);
+    if (st != LLGB_OK) return st;
+    const cudaError_t e = launch_nbody(v, kind, layout, eps, dt, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
+    return LLGB_OK;
+}
+
+llgb_status llgb_nbody_update(llgb_view* particles, float eps, float dt, int32_t traversal, void* stream)
+{
+    if (traversal != LLGB_TRAVERSE_INDEX && traversal != LLGB_TRAVERSE_BLOCKS)
+        return fail(LLGB_ERR_INVALID_ARG, "unknown traversal");
+    ParticleView v;
     int kind = 0, blob[7];
     uint64_t boff[7];
     const llgb_status st = particle_view(particles, &v, &kind, blob, boff);
     if (st != LLGB_OK) return st;
-    const cudaError_t e = launch_nbody(v, kind, eps, dt, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
+    const cudaError_t e = launch_nbody_update(v, kind, traversal, eps, dt, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "n-body update launch");
+    return LLGB_OK;
+}
+
+llgb_status llgb_nbody_move(llgb_view* particles, float dt, int32_t traversal, void* stream)
+{
+    if (traversal != LLGB_TRAVERSE_INDEX && traversal != LLGB_TRAVERSE_BLOCKS)
+        return fail(LLGB_ERR_INVALID_ARG, "unknown traversal");
+    ParticleView v;
+    int kind = 0, layout = 0, blob[7];
+    uint64_t boff[7];
+    const llgb_status st = particle_view(particles, &v, &kind, blob, boff, &layout);
+    if (st != LLGB_OK) return st;
+    const cudaError_t e = launch_nbody_move(v, kind, layout, traversal, dt, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "n-body move launch");
     return LLGB_OK;
 }
 
@@ -727,7 +781,7 @@ llgb_status llgb_nbody_step_instrumented(llgb_view* particles, float eps, float 
             in.hstart[f] = start[blob[f]];
         }
     }
-    const cudaError_t e = launch_nbody_instrumented(v, in, eps, dt, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = launch_nbody_instrumented(v, kind == PV_DIV, in, eps, dt, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "n-body launch");
     return LLGB_OK;
 }

@@ -8,6 +8,13 @@
 // or multi blob, AoSoA with a power-of-two lane count); the arithmetic does not
 // depend on the mapping, so every mapping gives the same bits.
 //
+// Two traversals of the records (the paper leaves mapping-aware loops open
+// in Sec. 5): the index traversal maps each record index through the mapping
+// on every access; the blocks traversal follows the layout -- in the move, an
+// AoSoA block's pos leaves are one run of 3 L floats updated from the vel run
+// after it, and SoA leaves are walked four records per thread, in 16-byte
+// accesses; in the update, addresses advance as (block, lane) cursors.
+//
 // Each block owns kI particles and splits the j range into kParts equal
 // slices, one warp each; a slice streams kJ-particle tiles through shared
 // memory.  The tile is a view with compile-time extents (Sec. 2: stateless
@@ -30,9 +37,45 @@ struct Addr {
         if (KIND == PV_AOS) return (uint64_t)i * 28u;
         if (KIND == PV_SOA) return (uint64_t)i * 4u;
         if (KIND == PV_AOSOA32) return (uint64_t)(i >> 5) * (32u * 28u) + (i & 31u) * 4u;
+        if (KIND == PV_DIV) {
+            const uint32_t b = i / v.lanes;
+            return (uint64_t)b * v.bstride + (uint64_t)(i - b * v.lanes) * 4u;
+        }
         return (uint64_t)(i >> v.lshift) * v.bstride + (uint64_t)(i & v.lmask) * 4u;
     }
 };
+
+// The blocks traversal's address: a (block, lane) cursor.  Placing it costs
+// one division; moving it 32 records on costs an add and a compare.
+struct Cursor {
+    uint64_t off;
+    uint32_t lane;
+    __device__ __forceinline__ void at(const ParticleView& v, uint32_t i)
+    {
+        const uint32_t b = i / v.lanes;
+        lane = i - b * v.lanes;
+        off = (uint64_t)b * v.bstride + (uint64_t)lane * 4u;
+    }
+    __device__ __forceinline__ void next32(const ParticleView& v)
+    {
+        lane += v.step_lanes;
+        off += v.step_off;
+        if (lane >= v.lanes) {
+            lane -= v.lanes;
+            off += v.wrap_off;
+        }
+    }
+};
+
+__device__ __forceinline__ float ld_at(const ParticleView& v, int f, uint64_t off)
+{
+    return *reinterpret_cast<const float*>(v.base[f] + off);
+}
+
+__device__ __forceinline__ void st_at(const ParticleView& v, int f, uint64_t off, float x)
+{
+    *reinterpret_cast<float*>(v.base[f] + off) = x;
+}
 
 template <int KIND>
 __device__ __forceinline__ float ld_leaf(const ParticleView& v, int f, uint32_t i)
@@ -123,10 +166,13 @@ __device__ __forceinline__ void interact(const float4 b, float px, float py, flo
 // One warp per j slice: it stages kJ-record tiles of its slice with warp-
 // level synchronisation only, and every lane interacts two particles (i and
 // i + 32) with each staged record.
-template <int KIND, int CM = 0, bool HEAT = false>
+// TRAV = TRAVERSE_INDEX maps every access's record index through the
+// mapping; TRAVERSE_BLOCKS walks (block, lane) cursors (uninstrumented only).
+template <int KIND, int CM = 0, bool HEAT = false, int TRAV = TRAVERSE_INDEX>
 __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v, float eps2, float dt,
                                                             uint32_t chunk, const NbodyInstr in)
 {
+    static_assert(TRAV == TRAVERSE_INDEX || (CM == 0 && !HEAT), "instrumented steps use the index traversal");
     __shared__ StaticBodyTile<kJ> tile[kParts];
     __shared__ float3 partial[kParts][kI];
     __shared__ unsigned long long bc[14];
@@ -136,19 +182,39 @@ __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v
     const uint32_t n = v.n;
     block_counts_init<CM>(bc);
     if (CM == 2) __syncthreads();
+    // record i (cursor c in the blocks traversal), leaf f
+    auto ld = [&](int f, uint32_t i, const Cursor& c) -> float {
+        if constexpr (TRAV == TRAVERSE_BLOCKS) return ld_at(v, f, c.off);
+        else return ld_i<KIND, CM, HEAT>(v, in, bc, f, i);
+    };
+    auto st = [&](int f, uint32_t i, const Cursor& c, float x) {
+        if constexpr (TRAV == TRAVERSE_BLOCKS) st_at(v, f, c.off, x);
+        else st_i<KIND, CM, HEAT>(v, in, bc, f, i, x);
+    };
+    // cursors of the block's own records (placed again after the j loop, so
+    // that they hold no registers through it)
+    Cursor own[kIPT] = {};
+    auto place_own = [&]() {
+        if constexpr (TRAV == TRAVERSE_BLOCKS) {
+            own[0].at(v, i0);
+            own[1] = own[0];
+            own[1].next32(v);
+        }
+    };
+    if (part == 0) place_own();
 
     // the block's own particles are read by slice 0 only (once each)
     float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
     if (part == 0) {
         if (i0 < n) {
-            p0x = ld_i<KIND, CM, HEAT>(v, in, bc, 0, i0);
-            p0y = ld_i<KIND, CM, HEAT>(v, in, bc, 1, i0);
-            p0z = ld_i<KIND, CM, HEAT>(v, in, bc, 2, i0);
+            p0x = ld(0, i0, own[0]);
+            p0y = ld(1, i0, own[0]);
+            p0z = ld(2, i0, own[0]);
         }
         if (i1 < n) {
-            p1x = ld_i<KIND, CM, HEAT>(v, in, bc, 0, i1);
-            p1y = ld_i<KIND, CM, HEAT>(v, in, bc, 1, i1);
-            p1z = ld_i<KIND, CM, HEAT>(v, in, bc, 2, i1);
+            p1x = ld(0, i1, own[1]);
+            p1y = ld(1, i1, own[1]);
+            p1z = ld(2, i1, own[1]);
         }
         partial[0][lane] = make_float3(p0x, p0y, p0z);
         partial[0][lane + kW] = make_float3(p1x, p1y, p1z);
@@ -162,16 +228,17 @@ __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v
     __syncthreads();
     float a0x = 0.f, a0y = 0.f, a0z = 0.f, a1x = 0.f, a1y = 0.f, a1z = 0.f;
     const uint32_t j0 = part * chunk;
+    Cursor cj = {};
+    if constexpr (TRAV == TRAVERSE_BLOCKS) cj.at(v, j0 + lane);
     for (uint32_t jt = 0; jt < chunk; jt += kJ) {
 #pragma unroll
         for (int r = 0; r < kJ / kW; ++r) {
             const uint32_t jl = jt + lane + r * kW;
             const uint32_t j = j0 + jl;
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);  // zero mass beyond n
-            if (j < n && jl < chunk)
-                q = make_float4(ld_i<KIND, CM, HEAT>(v, in, bc, 0, j), ld_i<KIND, CM, HEAT>(v, in, bc, 1, j),
-                                ld_i<KIND, CM, HEAT>(v, in, bc, 2, j), ld_i<KIND, CM, HEAT>(v, in, bc, 6, j));
+            if (j < n && jl < chunk) q = make_float4(ld(0, j, cj), ld(1, j, cj), ld(2, j, cj), ld(6, j, cj));
             tile[part](lane + r * kW) = q;
+            if constexpr (TRAV == TRAVERSE_BLOCKS) cj.next32(v);
         }
         __syncwarp();
         float t0x = 0.f, t0y = 0.f, t0z = 0.f, t1x = 0.f, t1y = 0.f, t1z = 0.f;
@@ -194,6 +261,7 @@ __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v
     __syncthreads();
     // warp 0 adds the slices in a fixed order, one particle per lane and pass
     if (part == 0) {
+        place_own();
 #pragma unroll
         for (int h = 0; h < kIPT; ++h) {
             const uint32_t li = lane + h * kW;
@@ -206,9 +274,9 @@ __global__ void __launch_bounds__(kW * kParts) nbody_update(const ParticleView v
                 sy += partial[p][li].y;
                 sz += partial[p][li].z;
             }
-            st_i<KIND, CM, HEAT>(v, in, bc, 3, i, fmaf(dt, sx, ld_i<KIND, CM, HEAT>(v, in, bc, 3, i)));
-            st_i<KIND, CM, HEAT>(v, in, bc, 4, i, fmaf(dt, sy, ld_i<KIND, CM, HEAT>(v, in, bc, 4, i)));
-            st_i<KIND, CM, HEAT>(v, in, bc, 5, i, fmaf(dt, sz, ld_i<KIND, CM, HEAT>(v, in, bc, 5, i)));
+            st(3, i, own[h], fmaf(dt, sx, ld(3, i, own[h])));
+            st(4, i, own[h], fmaf(dt, sy, ld(4, i, own[h])));
+            st(5, i, own[h], fmaf(dt, sz, ld(5, i, own[h])));
         }
     }
     if (CM == 2) {
@@ -237,45 +305,191 @@ __global__ void nbody_move(const ParticleView v, float dt, const NbodyInstr in)
     }
 }
 
-template <int KIND, int CM = 0, bool HEAT = false>
-static cudaError_t launch_kind(const ParticleView& v, float eps, float dt, cudaStream_t stream,
-                               const NbodyInstr& in = NbodyInstr{})
+// The blocks traversal of the move on SoA: four consecutive records of every
+// leaf per thread, as 16-byte accesses when VEC (all six leaf arrays 16-byte
+// aligned).
+template <bool VEC>
+__global__ void __launch_bounds__(256) nbody_move_soa(const ParticleView v, float dt)
+{
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = 4u * q;
+    if (i >= v.n) return;
+    if (VEC && i + 4u <= v.n) {
+        float4 p[3], w[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            p[k] = reinterpret_cast<const float4*>(v.base[k])[q];
+            w[k] = reinterpret_cast<const float4*>(v.base[3 + k])[q];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            p[k].x = fmaf(dt, w[k].x, p[k].x);
+            p[k].y = fmaf(dt, w[k].y, p[k].y);
+            p[k].z = fmaf(dt, w[k].z, p[k].z);
+            p[k].w = fmaf(dt, w[k].w, p[k].w);
+            reinterpret_cast<float4*>(v.base[k])[q] = p[k];
+        }
+        return;
+    }
+    const uint32_t e = min(i + 4u, v.n);
+    for (uint32_t r = i; r < e; ++r)
+        for (int k = 0; k < 3; ++k) {
+            float* pk = reinterpret_cast<float*>(v.base[k]) + r;
+            *pk = fmaf(dt, reinterpret_cast<const float*>(v.base[3 + k])[r], *pk);
+        }
+}
+
+// The blocks traversal of the move on AoSoA with L lanes: thread row y of a
+// CTA owns AoSoA block b; the block's pos leaves are one run of 3 L floats
+// and its vel leaves the next 3 L, element for element, so the row updates
+// the run in units (16-byte quads when VEC, i.e. L % 4 == 0; floats
+// otherwise).  The last block holds n - full * L < L records; only its used
+// lanes are touched.
+template <bool VEC>
+__global__ void __launch_bounds__(256) nbody_move_aosoa(const ParticleView v, float dt, uint32_t full)
+{
+    const uint32_t L = v.lanes;
+    const uint32_t b = blockIdx.x * blockDim.y + threadIdx.y;
+    uint8_t* const P = v.base[0] + (uint64_t)b * v.bstride;
+    const uint32_t vel = 12u * L;  // bytes from the pos run to the vel run
+    if (b < full) {
+        if (VEC) {
+            for (uint32_t u = threadIdx.x; u < 3u * L / 4u; u += blockDim.x) {
+                float4 p = *reinterpret_cast<const float4*>(P + 16u * u);
+                const float4 w = *reinterpret_cast<const float4*>(P + vel + 16u * u);
+                p.x = fmaf(dt, w.x, p.x);
+                p.y = fmaf(dt, w.y, p.y);
+                p.z = fmaf(dt, w.z, p.z);
+                p.w = fmaf(dt, w.w, p.w);
+                *reinterpret_cast<float4*>(P + 16u * u) = p;
+            }
+        } else {
+            for (uint32_t u = threadIdx.x; u < 3u * L; u += blockDim.x) {
+                float* p = reinterpret_cast<float*>(P + 4u * u);
+                *p = fmaf(dt, *reinterpret_cast<const float*>(P + vel + 4u * u), *p);
+            }
+        }
+    } else if (b == full) {
+        const uint32_t used = v.n - full * L;
+        for (uint32_t u = threadIdx.x; u < 3u * L; u += blockDim.x) {
+            if (u % L >= used) continue;
+            float* p = reinterpret_cast<float*>(P + 4u * u);
+            *p = fmaf(dt, *reinterpret_cast<const float*>(P + vel + 4u * u), *p);
+        }
+    }
+}
+
+template <int KIND, int CM = 0, bool HEAT = false, int TRAV = TRAVERSE_INDEX>
+static cudaError_t launch_update(const ParticleView& v, float eps, float dt, cudaStream_t stream,
+                                 const NbodyInstr& in = NbodyInstr{})
 {
     const uint32_t n = v.n;
     uint32_t chunk = (n + kParts - 1) / kParts;
     chunk = (chunk + kJ - 1) / kJ * kJ;
     const uint32_t blocks = (n + kI - 1) / kI;
-    nbody_update<KIND, CM, HEAT><<<blocks, kW * kParts, 0, stream>>>(v, eps * eps, dt, chunk, in);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    nbody_move<KIND, CM, HEAT><<<(n + 255) / 256, 256, 0, stream>>>(v, dt, in);
+    nbody_update<KIND, CM, HEAT, TRAV><<<blocks, kW * kParts, 0, stream>>>(v, eps * eps, dt, chunk, in);
     return cudaGetLastError();
+}
+
+template <int KIND, int CM = 0, bool HEAT = false>
+static cudaError_t launch_move(const ParticleView& v, float dt, cudaStream_t stream,
+                               const NbodyInstr& in = NbodyInstr{})
+{
+    nbody_move<KIND, CM, HEAT><<<(v.n + 255) / 256, 256, 0, stream>>>(v, dt, in);
+    return cudaGetLastError();
+}
+
+template <int KIND, int CM = 0, bool HEAT = false>
+static cudaError_t launch_kind(const ParticleView& v, float eps, float dt, cudaStream_t stream,
+                               const NbodyInstr& in = NbodyInstr{})
+{
+    const cudaError_t e = launch_update<KIND, CM, HEAT>(v, eps, dt, stream, in);
+    if (e != cudaSuccess) return e;
+    return launch_move<KIND, CM, HEAT>(v, dt, stream, in);
 }
 
 // Instrumented steps use the runtime address function; the arithmetic, and
 // so every result bit, is the plain step's.
-cudaError_t launch_nbody_instrumented(const ParticleView& v, const NbodyInstr& in, float eps, float dt,
+template <int KIND>
+static cudaError_t launch_instrumented(const ParticleView& v, const NbodyInstr& in, float eps, float dt,
+                                       cudaStream_t stream)
+{
+    const bool heat = in.heat != nullptr;
+    const int cm = in.counts ? in.count_mode : 0;
+    if (cm == 1) return heat ? launch_kind<KIND, 1, true>(v, eps, dt, stream, in)
+                             : launch_kind<KIND, 1, false>(v, eps, dt, stream, in);
+    if (cm == 2) return heat ? launch_kind<KIND, 2, true>(v, eps, dt, stream, in)
+                             : launch_kind<KIND, 2, false>(v, eps, dt, stream, in);
+    return heat ? launch_kind<KIND, 0, true>(v, eps, dt, stream, in)
+                : launch_kind<KIND, 0, false>(v, eps, dt, stream, in);
+}
+
+cudaError_t launch_nbody_instrumented(const ParticleView& v, bool div, const NbodyInstr& in, float eps, float dt,
                                       cudaStream_t stream)
 {
     if (v.n == 0) return cudaSuccess;
-    const bool heat = in.heat != nullptr;
-    const int cm = in.counts ? in.count_mode : 0;
-    if (cm == 1) return heat ? launch_kind<PV_GENERIC, 1, true>(v, eps, dt, stream, in)
-                             : launch_kind<PV_GENERIC, 1, false>(v, eps, dt, stream, in);
-    if (cm == 2) return heat ? launch_kind<PV_GENERIC, 2, true>(v, eps, dt, stream, in)
-                             : launch_kind<PV_GENERIC, 2, false>(v, eps, dt, stream, in);
-    return heat ? launch_kind<PV_GENERIC, 0, true>(v, eps, dt, stream, in)
-                : launch_kind<PV_GENERIC, 0, false>(v, eps, dt, stream, in);
+    return div ? launch_instrumented<PV_DIV>(v, in, eps, dt, stream)
+               : launch_instrumented<PV_GENERIC>(v, in, eps, dt, stream);
 }
 
-cudaError_t launch_nbody(const ParticleView& v, int kind, float eps, float dt, cudaStream_t stream)
+// The plain step: the update with the index traversal (within a few per cent
+// of the blocks traversal there, and fewer registers), the move with the
+// blocks traversal (the faster one for this memory-bound phase).
+cudaError_t launch_nbody(const ParticleView& v, int kind, int layout, float eps, float dt, cudaStream_t stream)
 {
     if (v.n == 0) return cudaSuccess;
+    const cudaError_t e = launch_nbody_update(v, kind, TRAVERSE_INDEX, eps, dt, stream);
+    if (e != cudaSuccess) return e;
+    return launch_nbody_move(v, kind, layout, TRAVERSE_BLOCKS, dt, stream);
+}
+
+cudaError_t launch_nbody_update(const ParticleView& v, int kind, int traversal, float eps, float dt,
+                                cudaStream_t stream)
+{
+    if (v.n == 0) return cudaSuccess;
+    if (traversal == TRAVERSE_BLOCKS) return launch_update<PV_GENERIC, 0, false, TRAVERSE_BLOCKS>(v, eps, dt, stream);
     switch (kind) {
-    case PV_AOS: return launch_kind<PV_AOS>(v, eps, dt, stream);
-    case PV_SOA: return launch_kind<PV_SOA>(v, eps, dt, stream);
-    case PV_AOSOA32: return launch_kind<PV_AOSOA32>(v, eps, dt, stream);
-    default: return launch_kind<PV_GENERIC>(v, eps, dt, stream);
+    case PV_AOS: return launch_update<PV_AOS>(v, eps, dt, stream);
+    case PV_SOA: return launch_update<PV_SOA>(v, eps, dt, stream);
+    case PV_AOSOA32: return launch_update<PV_AOSOA32>(v, eps, dt, stream);
+    case PV_DIV: return launch_update<PV_DIV>(v, eps, dt, stream);
+    default: return launch_update<PV_GENERIC>(v, eps, dt, stream);
+    }
+}
+
+cudaError_t launch_nbody_move(const ParticleView& v, int kind, int layout, int traversal, float dt,
+                              cudaStream_t stream)
+{
+    if (v.n == 0) return cudaSuccess;
+    if (traversal == TRAVERSE_BLOCKS && layout == 1) {
+        bool vec = true;
+        for (int f = 0; f < 6; ++f) vec = vec && (reinterpret_cast<uintptr_t>(v.base[f]) & 15u) == 0;
+        const uint32_t grid = (v.n + 1023u) / 1024u;  // 256 threads x 4 records
+        if (vec) nbody_move_soa<true><<<grid, 256, 0, stream>>>(v, dt);
+        else nbody_move_soa<false><<<grid, 256, 0, stream>>>(v, dt);
+        return cudaGetLastError();
+    }
+    if (traversal == TRAVERSE_BLOCKS && layout == 2) {
+        const uint32_t L = v.lanes;
+        const bool vec = L % 4u == 0 && (reinterpret_cast<uintptr_t>(v.base[0]) & 15u) == 0;
+        const uint32_t units = vec ? 3u * L / 4u : 3u * L;
+        const uint32_t bx = units < 256u ? units : 256u;
+        const uint32_t by = 256u / bx;
+        const uint32_t full = v.n / L;
+        const uint32_t blocks = full + (v.n % L ? 1u : 0u);
+        const dim3 block(bx, by);
+        const uint32_t grid = (blocks + by - 1) / by;
+        if (vec) nbody_move_aosoa<true><<<grid, block, 0, stream>>>(v, dt, full);
+        else nbody_move_aosoa<false><<<grid, block, 0, stream>>>(v, dt, full);
+        return cudaGetLastError();
+    }
+    // the index traversal; an AoS record is its own block, so AoS walks the same way in both
+    switch (kind) {
+    case PV_AOS: return launch_move<PV_AOS>(v, dt, stream);
+    case PV_SOA: return launch_move<PV_SOA>(v, dt, stream);
+    case PV_AOSOA32: return launch_move<PV_AOSOA32>(v, dt, stream);
+    case PV_DIV: return launch_move<PV_DIV>(v, dt, stream);
+    default: return launch_move<PV_GENERIC>(v, dt, stream);
     }
 }
 

@@ -83,7 +83,7 @@ class LaunchConfig(ctypes.Structure):
 EXPORTS = [
     "llgb_last_error", "llgb_version", "llgb_record_create", "llgb_record_destroy",
     "llgb_record_leaf_count", "llgb_record_size", "llgb_view_create", "llgb_view_destroy",
-    "llgb_nbody_step_instrumented", "llgb_heatmap_counters",
+    "llgb_nbody_step_instrumented", "llgb_heatmap_counters", "llgb_nbody_update", "llgb_nbody_move",
     "llgb_view_blob_count", "llgb_view_blob_size", "llgb_view_record_count",
     "llgb_view_bind", "llgb_copy", "llgb_pack", "llgb_unpack", "llgb_copy_config",
     "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
@@ -129,6 +129,8 @@ def lib():
         L.llgb_copy_with.argtypes = [p, p, ctypes.POINTER(LaunchConfig), p]
         L.llgb_nbody_step.argtypes = [p, ctypes.c_float, ctypes.c_float, p]
         L.llgb_nbody_step_instrumented.argtypes = [p, ctypes.c_float, ctypes.c_float, p, i32, p, u64, p]
+        L.llgb_nbody_update.argtypes = [p, ctypes.c_float, ctypes.c_float, i32, p]
+        L.llgb_nbody_move.argtypes = [p, ctypes.c_float, i32, p]
         L.llgb_heatmap_counters.argtypes = [p, u64, ctypes.POINTER(u64)]
         L.llgb_device_status.argtypes = [ctypes.POINTER(i32), i32]
         L.llgb_batch_create.argtypes = [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)]
@@ -318,6 +320,19 @@ def llgb_copy_with(src: View, dst: View, cfg: dict, stream=None) -> None:
 
 def llgb_nbody_step(view: View, eps: float, dt: float, stream=None) -> None:
     check(lib().llgb_nbody_step(view.handle, float(eps), float(dt), _stream_ptr(stream)))
+
+
+TRAVERSALS = {"index": 0, "blocks": 1}
+
+
+def llgb_nbody_update(view: View, eps: float, dt: float, traversal="index", stream=None) -> None:
+    """The update phase alone; traversal 'index' or 'blocks'."""
+    check(lib().llgb_nbody_update(view.handle, float(eps), float(dt), TRAVERSALS[traversal], _stream_ptr(stream)))
+
+
+def llgb_nbody_move(view: View, dt: float, traversal="index", stream=None) -> None:
+    """The move phase alone; traversal 'index' or 'blocks'."""
+    check(lib().llgb_nbody_move(view.handle, float(dt), TRAVERSALS[traversal], _stream_ptr(stream)))
 
 
 COUNT_MODES = {"atomic": 1, "block": 2}

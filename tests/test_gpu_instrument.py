@@ -14,7 +14,7 @@ from gpu_util import device_view_of, ensure_library, sync_and_check_status
 pytestmark = pytest.mark.gpu
 
 MAPS = [{"kind": "aos"}, {"kind": "soa_mb"}, {"kind": "soa_sb"}, {"kind": "aosoa", "lanes": 8},
-        {"kind": "aosoa", "lanes": 32}, {"kind": "aosoa", "lanes": 64}]
+        {"kind": "aosoa", "lanes": 32}, {"kind": "aosoa", "lanes": 64}, {"kind": "aosoa", "lanes": 48}]
 EPS, DT = 0.01, 1e-4
 
 
