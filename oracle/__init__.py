@@ -73,6 +73,7 @@ _Mapping._fields_ = [
     ("inner", ctypes.POINTER(_Mapping)),
     ("split_mask", ctypes.c_uint64),
     ("inner2", ctypes.POINTER(_Mapping)),
+    ("bit_lanes", ctypes.c_uint64),
 ]
 
 _lib = None
@@ -117,6 +118,8 @@ def _to_c_mapping(m: dict, keep: list) -> _Mapping:
     c.aos_packed = int(m.get("packed", 0))
     c.subarray_align = int(m.get("subarray_align", 0))
     c.lanes = int(m.get("lanes", 1))
+    if m["kind"] in ("bitpack_int", "bitpack_float"):
+        c.bit_lanes = int(m.get("lanes", 0))  # 0: SoA organisation
     c.bits = int(m.get("bits", 0))
     c.exp_bits = int(m.get("exp", 0))
     c.man_bits = int(m.get("man", 0))

@@ -139,6 +139,38 @@ static void leaf_float(const orc_mapping* m, int32_t f, int* e, int* man)
     *man = m->field_man ? m->field_man[f] : m->man_bits;
 }
 
+/* Width in bits of leaf f's code in a bit-packed mapping. */
+static int code_width(const orc_mapping* m, int32_t f)
+{
+    if (m->kind == ORC_BITPACK_INT) return leaf_bits(m, f);
+    int e = 0, man = 0;
+    leaf_float(m, f, &e, &man);
+    return 1 + e + man;
+}
+
+/* Where the code of leaf f of record i lies in a bit-packed mapping; returns
+ * the blob, *bit its first bit.  bit_lanes == 0 (Sec. 3, SoA): blob f holds
+ * leaf f's codes back to back.  bit_lanes == L: one blob of blocks of L
+ * records; with R the bits of one record's codes, block i / L starts at bit
+ * (i / L) L R and holds the L codes of leaf 0, then the L codes of leaf 1,
+ * and so on; record i is lane i % L of its block. */
+static int32_t bits_locate(int32_t nf, const orc_mapping* m, uint64_t i, int32_t f, uint64_t* bit)
+{
+    const uint64_t w = (uint64_t)code_width(m, f);
+    if (m->bit_lanes == 0) {
+        *bit = i * w;
+        return f;
+    }
+    uint64_t R = 0, prefix = 0;
+    for (int32_t g = 0; g < nf; ++g) {
+        if (g == f) prefix = R;
+        R += (uint64_t)code_width(m, g);
+    }
+    const uint64_t L = m->bit_lanes;
+    *bit = (i / L) * L * R + L * prefix + (i % L) * w;
+    return 0;
+}
+
 /* --------------------------------------------------------------- checks -- */
 
 int orc_check(const int32_t* types, int32_t nf, const orc_mapping* m)
@@ -321,8 +353,10 @@ int32_t orc_blob_count(const int32_t* types, int32_t nf, const orc_mapping* m)
     switch (m->kind) {
     case ORC_AOS: case ORC_SOA_SB: case ORC_AOSOA:
         return 1;
-    case ORC_SOA_MB: case ORC_BITPACK_INT: case ORC_BITPACK_FLOAT:
+    case ORC_SOA_MB:
         return nf;
+    case ORC_BITPACK_INT: case ORC_BITPACK_FLOAT:
+        return m->bit_lanes ? 1 : nf;
     case ORC_BYTESPLIT: case ORC_CHANGETYPE: {
         int32_t it[MAX_LEAVES];
         int ni = inner_types(types, nf, m, it);
@@ -357,16 +391,14 @@ uint64_t orc_blob_size(const int32_t* types, int32_t nf, const orc_mapping* m,
         return blocks * m->lanes * record_size(types, nf, 1);
     }
     case ORC_BITPACK_INT: case ORC_BITPACK_FLOAT: {
-        uint64_t w;
-        if (m->kind == ORC_BITPACK_INT) {
-            w = (uint64_t)leaf_bits(m, k);
-        } else {
-            int e, man;
-            leaf_float(m, k, &e, &man);
-            w = (uint64_t)(1 + e + man);
-        }
         /* whole 32-bit words; bits after the last value are zero */
-        return 4 * ((n * w + 31) / 32);
+        if (m->bit_lanes) {
+            uint64_t R = 0;
+            for (int32_t g = 0; g < nf; ++g) R += (uint64_t)code_width(m, g);
+            const uint64_t blocks = (n + m->bit_lanes - 1) / m->bit_lanes;
+            return 4 * ((blocks * m->bit_lanes * R + 31) / 32);
+        }
+        return 4 * ((n * (uint64_t)code_width(m, k) + 31) / 32);
     }
     case ORC_BYTESPLIT: case ORC_CHANGETYPE: {
         int32_t it[MAX_LEAVES];
@@ -500,7 +532,9 @@ uint64_t orc_load(const int32_t* types, int32_t nf, const orc_mapping* m, uint64
         /* Sec. 3: unpacked when loaded.  Signed leaves are sign-extended from
          * bit b-1 (reading of the paper, which gives no sign rule). */
         int w = leaf_bits(m, f);
-        uint64_t code = stream_get(blobs[f], i * (uint64_t)w, w);
+        uint64_t bit;
+        int32_t b = bits_locate(nf, m, i, f, &bit);
+        uint64_t code = stream_get(blobs[b], bit, w);
         if (is_signed_int(t) && ((code >> (w - 1)) & 1u)) code |= ~low_mask(w);
         return code & low_mask(8 * s);
     }
@@ -509,7 +543,9 @@ uint64_t orc_load(const int32_t* types, int32_t nf, const orc_mapping* m, uint64
         leaf_float(m, f, &e, &man);
         float_format(t, &te, &tm);
         int w = 1 + e + man;
-        uint64_t code = stream_get(blobs[f], i * (uint64_t)w, w);
+        uint64_t bit;
+        int32_t b = bits_locate(nf, m, i, f, &bit);
+        uint64_t code = stream_get(blobs[b], bit, w);
         return orc_convert(code, e, man, te, tm);
     }
     case ORC_BYTESPLIT: {
@@ -564,7 +600,9 @@ void orc_store(const int32_t* types, int32_t nf, const orc_mapping* m, uint64_t 
         /* Sec. 3: packed when stored: the low b bits of the two's-complement
          * value, i.e. v mod 2^b (wrap-around, no saturation). */
         int w = leaf_bits(m, f);
-        stream_put(blobs[f], i * (uint64_t)w, w, v & low_mask(w));
+        uint64_t bit;
+        int32_t b = bits_locate(nf, m, i, f, &bit);
+        stream_put(blobs[b], bit, w, v & low_mask(w));
         return;
     }
     case ORC_BITPACK_FLOAT: {
@@ -572,7 +610,9 @@ void orc_store(const int32_t* types, int32_t nf, const orc_mapping* m, uint64_t 
         leaf_float(m, f, &e, &man);
         float_format(t, &te, &tm);
         int w = 1 + e + man;
-        stream_put(blobs[f], i * (uint64_t)w, w, orc_convert(v, te, tm, e, man));
+        uint64_t bit;
+        int32_t b = bits_locate(nf, m, i, f, &bit);
+        stream_put(blobs[b], bit, w, orc_convert(v, te, tm, e, man));
         return;
     }
     case ORC_BYTESPLIT: {

@@ -11,7 +11,8 @@
  *   - a linear array of n records (extents are linearised row-major before
  *     they reach the oracle, Sec. 2);
  *   - the mappings AoS, SoA single/multi blob, AoSoA<L> (Sec. 5, Fig. 3 text),
- *     BitpackIntSoA and BitpackFloatSoA (Sec. 3), ChangeType (Sec. 3) and
+ *     BitpackIntSoA and BitpackFloatSoA (Sec. 3), also organised as AoSoA
+ *     (the generalisation Sec. 3 announces), ChangeType (Sec. 3) and
  *     Bytesplit (Sec. 3);
  *   - the layout-aware copy (Sec. 1): every field of every record is loaded
  *     through the source mapping and stored through the destination mapping;
@@ -73,6 +74,9 @@ typedef struct orc_mapping {
                                         mapping of the selected leaves            */
     uint64_t split_mask;         /* Split: bit f set = leaf f is selected          */
     const struct orc_mapping* inner2; /* Split: mapping of the other leaves        */
+    uint64_t bit_lanes;          /* Bitpack*: 0 = one stream per leaf (SoA);
+                                    L >= 1 = one blob of blocks of L records,
+                                    each leaf's L codes in turn (AoSoA)        */
 } orc_mapping;
 
 /* Size in bytes of a leaf type; 0 for an unknown type. */
