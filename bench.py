@@ -627,11 +627,39 @@ def split_rows(device, entry):
     return rows
 
 
+def bitpack_aosoa_rows(device, entry):
+    """Bit-packed mappings organised as AoSoA (L lanes) against the SoA
+    organisation, packed from and unpacked to SoA multi-blob: 2^26 INT6
+    records at b = 12, 2^25 MIXED_F records at E8M23."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, synth
+    soa = {"kind": "soa_mb"}
+    rows = {}
+    for label, kind, n, rec_leaves, mp in (
+            ("INT6 b=12", "int6", 1 << 26, synth.INT6, {"kind": "bitpack_int", "bits": 12}),
+            ("MIXED_F E8M23", "mixed_f", 1 << 25, synth.MIXED_F, {"kind": "bitpack_float", "exp": 8, "man": 23})):
+        rec = llgb.Record(rec_leaves)
+        fields = synth.device_fields(kind, n, 29, device=device)
+        base = llgb.View(rec, soa, (n,), blobs=[f.contiguous().view(torch.uint8) for f in fields])
+        plain = llgb.View(rec, soa, (n,))
+        for org, m in (("SoA", mp), ("AoSoA32", dict(mp, lanes=32)), ("AoSoA256", dict(mp, lanes=256))):
+            packed = llgb.View(rec, m, (n,))
+            nbytes = sum(llgb.blob_sizes(rec, soa, (n,))) + sum(llgb.blob_sizes(rec, m, (n,)))
+            rows[f"{label} {org}"] = {"pack": entry(nbytes, time_copy(base, packed)),
+                                      "unpack": entry(nbytes, time_copy(packed, plain))}
+            del packed
+            torch.cuda.empty_cache()
+        del fields, base, plain
+        torch.cuda.empty_cache()
+    return rows
+
+
 def sweeps_bench(device):
     """The configurations the suite's step holds one point of: BitpackInt at
     b in {1, 3, 7, 12, 17, 31} (2^26 INT6 records), BitpackFloat at the 12
     (E, M) formats (2^25 MIXED_F records), both from / to SoA multi-blob;
-    copies into and out of Split / Null views (2^26 records); and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose
+    copies into and out of Split / Null views (2^26 records); the bit-packed
+    AoSoA organisation against SoA; and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose
     3.7 MB fit L2: its latency is reported warm and with L2 flushed."""
     import torch
     from paper_2302_08251_gb300 import llgb, synth
@@ -679,6 +707,7 @@ def sweeps_bench(device):
     torch.cuda.empty_cache()
 
     out["F2 Split / Null"] = split_rows(device, entry)
+    out["F3 bit-packed AoSoA organisation"] = bitpack_aosoa_rows(device, entry)
 
     n = 65536
     rec = llgb.Record(synth.PARTICLE)

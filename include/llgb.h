@@ -151,6 +151,14 @@ enum {
  *                 (or man_bits) mantissa bits, IEEE-style, round to nearest
  *                 even, overflow to INF, NaN kept quiet; one stream per leaf.
  *                 2 <= E <= 11, 1 <= M <= 52, 1+E+M <= 64.
+ *                 BITPACK_INT and BITPACK_FLOAT are organised by bit_lanes:
+ *                 0 = SoA (the streams above, one blob per leaf); L = AoSoA:
+ *                 one blob of blocks of L records, each block holding leaf
+ *                 0's L codes, then leaf 1's, and so on (the generalisation
+ *                 of the SoA organisation that Sec. 3 announces), the last
+ *                 block whole with zero codes in its unused lanes.  L is a
+ *                 power of two from 32 to 1024, so that every run of a
+ *                 block's codes starts on a 32-bit word.
  *  BYTESPLIT:     each leaf becomes size-of-leaf u8 leaves (its little-endian
  *                 bytes) forwarded to `inner`.
  *  CHANGETYPE:    leaves of type ct_from[k] are stored as ct_to[k] (floating
@@ -181,6 +189,7 @@ typedef struct llgb_mapping_desc {
     const struct llgb_mapping_desc* inner;
     uint64_t split_mask;                     /* SPLIT: bit f = leaf f to `inner` */
     const struct llgb_mapping_desc* inner2;  /* SPLIT: mapping of the others     */
+    uint64_t bit_lanes;                      /* BITPACK_*: 0 SoA, else AoSoA lanes */
 } llgb_mapping_desc;
 
 /* ---------------------------------------------------------------- view -- */

@@ -95,6 +95,7 @@ bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
 // else the general kernel (0).
 int job_mode(const JobDesc& J, int threads)
 {
+    if (J.seg) return 1;
     int mode = J.gather;
     if (mode == 0) return 0;
     // words the gather programs cover: every run (interleaved), or the whole
@@ -292,11 +293,11 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     args.dst_stages = (uint16_t)c.dst_stages;
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
-    int mode = c.engine == LLGB_ENGINE_VALUE ? 0 : job_mode(args.job, c.threads);
+    int mode = c.engine == LLGB_ENGINE_VALUE ? (args.job.seg ? 1 : 0) : job_mode(args.job, c.threads);
     // a gather program is built once per job by every CTA: with at most two
     // tiles per CTA that costs more than it saves, and the value loops
     // (whole-element moves) need no program
-    if (c.engine == LLGB_ENGINE_AUTO && mode != 0 && args.total_tiles <= 2u * (uint32_t)grid) mode = 0;
+    if (c.engine == LLGB_ENGINE_AUTO && mode >= 2 && args.total_tiles <= 2u * (uint32_t)grid) mode = 0;
     if (c.threads / 32 <= (int)producer_warps(mode))
         return fail(LLGB_ERR_INVALID_ARG, "launch config leaves no consumer warp");
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
@@ -382,10 +383,11 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
     cudaGetDevice(&b->device);
-    llgb_batch::Group groups[3];
+    llgb_batch::Group groups[4];
     groups[0].mode = 0;
     groups[1].mode = 2;
     groups[2].mode = 4;
+    groups[3].mode = 1;
     for (int32_t k = 0; k < n; ++k) {
         llgb_status st = check_pair(src[k], dst[k]);
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
@@ -394,7 +396,7 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         int mode = 0;
         st = plan_batch_job(src[k], dst[k], &J, &mode, 256);
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
-        llgb_batch::Group& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : 2)];
+        llgb_batch::Group& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : (mode == 4 ? 2 : 3))];
         g.starts.push_back((uint32_t)b->tiles);
         g.jobs.push_back(J);
         for (uint64_t s : src[k]->plan.blob_sizes) b->bytes += s;
@@ -415,7 +417,7 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         if (total > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
         g.starts.push_back((uint32_t)total);
         int ctas = 2;
-        uint16_t ns = g.mode != 0 ? 4 : 2, nd = g.mode != 0 ? 3 : 2;
+        uint16_t ns = g.mode >= 2 ? 4 : 2, nd = g.mode >= 2 ? 3 : 2;
         auto need = [&]() {
             return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
         };

@@ -286,8 +286,11 @@ __device__ __forceinline__ void or_bits(uint8_t* base, uint32_t pos, uint32_t w,
 }
 
 // One VALUE item: load the logical value through LOP, store it through SOP.
-// Two records per iteration keep two independent chains in flight.
-template <int LOP, int SOP>
+// Two records per iteration keep two independent chains in flight.  SEG: a
+// bit leaf of the item is organised as AoSoA (runs of `lanes` codes,
+// `bstride` bytes apart); a separate instantiation, so that SoA streams keep
+// their plain addressing (and its register budget).
+template <int LOP, int SOP, bool SEG = false>
 __device__ __noinline__ void value_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* __restrict__ simg,
                                         uint8_t* __restrict__ dimg, Span sp, uint32_t nvalid)
 {
@@ -309,15 +312,18 @@ __device__ __noinline__ void value_loop(const ItemDesc& I, const JobDesc& J, con
         if (LOP == L_DIRECT) return ld_elem(simg + eoff(A, r), size, A.align);
         if (LOP == L_CT) return fconv(ld_elem(simg + eoff(A, r), I.s_size, A.align), I.s_e, I.s_m, I.l_e, I.l_m);
         if (is_bits_src) {
+            // the run holding record r, and r's lane in it
+            const uint8_t* run = SEG ? simg + A.sbase + (r >> A.lshift) * A.bstride : simg + A.sbase;
+            const uint32_t rl = SEG ? r & (A.lanes - 1u) : r;
             uint64_t c;
             if (a_aligned) {
-                c = ld_elem(simg + A.sbase + r * abytes, (int)abytes, (int)abytes);
+                c = ld_elem(run + rl * abytes, (int)abytes, SEG ? (int)min(abytes, A.align) : (int)abytes);
             } else if (A.bits <= 32) {
-                const uint32_t* wd = reinterpret_cast<const uint32_t*>(simg + A.sbase);
-                const uint32_t pos = r * A.bits;
+                const uint32_t* wd = reinterpret_cast<const uint32_t*>(run);
+                const uint32_t pos = rl * A.bits;
                 c = __funnelshift_r(wd[pos >> 5], wd[(pos >> 5) + 1], pos & 31u) & (uint32_t)smask;
             } else {
-                c = ld_bits(simg + A.sbase, r * A.bits, A.bits);
+                c = ld_bits(run, rl * A.bits, A.bits);
             }
             if (LOP == L_BITS_INT) {
                 if (I.is_signed && ((c >> (A.bits - 1)) & 1ull)) c |= ~smask;
@@ -339,10 +345,12 @@ __device__ __noinline__ void value_loop(const ItemDesc& I, const JobDesc& J, con
             st_elem(dimg + eoff(B, r), I.d_size, B.align, fconv(v, I.l_e, I.l_m, I.d_e, I.d_m));
         } else if (SOP == S_BITS_INT || SOP == S_BITS_FLOAT) {
             const uint64_t c = SOP == S_BITS_INT ? (v & dmask) : fconv(v, I.l_e, I.l_m, I.d_e, I.d_m);
+            uint8_t* run = SEG ? dimg + B.sbase + (r >> B.lshift) * B.bstride : dimg + B.sbase;
+            const uint32_t rl = SEG ? r & (B.lanes - 1u) : r;
             if (d_aligned)
-                st_elem(dimg + B.sbase + r * dbytes, (int)dbytes, (int)dbytes, c);
+                st_elem(run + rl * dbytes, (int)dbytes, SEG ? (int)min(dbytes, B.align) : (int)dbytes, c);
             else
-                or_bits(dimg + B.sbase, r * I.d_bits, I.d_bits, c);
+                or_bits(run, rl * I.d_bits, I.d_bits, c);
         } else {  // S_SPLIT
             for (int j = 0; j < size; ++j) {
                 const LeafRegs D = leaf_regs(J.dst.leaves[I.dst_leaf + j]);
@@ -359,10 +367,33 @@ __device__ __noinline__ void value_loop(const ItemDesc& I, const JobDesc& J, con
     }
 }
 
-template <int LOP>
+// SEGOK: the kernel mode that runs jobs with AoSoA-organised bit leaves (1);
+// the other value mode (0) never calls their loops, which keeps its register
+// budget (calls share the kernel's registers).
+template <int LOP, bool SEGOK>
 __device__ __forceinline__ void value_dispatch(const ItemDesc& I, const JobDesc& J, const uint8_t* simg,
                                                uint8_t* dimg, Span sp, uint32_t nvalid)
 {
+    constexpr bool bits_src = LOP == L_BITS_INT || LOP == L_BITS_FLOAT;
+    const bool seg_src = bits_src && J.src.leaves[I.src_leaf].lanes != 0;
+    const bool seg_dst = (I.sop == S_BITS_INT || I.sop == S_BITS_FLOAT) && J.dst.leaves[I.dst_leaf].lanes != 0;
+    if constexpr (SEGOK) {
+        if (seg_src || seg_dst) {  // AoSoA-organised bit leaves
+            switch (I.sop) {
+            case S_BITS_INT: value_loop<LOP, S_BITS_INT, true>(I, J, simg, dimg, sp, nvalid); return;
+            case S_BITS_FLOAT: value_loop<LOP, S_BITS_FLOAT, true>(I, J, simg, dimg, sp, nvalid); return;
+            default:
+                if constexpr (bits_src) {
+                    switch (I.sop) {
+                    case S_DIRECT: value_loop<LOP, S_DIRECT, true>(I, J, simg, dimg, sp, nvalid); return;
+                    case S_CT: value_loop<LOP, S_CT, true>(I, J, simg, dimg, sp, nvalid); return;
+                    default: value_loop<LOP, S_SPLIT, true>(I, J, simg, dimg, sp, nvalid); return;
+                    }
+                }
+                return;
+            }
+        }
+    }
     switch (I.sop) {
     case S_DIRECT: value_loop<LOP, S_DIRECT>(I, J, simg, dimg, sp, nvalid); break;
     case S_CT: value_loop<LOP, S_CT>(I, J, simg, dimg, sp, nvalid); break;
@@ -1013,12 +1044,21 @@ __device__ __noinline__ void zero_streams(const JobDesc& J, uint8_t* dimg)
     for (int k = 0; k < J.npacks; ++k) {
         const PackDesc& P = J.packs[k];
         if (!P.ored) continue;
-        uint4* z = reinterpret_cast<uint4*>(dimg + P.dst_sbase);
-        for (uint32_t q = ctid(); q < (P.bytes + 15u) / 16u; q += cnum()) z[q] = make_uint4(0, 0, 0, 0);
+        if (P.runs == 1) {
+            uint4* z = reinterpret_cast<uint4*>(dimg + P.dst_sbase);
+            for (uint32_t q = ctid(); q < (P.bytes + 15u) / 16u; q += cnum()) z[q] = make_uint4(0, 0, 0, 0);
+            continue;
+        }
+        const uint32_t wpr = P.bytes / 4u;  // words per run
+        for (uint32_t w = ctid(); w < P.runs * wpr; w += cnum()) {
+            const uint32_t run = w / wpr;
+            *reinterpret_cast<uint32_t*>(dimg + P.dst_sbase + run * P.run_stride + 4u * (w - run * wpr)) = 0u;
+        }
     }
 }
 
 // Quads [q0, q1) (128 records each) of one item.
+template <bool SEGOK>
 __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc& I, const uint8_t* simg,
                                                uint8_t* dimg, uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
@@ -1035,12 +1075,12 @@ __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc&
         }
     } else if (!run_fast(I, J, simg, dimg, q0, q1, nvalid)) {
         switch (I.lop) {
-        case L_DIRECT: value_dispatch<L_DIRECT>(I, J, simg, dimg, sp, nvalid); break;
-        case L_CT: value_dispatch<L_CT>(I, J, simg, dimg, sp, nvalid); break;
-        case L_BITS_INT: value_dispatch<L_BITS_INT>(I, J, simg, dimg, sp, nvalid); break;
-        case L_BITS_FLOAT: value_dispatch<L_BITS_FLOAT>(I, J, simg, dimg, sp, nvalid); break;
-        case L_NULL: value_dispatch<L_NULL>(I, J, simg, dimg, sp, nvalid); break;
-        default: value_dispatch<L_SPLIT>(I, J, simg, dimg, sp, nvalid); break;
+        case L_DIRECT: value_dispatch<L_DIRECT, SEGOK>(I, J, simg, dimg, sp, nvalid); break;
+        case L_CT: value_dispatch<L_CT, SEGOK>(I, J, simg, dimg, sp, nvalid); break;
+        case L_BITS_INT: value_dispatch<L_BITS_INT, SEGOK>(I, J, simg, dimg, sp, nvalid); break;
+        case L_BITS_FLOAT: value_dispatch<L_BITS_FLOAT, SEGOK>(I, J, simg, dimg, sp, nvalid); break;
+        case L_NULL: value_dispatch<L_NULL, SEGOK>(I, J, simg, dimg, sp, nvalid); break;
+        default: value_dispatch<L_SPLIT, SEGOK>(I, J, simg, dimg, sp, nvalid); break;
         }
     }
 }
@@ -1062,13 +1102,14 @@ __device__ __forceinline__ ItemShare item_share(const JobDesc& J)
     return ItemShare{it, lo - it * Q, hi - lo};
 }
 
+template <bool SEGOK>
 __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid, ItemShare S)
 {
     const uint32_t Q = J.tile >> 7;
     uint32_t it = S.item, q0 = S.quad, left = S.count;
     while (left) {
         const uint32_t q1 = min(Q, q0 + left);
-        run_item_quads(J, J.items[it], simg, dimg, q0, q1, nvalid);
+        run_item_quads<SEGOK>(J, J.items[it], simg, dimg, q0, q1, nvalid);
         left -= q1 - q0;
         ++it;
         q0 = 0;
@@ -1532,8 +1573,8 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             consumer_sync();
             cur_job = (int)j;
             zeroed = 0;
-            if (MODE == 0) share = item_share(H.job);
-            if (MODE != 0) {
+            if (MODE <= 1) share = item_share(H.job);
+            if (MODE >= 2) {
                 gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
                 build_gather<MODE>(H.job, zero_word, gather_words, gp);
             }
@@ -1571,14 +1612,14 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
         // (A gather program writes every word, zeros included.)  The store
         // of the stage's previous tile has read it (dempty), and that tile's
         // writers all arrived before the store was issued.
-        const bool items_here = MODE == 0 || t >= J.nfull;
+        const bool items_here = MODE <= 1 || t >= J.nfull;
         if (items_here && !(zeroed & (1u << d))) {
             uint4* z = reinterpret_cast<uint4*>(dimg);
             for (uint32_t w = ctid(); w < a.dst_stage_bytes / 16u; w += cnum()) z[w] = make_uint4(0, 0, 0, 0);
             zeroed |= 1u << d;
             sync_needed = true;
         }
-        if (MODE == 0 && J.ored) {
+        if (MODE <= 1 && J.ored) {
             zero_streams(J, dimg);
             sync_needed = true;
         }
@@ -1590,7 +1631,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                 for (uint32_t b = ctid(); b < Z.bytes; b += cnum()) p[b] = 0;
             }
         }
-        if (MODE != 0) {
+        if (MODE >= 2) {
             if (t < J.nfull) {
                 run_gather<MODE>(gp, simg, dimg, gather_words);
                 zeroed |= 1u << d;
@@ -1598,7 +1639,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                 run_moves(J, simg, dimg, nvalid);
             }
         } else {
-            run_items(J, simg, dimg, nvalid, share);
+            run_items<MODE == 1>(J, simg, dimg, nvalid, share);
         }
         fence_proxy_async();
         __syncwarp();
@@ -1622,8 +1663,9 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     }
 }
 
-// MODE 0: general items and packs.  MODE 2 / 4: every job is made of byte
-// moves; full tiles run gather programs of that form.
+// MODE 0: general items and packs.  MODE 1: the same, for jobs with bit
+// leaves organised as AoSoA.  MODE 2 / 4: every job is made of byte moves;
+// full tiles run gather programs of that form.
 template <int MODE>
 __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ CopyArgs a)
 {
@@ -1708,6 +1750,7 @@ static cudaError_t prepare_mode(size_t smem_bytes)
 cudaError_t prepare_copy(int mode, size_t smem_bytes)
 {
     switch (mode) {
+    case 1: return prepare_mode<1>(smem_bytes);
     case 2: return prepare_mode<2>(smem_bytes);
     case 4: return prepare_mode<4>(smem_bytes);
     default: return prepare_mode<0>(smem_bytes);
@@ -1727,6 +1770,7 @@ cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, s
                         cudaStream_t stream)
 {
     switch (mode) {
+    case 1: return launch_mode<1>(args, grid, threads, smem_bytes, stream);
     case 2: return launch_mode<2>(args, grid, threads, smem_bytes, stream);
     case 4: return launch_mode<4>(args, grid, threads, smem_bytes, stream);
     default: return launch_mode<0>(args, grid, threads, smem_bytes, stream);

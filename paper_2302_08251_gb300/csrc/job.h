@@ -24,7 +24,7 @@ constexpr int kMaxZeros = 32;   // destination byte ranges owned by no leaf
 constexpr int kStageZeroBytes = 16;  // zero block at the end of every source stage
 // Warps of a CTA that issue its TMA copies: value kernels (mode 0) have a
 // load warp and a store warp; gather kernels one warp for both.
-constexpr unsigned producer_warps(int mode) { return mode == 0 ? 2u : 1u; }
+constexpr unsigned producer_warps(int mode) { return mode <= 1 ? 2u : 1u; }
 
 // One contiguous run of a tile in a blob.  For tile t it covers
 // [gbase + t * tile_bytes, + tile_bytes) (the last tile: tail_bytes) and
@@ -129,15 +129,18 @@ enum FastKind : uint8_t {
 
 // A bit-stream destination leaf.  Specialised loops store whole words of the
 // stream; a generic item ORs its codes into it (unless the width is 8, 16,
-// 32 or 64 bits), and then the consumers zero the stream's `bytes` at
-// `dst_sbase` before every tile (`ored`).
+// 32 or 64 bits), and then the consumers zero the stream before every tile
+// (`ored`): `runs` runs of `bytes` bytes, `run_stride` apart, from
+// `dst_sbase` (one run for a SoA stream; one per block for AoSoA).
 struct PackDesc {
     uint32_t dst_sbase;  // destination image offset of the stream
-    uint32_t bytes;      // stream bytes per tile
+    uint32_t bytes;      // bytes per run (a multiple of 4)
+    uint32_t run_stride;
+    uint16_t runs;
     uint8_t bits;
     uint8_t aligned;
     uint8_t ored;
-    uint8_t pad[5];
+    uint8_t pad[7];
 };
 
 struct SideDesc {
@@ -177,7 +180,8 @@ struct JobDesc {
     uint8_t gather;      // full tiles use gather programs: 0 no, 2 or 4 source words
     uint8_t interleave;  // 4-word gathers: deal destination words round-robin over the runs
     uint8_t ored;        // some PackDesc has `ored` set: zero those streams before every tile
-    uint8_t pad[7];
+    uint8_t seg;         // a bit leaf is organised as AoSoA: the job runs in kernel mode 1
+    uint8_t pad[6];
 };
 
 // Launch-wide parameters of the copy kernel.

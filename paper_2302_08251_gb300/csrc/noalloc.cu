@@ -34,7 +34,7 @@ using namespace llgb;
 namespace {
 
 constexpr int kNoallocPairs = 64;      // most pairs one call accepts
-constexpr int kModes = 3;              // kernel modes: general, 2-word and 4-word gathers
+constexpr int kModes = 4;              // kernel modes: general, 2-word and 4-word gathers, AoSoA bits
 constexpr int kMaxDevices = 64;
 constexpr size_t kTableBytes = (size_t)kNoallocPairs * sizeof(JobDesc);
 constexpr size_t kStartsBytes = (size_t)kModes * (kNoallocPairs + 1) * sizeof(uint32_t);
@@ -91,7 +91,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
     // Plan every pair and order the jobs by kernel mode.
     int mode_of[kNoallocPairs];
     int order[kNoallocPairs];
-    int count[kModes] = {0, 0, 0};
+    int count[kModes] = {0, 0, 0, 0};
     static thread_local JobDesc planned[kNoallocPairs];
     int njobs = 0;
     for (int32_t k = 0; k < n; ++k) {
@@ -106,12 +106,12 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
         int m = 0;
         st = internal_plan_pair(src[k], dst[k], &planned[njobs], &m, 256);
         if (st != LLGB_OK) return st;
-        mode_of[njobs] = m == 0 ? 0 : (m == 2 ? 1 : 2);
+        mode_of[njobs] = m == 0 ? 0 : (m == 2 ? 1 : (m == 4 ? 2 : 3));
         ++count[mode_of[njobs]];
         ++njobs;
     }
     if (njobs == 0) return LLGB_OK;
-    int at[kModes] = {0, count[0], count[0] + count[1]};
+    int at[kModes] = {0, count[0], count[0] + count[1], count[0] + count[1] + count[2]};
     for (int q = 0; q < njobs; ++q) order[at[mode_of[q]]++] = q;
     for (int q = 0; q < njobs; ++q) staging.jobs[q] = planned[order[q]];
 
@@ -142,7 +142,8 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
         if (total > 0xFFFFFFFFull) return internal_fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
         staging.starts[g][count[g]] = (uint32_t)total;
         int ctas = 2;
-        uint16_t ns = g != 0 ? 4 : 2, nd = g != 0 ? 3 : 2;
+        const bool gather = g == 1 || g == 2;
+        uint16_t ns = gather ? 4 : 2, nd = gather ? 3 : 2;
         auto need = [&]() {
             return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
         };
@@ -179,7 +180,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
     if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     for (int g = 0; g < kModes; ++g) {
         if (launch[g].grid == 0) continue;
-        const int mode = g == 0 ? 0 : (g == 1 ? 2 : 4);
+        const int mode = g == 0 ? 0 : (g == 1 ? 2 : (g == 2 ? 4 : 1));
         e = launch_copy(launch[g].args, mode, launch[g].grid, launch[g].threads, launch[g].smem, s);
         if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     }

@@ -273,6 +273,11 @@ llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llg
     v.aos_packed = base->aos_packed ? 1 : 0;
     v.subarray_align = base->subarray_align;
     v.lanes = v.base == BASE_AOSOA ? base->lanes : 1;
+    v.bit_lanes = is_bits_base(v.base) ? base->bit_lanes : 0;
+    if (v.bit_lanes && (v.bit_lanes < 32 || v.bit_lanes > 1024 || (v.bit_lanes & (v.bit_lanes - 1)))) {
+        *why = "bit-packed AoSoA: bit_lanes must be a power of two from 32 to 1024";
+        return LLGB_ERR_UNSUPPORTED;
+    }
 
     if (v.base == BASE_BITS_INT) {
         // Sec. 3 BitpackIntSoA: a bit count for integral leaves.
@@ -371,6 +376,20 @@ llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llg
         break;
     }
     default:  // bit streams: whole 32-bit words per leaf
+        if (v.bit_lanes) {  // AoSoA organisation: runs of L codes, word-aligned
+            uint64_t R = 0;
+            for (int g = 0; g < ns; ++g) {
+                v.leaf_offset[g] = v.bit_lanes * R / 8;
+                R += v.stored[g].bits;
+            }
+            v.bit_block_bytes = v.bit_lanes * R / 8;
+            const uint64_t blocks = n / v.bit_lanes + (n % v.bit_lanes ? 1 : 0);
+            uint64_t size = 0;
+            ok = mul_ok(blocks, v.bit_block_bytes, &size);
+            v.blob_sizes.push_back(size);
+            for (int g = 0; g < ns; ++g) v.seg_end[g] = size;
+            break;
+        }
         for (int g = 0; g < ns; ++g) {
             uint64_t bits = 0;
             ok = ok && mul_ok(n, (uint64_t)v.stored[g].bits, &bits);
@@ -396,7 +415,8 @@ llgb_status plan_view(const llgb_record& rec, const llgb_extents& ext, const llg
         }
     // Signature of the layout, for caches keyed by mapping pair.
     std::string sig = "w" + std::to_string(v.wrap) + "b" + std::to_string(v.base) + "p" + std::to_string(v.aos_packed) +
-                      "a" + std::to_string(v.subarray_align) + "l" + std::to_string(v.lanes) + ":";
+                      "a" + std::to_string(v.subarray_align) + "l" + std::to_string(v.lanes) + "o" +
+                      std::to_string(v.bit_lanes) + ":";
     for (int f = 0; f < nf; ++f) sig += std::to_string(v.types[f]) + ",";
     sig += ":";
     for (const StoredLeaf& l : v.stored)
@@ -420,6 +440,7 @@ static uint64_t gcd64(uint64_t a, uint64_t b)
 static uint64_t lane_quantum(const ViewPlan& v, uint64_t q)
 {
     if (v.base == BASE_AOSOA) q = q / gcd64(q, v.lanes) * v.lanes;
+    if (v.bit_lanes) q = q / gcd64(q, v.bit_lanes) * v.bit_lanes;
     for (const ViewPlan& p : v.parts) q = lane_quantum(p, q);
     return q;
 }
@@ -539,17 +560,38 @@ static llgb_status plan_side_part(const ViewPlan& v, int blob0, int leaf0, uint3
         }
         break;
     default:
+        // a bit leaf's code of tile record r starts at bit
+        //   8 (sbase + (r >> lshift) bstride) + (r & (lanes - 1)) bits;
+        // a SoA stream is one run (lanes 0: mask all ones, lshift 31).
+        if (v.bit_lanes) {
+            const int64_t sb = add_seg(0, 0, (uint64_t)tile / v.bit_lanes * v.bit_block_bytes, v.seg_end[0]);
+            if (sb < 0) break;
+            uint8_t shift = 0;
+            while ((1ull << shift) < v.bit_lanes) ++shift;
+            for (int g = 0; g < ns; ++g) {
+                leaves[g].sbase = (uint32_t)(sb + v.leaf_offset[g]);
+                leaves[g].bstride = (uint32_t)v.bit_block_bytes;
+                leaves[g].lanes = (uint32_t)v.bit_lanes;
+                leaves[g].lshift = shift;
+                leaves[g].kind = LEAF_BITS;
+                leaves[g].bits = (uint8_t)v.stored[g].bits;
+            }
+            break;
+        }
         for (int g = 0; g < ns; ++g) {
             const uint64_t w = v.stored[g].bits;
             const int64_t sb = add_seg(v.leaf_blob[g], 0, (uint64_t)tile * w / 8, v.seg_end[g]);
             if (sb < 0) break;
             leaves[g].sbase = (uint32_t)sb;
+            leaves[g].bstride = 0;
+            leaves[g].lanes = 0;
+            leaves[g].lshift = 31;
             leaves[g].kind = LEAF_BITS;
             leaves[g].bits = (uint8_t)w;
         }
         break;
     }
-    const int expect_segs = (v.base == BASE_AOS || v.base == BASE_AOSOA) ? 1 : ns;
+    const int expect_segs = (v.base == BASE_AOS || v.base == BASE_AOSOA || v.bit_lanes) ? 1 : ns;
     if (S->nsegs - segs0 != expect_segs) {
         *why = "internal: a tile run does not fit its blob region";
         return LLGB_ERR_INVALID_ARG;
@@ -589,6 +631,8 @@ static bool fmt_is(int e, int m, int fe, int fm) { return e == fe && m == fm; }
 // The specialised loop a VALUE item can run in (FastKind), or FK_GENERIC.
 static int fast_kind(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
 {
+    // codes in AoSoA-organised bit blobs run in the generic loop
+    if ((A.kind == LEAF_BITS && A.lanes) || (B.kind == LEAF_BITS && B.lanes)) return FK_GENERIC;
     const bool a_aff = A.kind == LEAF_AFFINE, b_aff = B.kind == LEAF_AFFINE;
     const bool a_al = A.kind == LEAF_BITS && (A.bits == 8 || A.bits == 16 || A.bits == 32 || A.bits == 64);
     const bool b_al = B.kind == LEAF_BITS && (B.bits == 8 || B.bits == 16 || B.bits == 32 || B.bits == 64);
@@ -729,9 +773,23 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         P.bits = (uint8_t)dst.stored[g].bits;
         P.dst_sbase = job->dst.leaves[g].sbase;
         P.aligned = (P.bits == 8 || P.bits == 16 || P.bits == 32 || P.bits == 64) ? 1 : 0;
-        P.bytes = (uint32_t)((uint64_t)tile * P.bits / 8);
+        const LeafDesc& D = job->dst.leaves[g];
+        if (D.lanes) {  // AoSoA organisation: tile / L runs of L codes
+            P.bytes = D.lanes * P.bits / 8;
+            P.runs = (uint16_t)(tile / D.lanes);
+            P.run_stride = D.bstride;
+        } else {
+            P.bytes = (uint32_t)((uint64_t)tile * P.bits / 8);
+            P.runs = 1;
+            P.run_stride = 0;
+        }
     }
     job->code_bytes = 0;
+    job->seg = 0;
+    for (int g = 0; g < job->src.nleaves; ++g)
+        if (job->src.leaves[g].kind == LEAF_BITS && job->src.leaves[g].lanes) job->seg = 1;
+    for (int g = 0; g < job->dst.nleaves; ++g)
+        if (job->dst.leaves[g].kind == LEAF_BITS && job->dst.leaves[g].lanes) job->seg = 1;
 
     // Items: one per leaf, or one per byte where a side splits bytes.
     const int nf = (int)src.types.size();

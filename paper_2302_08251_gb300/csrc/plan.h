@@ -48,6 +48,11 @@ struct ViewPlan {
     int aos_packed = 0;
     uint64_t subarray_align = 0;
     uint64_t lanes = 1;
+    // Bit-packed bases: 0 = SoA (one stream per leaf); L = AoSoA, one blob of
+    // blocks of L records, bit_block_bytes each, leaf g's L codes at byte
+    // leaf_offset[g] of its block.
+    uint64_t bit_lanes = 0;
+    uint64_t bit_block_bytes = 0;
     std::vector<StoredLeaf> stored;
     std::vector<Recipe> recipes;       // one per logical leaf
     std::vector<uint64_t> leaf_offset; // AoS / AoSoA: offset inside the record

@@ -63,6 +63,7 @@ MappingDesc._fields_ = [
     ("inner", ctypes.POINTER(MappingDesc)),
     ("split_mask", ctypes.c_uint64),
     ("inner2", ctypes.POINTER(MappingDesc)),
+    ("bit_lanes", ctypes.c_uint64),
 ]
 
 
@@ -164,6 +165,8 @@ def mapping_desc(m: dict, keep: list) -> MappingDesc:
     c.aos_packed = int(m.get("packed", 0))
     c.subarray_align = int(m.get("subarray_align", 0))
     c.lanes = int(m.get("lanes", 1))
+    if m["kind"] in ("bitpack_int", "bitpack_float"):
+        c.bit_lanes = int(m.get("lanes", 0))  # 0: SoA organisation
     c.bits = int(m.get("bits", 0))
     c.exp_bits = int(m.get("exp", 0))
     c.man_bits = int(m.get("man", 0))

@@ -248,3 +248,28 @@ def test_split_of_bitpacked_integers_and_plain_floats_plans():
     _, sizes = host_view(rec, m, 1000)
     assert sizes == oracle.OracleView(rec, m, 1000).blob_sizes == [1500, 1500, 4000, 4000]
 
+
+
+@pytest.mark.parametrize("m", [
+    {"kind": "bitpack_int", "bits": 12, "lanes": 32},
+    {"kind": "bitpack_int", "bits": 0, "field_bits": [1, 3, 7, 12, 17, 31], "lanes": 64},
+    {"kind": "bitpack_int", "bits": 32, "lanes": 1024},
+])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1000, 4097])
+def test_bitpacked_aosoa_blob_sizes_match_the_oracle(m, n):
+    _, sizes = host_view(synth.INT6, m, n)
+    assert sizes == oracle.OracleView(synth.INT6, m, n).blob_sizes
+
+
+def test_bitpacked_float_aosoa_blob_sizes_match_the_oracle():
+    m = {"kind": "bitpack_float", "exp": 5, "man": 10, "lanes": 128}
+    for n in (1, 127, 128, 129, 5000):
+        _, sizes = host_view(synth.MIXED_F, m, n)
+        assert sizes == oracle.OracleView(synth.MIXED_F, m, n).blob_sizes
+
+
+@pytest.mark.parametrize("lanes", [1, 8, 16, 48, 2048])
+def test_bitpacked_aosoa_needs_power_of_two_lanes_from_32_to_1024(lanes):
+    with pytest.raises(llgb.LlgbError) as err:
+        host_view(synth.INT6, {"kind": "bitpack_int", "bits": 12, "lanes": lanes}, 100)
+    assert err.value.status == llgb.ERR_UNSUPPORTED

@@ -1,0 +1,127 @@
+"""GPU parity of bit-packed mappings organised as AoSoA against the oracle,
+byte for byte (destination blobs pre-filled with 0xAB): packing from plain
+layouts, unpacking back, between the SoA and AoSoA organisations, inside a
+Split, at ragged record counts and over many tiles.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08251_gb300 import llgb, synth
+from helpers import oracle_view
+from gpu_util import assert_same_bytes, device_view_of, empty_device_view, ensure_library, sync_and_check_status
+
+pytestmark = pytest.mark.gpu
+
+INT_MAPS = [
+    {"kind": "bitpack_int", "bits": 12, "lanes": 32},
+    {"kind": "bitpack_int", "bits": 0, "field_bits": [1, 3, 7, 12, 17, 31], "lanes": 64},
+    {"kind": "bitpack_int", "bits": 0, "field_bits": [32, 5, 9, 1, 30, 2], "lanes": 128},
+    {"kind": "bitpack_int", "bits": 8, "lanes": 1024},
+    {"kind": "bitpack_int", "bits": 16, "lanes": 32},
+]
+FLOAT_MAPS = [
+    {"kind": "bitpack_float", "exp": 8, "man": 23, "lanes": 32},
+    {"kind": "bitpack_float", "exp": 5, "man": 10, "lanes": 128},
+    {"kind": "bitpack_float", "exp": 0, "man": 0, "field_exp": [11, 6, 4, 8], "field_man": [52, 9, 3, 7],
+     "lanes": 64},
+    # a 9-bit leaf first: the 64- and 32-bit codes after it sit on 4-byte, not 8-byte, boundaries
+    {"kind": "bitpack_float", "exp": 0, "man": 0, "field_exp": [4, 11, 8, 8], "field_man": [4, 52, 23, 23],
+     "lanes": 32},
+]
+PLAIN = [{"kind": "soa_mb"}, {"kind": "aos"}, {"kind": "aosoa", "lanes": 32}]
+SIZES = [1, 33, 1000, 5007]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return ensure_library()
+
+
+def run_pair(rec, fields, src_map, dst_map, cfg=None):
+    n = len(fields[0])
+    src_o = oracle_view(rec, src_map, fields)
+    dst_o = oracle.OracleView(rec, dst_map, n)
+    src_o.copy_to(dst_o)
+    src_g = device_view_of(src_o)
+    dst_g = empty_device_view(rec, dst_map, n)
+    if cfg is None:
+        llgb.llgb_copy(src_g, dst_g)
+    else:
+        llgb.llgb_copy_with(src_g, dst_g, cfg)
+    sync_and_check_status()
+    assert_same_bytes(dst_g, dst_o, f"{src_map} -> {dst_map}")
+
+
+def int_fields(n, seed, in_range=True):
+    if in_range:
+        return synth.int6(n, 12, seed)
+    return synth.uniform_fields(synth.INT6, n, seed)  # wrap and sign-extend
+
+
+def float_fields(n, seed):
+    cols = synth.mixed_f(n, seed)
+    sp = synth.special_f64(max(0, n - 24), seed)[:n]
+    cols[0] = np.where(np.arange(n) % 3 == 0, sp, cols[0])
+    return cols
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("plain", range(len(PLAIN)))
+@pytest.mark.parametrize("m", range(len(INT_MAPS)))
+def test_int_pack_and_unpack(m, plain, n):
+    for in_range in (True, False):
+        f = int_fields(n, n + m, in_range)
+        run_pair(synth.INT6, f, PLAIN[plain], INT_MAPS[m])
+        run_pair(synth.INT6, f, INT_MAPS[m], PLAIN[plain])
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("plain", range(len(PLAIN)))
+@pytest.mark.parametrize("m", range(len(FLOAT_MAPS)))
+def test_float_pack_and_unpack(m, plain, n):
+    f = float_fields(n, n + 7 * m)
+    run_pair(synth.MIXED_F, f, PLAIN[plain], FLOAT_MAPS[m])
+    run_pair(synth.MIXED_F, f, FLOAT_MAPS[m], PLAIN[plain])
+
+
+@pytest.mark.parametrize("lanes", [32, 256])
+def test_between_the_soa_and_aosoa_organisations(lanes):
+    n = 3000 + 11
+    f = int_fields(n, 5, in_range=False)
+    soa = {"kind": "bitpack_int", "bits": 0, "field_bits": [1, 3, 7, 12, 17, 31]}
+    aosoa = dict(soa, lanes=lanes)
+    run_pair(synth.INT6, f, soa, aosoa)
+    run_pair(synth.INT6, f, aosoa, soa)
+    g = float_fields(n, 6)
+    fs = {"kind": "bitpack_float", "exp": 8, "man": 12}
+    run_pair(synth.MIXED_F, g, fs, dict(fs, lanes=lanes))
+    run_pair(synth.MIXED_F, g, dict(fs, lanes=lanes), fs)
+
+
+def test_inside_a_split():
+    n = 4000 + 3
+    f = int_fields(n, 9)
+    m = {"kind": "split", "fields": [0, 2, 4], "inner": {"kind": "bitpack_int", "bits": 12, "lanes": 64},
+         "rest": {"kind": "soa_mb"}}
+    run_pair(synth.INT6, f, {"kind": "aos"}, m)
+    run_pair(synth.INT6, f, m, {"kind": "aos"})
+
+
+@pytest.mark.parametrize("tile,threads", [(128, 128), (1024, 256), (2048, 512)])
+def test_launch_shapes(tile, threads):
+    n = 20000 + 5
+    f = int_fields(n, 2, in_range=False)
+    m = {"kind": "bitpack_int", "bits": 0, "field_bits": [1, 3, 7, 12, 17, 31], "lanes": 128}
+    cfg = {"tile_records": tile, "src_stages": 2, "dst_stages": 2, "threads": threads, "ctas_per_sm": 1,
+           "engine": "value"}
+    run_pair(synth.INT6, f, {"kind": "soa_mb"}, m, cfg)
+    run_pair(synth.INT6, f, m, {"kind": "soa_mb"}, cfg)
+
+
+def test_many_tiles():
+    n = (1 << 20) + 3
+    f = int_fields(n, 4)
+    m = {"kind": "bitpack_int", "bits": 12, "lanes": 32}
+    run_pair(synth.INT6, f, {"kind": "soa_mb"}, m)
+    run_pair(synth.INT6, f, m, {"kind": "aos"})
