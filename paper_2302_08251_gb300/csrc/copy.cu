@@ -521,7 +521,27 @@ __device__ __forceinline__ LaneRun affine_run(const LeafDesc& L, uint32_t lane)
     return R;
 }
 
-// Whole-byte streams: a dense array of SZ-byte codes.
+// Where super-group g of a bit leaf starts, relative to super-group 0:
+// (g >> ksh) * bstride + (g & kmask) * step.  A SoA stream is one run (ksh
+// 31, kmask all ones: g * step); an AoSoA-organised leaf has 2^ksh
+// super-groups per run of L codes (L >= 32 V), runs bstride bytes apart.
+struct SgSteps {
+    uint32_t step, bstride, ksh, kmask;
+};
+
+__device__ __forceinline__ SgSteps sg_steps(const LeafDesc& L, uint32_t step, int V)
+{
+    if (L.lanes == 0) return SgSteps{step, 0u, 31u, 0xFFFFFFFFu};
+    const uint32_t ksh = L.lshift - 5u - (V == 4 ? 2u : (V == 2 ? 1u : 0u));
+    return SgSteps{step, L.bstride, ksh, (1u << ksh) - 1u};
+}
+
+__device__ __forceinline__ uint32_t sg_off(const SgSteps& S, uint32_t g)
+{
+    return (g >> S.ksh) * S.bstride + (g & S.kmask) * S.step;
+}
+
+// Whole-byte streams: a dense array of SZ-byte codes (per run).
 template <int V, int SZ>
 __device__ __forceinline__ LaneRun stream_run(const LeafDesc& L, uint32_t lane)
 {
@@ -529,7 +549,7 @@ __device__ __forceinline__ LaneRun stream_run(const LeafDesc& L, uint32_t lane)
     R.step = 32u * V * SZ;
     R.off = L.sbase + (uint32_t)V * lane * SZ;
     R.vstride = SZ;
-    R.vec = run_vec_ok<V, SZ>(R.off, R.step, R.vstride);
+    R.vec = run_vec_ok<V, SZ>(R.off, R.step, R.vstride) && (L.bstride % 16u == 0u);
     return R;
 }
 
@@ -765,20 +785,29 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
 
     LaneRun RA{}, RB{};
     ChunkLane KA{}, KB{};
+    SgSteps GA{}, GB{};
     uint32_t ca = 0u, cb = 0u, abase = 0u, bbase = 0u;
-    if (LK == FL_AFF) RA = affine_run<V, SZL>(LA, lane);
-    else if (LK == FL_AL) RA = stream_run<V, SZL>(LA, lane);
-    else {
+    if (LK == FL_AFF) {
+        RA = affine_run<V, SZL>(LA, lane);
+    } else if (LK == FL_AL) {
+        RA = stream_run<V, SZL>(LA, lane);
+        GA = sg_steps(LA, RA.step, V);
+    } else {
         ca = (uint32_t)V * wa;
         KA = chunk_lane(ca, lane, false);
         abase = sa + LA.sbase + 4u * KA.word;
+        GA = sg_steps(LA, 4u * ca, V);
     }
-    if (SK == FS_AFF) RB = affine_run<V, SZS>(LB, lane);
-    else if (SK == FS_AL) RB = stream_run<V, SZS>(LB, lane);
-    else {
+    if (SK == FS_AFF) {
+        RB = affine_run<V, SZS>(LB, lane);
+    } else if (SK == FS_AL) {
+        RB = stream_run<V, SZS>(LB, lane);
+        GB = sg_steps(LB, RB.step, V);
+    } else {
         cb = (uint32_t)V * wb;
         KB = chunk_lane(cb, lane, true);
         bbase = da + LB.sbase + 4u * lane;
+        GB = sg_steps(LB, 4u * cb, V);
     }
     const T amask = (T)low_bits64((int)wa), bmask = (T)low_bits64((int)wb);
 
@@ -795,7 +824,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
                 if (gg >= g1 || rec0 >= nvalid) continue;
             }
             if (LK == FL_BITS) {
-                const uint32_t p = abase + 4u * gg * ca;
+                const uint32_t p = abase + sg_off(GA, gg);
                 const uint32_t w0 = (uint32_t)lds<4>(p), w1 = (uint32_t)lds<4>(p + 4u), w2 = (uint32_t)lds<4>(p + 8u);
                 const uint64_t chunk = ((uint64_t)__funnelshift_r(w1, w2, KA.sh) << 32) | __funnelshift_r(w0, w1, KA.sh);
 #pragma unroll
@@ -804,7 +833,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
                     x[b][v] = (!CHECK || rec0 + v < nvalid) ? c : (T)0u;
                 }
             } else {
-                const uint32_t p = sa + RA.off + gg * RA.step;
+                const uint32_t p = sa + RA.off + (LK == FL_AL ? sg_off(GA, gg) : gg * RA.step);
                 if (!CHECK || rec0 + V <= nvalid) {
                     ld_run<V, SZL, T>(p, RA, x[b]);
                 } else {
@@ -826,7 +855,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
 #pragma unroll
                 for (int v = 0; v < V; ++v) chunk |= (uint64_t)(x[b][v] & bmask) << (v * wb);
                 const uint32_t lo = (uint32_t)chunk, hi = (uint32_t)(chunk >> 32);
-                const uint32_t q = bbase + 4u * gg * cb;
+                const uint32_t q = bbase + sg_off(GB, gg);
                 const uint32_t w0 = chunk_word<MANY>(lo, hi, cb, KB, 0);
                 if (lane < cb) sts<4>(q, w0);
                 if (cb > 32u) {
@@ -834,7 +863,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
                     if (lane + 32u < cb) sts<4>(q + 128u, w1);
                 }
             } else {
-                st_run<V, SZS, T>(da + RB.off + gg * RB.step, RB, x[b]);
+                st_run<V, SZS, T>(da + RB.off + (SK == FS_AL ? sg_off(GB, gg) : gg * RB.step), RB, x[b]);
             }
         }
     };
@@ -1050,9 +1079,10 @@ __device__ __noinline__ void zero_streams(const JobDesc& J, uint8_t* dimg)
             continue;
         }
         const uint32_t wpr = P.bytes / 4u;  // words per run
+        const uint32_t stride = J.dst.leaves[P.leaf].bstride;
         for (uint32_t w = ctid(); w < P.runs * wpr; w += cnum()) {
             const uint32_t run = w / wpr;
-            *reinterpret_cast<uint32_t*>(dimg + P.dst_sbase + run * P.run_stride + 4u * (w - run * wpr)) = 0u;
+            *reinterpret_cast<uint32_t*>(dimg + P.dst_sbase + run * stride + 4u * (w - run * wpr)) = 0u;
         }
     }
 }

@@ -130,17 +130,17 @@ enum FastKind : uint8_t {
 // A bit-stream destination leaf.  Specialised loops store whole words of the
 // stream; a generic item ORs its codes into it (unless the width is 8, 16,
 // 32 or 64 bits), and then the consumers zero the stream before every tile
-// (`ored`): `runs` runs of `bytes` bytes, `run_stride` apart, from
-// `dst_sbase` (one run for a SoA stream; one per block for AoSoA).
+// (`ored`): `runs` runs of `bytes` bytes from `dst_sbase`, the destination
+// leaf's bstride apart (one run for a SoA stream; one per block for AoSoA).
 struct PackDesc {
     uint32_t dst_sbase;  // destination image offset of the stream
     uint32_t bytes;      // bytes per run (a multiple of 4)
-    uint32_t run_stride;
-    uint16_t runs;
     uint8_t bits;
     uint8_t aligned;
     uint8_t ored;
-    uint8_t pad[7];
+    uint8_t leaf;        // destination leaf
+    uint16_t runs;
+    uint8_t pad[2];
 };
 
 struct SideDesc {

@@ -631,8 +631,6 @@ static bool fmt_is(int e, int m, int fe, int fm) { return e == fe && m == fm; }
 // The specialised loop a VALUE item can run in (FastKind), or FK_GENERIC.
 static int fast_kind(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
 {
-    // codes in AoSoA-organised bit blobs run in the generic loop
-    if ((A.kind == LEAF_BITS && A.lanes) || (B.kind == LEAF_BITS && B.lanes)) return FK_GENERIC;
     const bool a_aff = A.kind == LEAF_AFFINE, b_aff = B.kind == LEAF_AFFINE;
     const bool a_al = A.kind == LEAF_BITS && (A.bits == 8 || A.bits == 16 || A.bits == 32 || A.bits == 64);
     const bool b_al = B.kind == LEAF_BITS && (B.bits == 8 || B.bits == 16 || B.bits == 32 || B.bits == 64);
@@ -699,7 +697,10 @@ static void set_fast_kind(ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
         V = 16 / widest;
     }
     }
-    if (k != FK_GENERIC && affine_for(A, V) && affine_for(B, V)) {
+    // an AoSoA-organised bit leaf: a super-group of 32 V records must lie in
+    // one run of its L codes
+    auto runs_ok = [&](const LeafDesc& L) { return L.kind != LEAF_BITS || L.lanes == 0 || L.lanes >= 32u * V; };
+    if (k != FK_GENERIC && affine_for(A, V) && affine_for(B, V) && runs_ok(A) && runs_ok(B)) {
         it.fast = (uint8_t)k;
         it.vpl = (uint8_t)V;
     } else {
@@ -774,22 +775,16 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         P.dst_sbase = job->dst.leaves[g].sbase;
         P.aligned = (P.bits == 8 || P.bits == 16 || P.bits == 32 || P.bits == 64) ? 1 : 0;
         const LeafDesc& D = job->dst.leaves[g];
+        P.leaf = (uint8_t)g;
         if (D.lanes) {  // AoSoA organisation: tile / L runs of L codes
             P.bytes = D.lanes * P.bits / 8;
             P.runs = (uint16_t)(tile / D.lanes);
-            P.run_stride = D.bstride;
         } else {
             P.bytes = (uint32_t)((uint64_t)tile * P.bits / 8);
             P.runs = 1;
-            P.run_stride = 0;
         }
     }
     job->code_bytes = 0;
-    job->seg = 0;
-    for (int g = 0; g < job->src.nleaves; ++g)
-        if (job->src.leaves[g].kind == LEAF_BITS && job->src.leaves[g].lanes) job->seg = 1;
-    for (int g = 0; g < job->dst.nleaves; ++g)
-        if (job->dst.leaves[g].kind == LEAF_BITS && job->dst.leaves[g].lanes) job->seg = 1;
 
     // Items: one per leaf, or one per byte where a side splits bytes.
     const int nf = (int)src.types.size();
@@ -907,6 +902,15 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
             set_fast_kind(it, job->src.leaves[a.first], job->dst.leaves[b.first]);
             if (!add(it)) return too_many();
         }
+    }
+    // A generic item on an AoSoA-organised bit leaf runs in kernel mode 1.
+    job->seg = 0;
+    for (int k = 0; k < job->nitems; ++k) {
+        const ItemDesc& it = job->items[k];
+        if (it.op != ITEM_VALUE || it.fast != FK_GENERIC) continue;
+        const LeafDesc& A = job->src.leaves[it.src_leaf];
+        const LeafDesc& B = job->dst.leaves[it.dst_leaf];
+        if ((A.kind == LEAF_BITS && A.lanes) || (B.kind == LEAF_BITS && B.lanes)) job->seg = 1;
     }
     for (int k = 0; k < job->nitems; ++k) {
         const ItemDesc& it = job->items[k];

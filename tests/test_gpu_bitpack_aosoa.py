@@ -119,9 +119,43 @@ def test_launch_shapes(tile, threads):
     run_pair(synth.INT6, f, m, {"kind": "soa_mb"}, cfg)
 
 
-def test_many_tiles():
+@pytest.mark.parametrize("lanes", [32, 256])
+def test_many_tiles(lanes):
+    # lanes 32: the generic loop (a 128-record super-group spans runs); 256:
+    # the word-assembling loops, two super-groups per run
     n = (1 << 20) + 3
     f = int_fields(n, 4)
-    m = {"kind": "bitpack_int", "bits": 12, "lanes": 32}
+    m = {"kind": "bitpack_int", "bits": 12, "lanes": lanes}
     run_pair(synth.INT6, f, {"kind": "soa_mb"}, m)
     run_pair(synth.INT6, f, m, {"kind": "aos"})
+    g = float_fields(n // 4, 5)
+    fm = {"kind": "bitpack_float", "exp": 8, "man": 23, "lanes": lanes}
+    run_pair(synth.MIXED_F, g, {"kind": "soa_mb"}, fm)
+    run_pair(synth.MIXED_F, g, fm, {"kind": "soa_mb"})
+
+
+@pytest.mark.parametrize("noalloc", [False, True])
+def test_batched_with_plain_pairs(noalloc):
+    # AoSoA-organised bit jobs (kernel mode 1, and mode 0 where the fast
+    # loops cover them) batched beside plain re-layouts (modes 0 and 2/4)
+    cases = []
+    for k, (m, n) in enumerate([(INT_MAPS[0], 3001), (INT_MAPS[2], 777), ({"kind": "aos"}, 5000),
+                                ({"kind": "bitpack_int", "bits": 12, "lanes": 256}, 4099),
+                                ({"kind": "aosoa", "lanes": 32}, 1200)]):
+        f = int_fields(n, 30 + k, in_range=False)
+        src_o = oracle_view(synth.INT6, {"kind": "soa_mb"}, f)
+        dst_o = oracle.OracleView(synth.INT6, m, n)
+        src_o.copy_to(dst_o)
+        cases.append((device_view_of(src_o), empty_device_view(synth.INT6, m, n), dst_o, m))
+    pairs = [(s, d) for s, d, _, _ in cases]
+    if noalloc:
+        llgb.llgb_batch_copy_noalloc(pairs)
+    else:
+        batch = llgb.Batch(pairs)
+        assert 1 <= batch.info()["launches"] <= 4
+        batch.launch()
+    sync_and_check_status()
+    for _, d, want, m in cases:
+        assert_same_bytes(d, want, str(m))
+    if not noalloc:
+        batch.close()
