@@ -754,7 +754,9 @@ __device__ __forceinline__ T fast_convert(T x, const ConvRegs& c)
 // [g0, g1) of the tile; records at or past nvalid read as zero (and so are
 // written as zero).  Super-groups whose records are all valid run without
 // any checks.
-template <int LK, int SK, int SZL, int SZS, int CV, bool CONV_ON_LOAD, int V, bool MANY>
+// RUNS: a stream side is AoSoA-organised (super-group offsets by sg_off); a
+// separate instantiation, so that SoA streams keep one multiply per address.
+template <int LK, int SK, int SZL, int SZS, int CV, bool CONV_ON_LOAD, int V, bool MANY, bool RUNS = false>
 __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
                                        uint32_t g0, uint32_t g1, uint32_t nvalid)
 {
@@ -824,7 +826,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
                 if (gg >= g1 || rec0 >= nvalid) continue;
             }
             if (LK == FL_BITS) {
-                const uint32_t p = abase + sg_off(GA, gg);
+                const uint32_t p = abase + (RUNS ? sg_off(GA, gg) : gg * GA.step);
                 const uint32_t w0 = (uint32_t)lds<4>(p), w1 = (uint32_t)lds<4>(p + 4u), w2 = (uint32_t)lds<4>(p + 8u);
                 const uint64_t chunk = ((uint64_t)__funnelshift_r(w1, w2, KA.sh) << 32) | __funnelshift_r(w0, w1, KA.sh);
 #pragma unroll
@@ -833,7 +835,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
                     x[b][v] = (!CHECK || rec0 + v < nvalid) ? c : (T)0u;
                 }
             } else {
-                const uint32_t p = sa + RA.off + (LK == FL_AL ? sg_off(GA, gg) : gg * RA.step);
+                const uint32_t p = sa + RA.off + (RUNS && LK == FL_AL ? sg_off(GA, gg) : gg * RA.step);
                 if (!CHECK || rec0 + V <= nvalid) {
                     ld_run<V, SZL, T>(p, RA, x[b]);
                 } else {
@@ -855,7 +857,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
 #pragma unroll
                 for (int v = 0; v < V; ++v) chunk |= (uint64_t)(x[b][v] & bmask) << (v * wb);
                 const uint32_t lo = (uint32_t)chunk, hi = (uint32_t)(chunk >> 32);
-                const uint32_t q = bbase + sg_off(GB, gg);
+                const uint32_t q = bbase + (RUNS ? sg_off(GB, gg) : gg * GB.step);
                 const uint32_t w0 = chunk_word<MANY>(lo, hi, cb, KB, 0);
                 if (lane < cb) sts<4>(q, w0);
                 if (cb > 32u) {
@@ -863,7 +865,7 @@ __device__ __noinline__ void fast_loop(const ItemDesc& I, const JobDesc& J, cons
                     if (lane + 32u < cb) sts<4>(q + 128u, w1);
                 }
             } else {
-                st_run<V, SZS, T>(da + RB.off + (SK == FS_AL ? sg_off(GB, gg) : gg * RB.step), RB, x[b]);
+                st_run<V, SZS, T>(da + RB.off + (RUNS && SK == FS_AL ? sg_off(GB, gg) : gg * RB.step), RB, x[b]);
             }
         }
     };
@@ -1001,8 +1003,14 @@ __device__ __noinline__ void split_loop(const ItemDesc& I, const JobDesc& J, con
 __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
                                          uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
-#define LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, V, MANY) \
-    fast_loop<LK, SK, SZL, SZS, CV, OL, V, MANY>(I, J, simg, dimg, q0 * (4u / V), q1 * (4u / V), nvalid)
+#define LLGB_FAST_V(LK, SK, SZL, SZS, CV, OL, V, MANY)                                                 \
+    do {                                                                                                \
+        if (I.runs)                                                                                     \
+            fast_loop<LK, SK, SZL, SZS, CV, OL, V, MANY, true>(I, J, simg, dimg, q0 * (4u / V), q1 * (4u / V), \
+                                                               nvalid);                                 \
+        else                                                                                            \
+            fast_loop<LK, SK, SZL, SZS, CV, OL, V, MANY>(I, J, simg, dimg, q0 * (4u / V), q1 * (4u / V), nvalid); \
+    } while (0)
 // streams: V from the width; chunks under 32 bits (widths below 8) take MANY
 #define LLGB_FAST(K, LK, SK, SZL, SZS, CV, OL)                                             \
     case K:                                                                                \

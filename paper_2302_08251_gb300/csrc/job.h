@@ -83,7 +83,8 @@ struct ItemDesc {
     uint8_t d_bits;      // destination bits (S_BITS_*)
     uint8_t fast;        // FastKind of the specialised loop, FK_GENERIC if none
     uint8_t vpl;         // specialised loop: consecutive records per lane (1, 2, 4)
-    uint8_t pad[2];
+    uint8_t runs;        // specialised loop: a bit leaf of the item is AoSoA-organised
+    uint8_t pad;
 };
 
 // Specialised VALUE loops (element sizes and conversion fixed at compile time).

@@ -703,6 +703,7 @@ static void set_fast_kind(ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
     if (k != FK_GENERIC && affine_for(A, V) && affine_for(B, V) && runs_ok(A) && runs_ok(B)) {
         it.fast = (uint8_t)k;
         it.vpl = (uint8_t)V;
+        it.runs = ((A.kind == LEAF_BITS && A.lanes) || (B.kind == LEAF_BITS && B.lanes)) ? 1 : 0;
     } else {
         it.fast = FK_GENERIC;
         it.vpl = 0;
