@@ -854,10 +854,36 @@ def main():
                     help="skip the n-body, e2e and CPU-baseline legs (profiling runs)")
     ap.add_argument("--only", default=None, help="run only rows whose name contains this")
     ap.add_argument("--scale", type=int, default=1, help="divide record counts (profiling)")
+    ap.add_argument("--nbody-only", action="store_true",
+                    help="run only W + K n-body steps on 65,536 SoA particles (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.nbody_only:
+        return run_nbody_only(args)
     return run_gpu(args)
+
+
+def run_nbody_only(args):
+    """W + K plain n-body steps on 65,536 particles through a SoA view, for
+    profiling the update and move kernels; prints the mean step time."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, synth
+    n = 65536
+    rec = llgb.Record(synth.PARTICLE)
+    fields = synth.device_fields("particle", n, 7, device="cuda")
+    v = llgb.View(rec, {"kind": "soa_mb"}, (n,), blobs=[f.view(torch.uint8) for f in fields])
+    for _ in range(args.warmup):
+        llgb.llgb_nbody_step(v, 0.01, 1e-4)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        llgb.llgb_nbody_step(v, 0.01, 1e-4)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"nbody_ms_per_step": round(a.elapsed_time(b) / max(1, args.steps), 4), "n": n}))
+    return 0
 
 
 if __name__ == "__main__":

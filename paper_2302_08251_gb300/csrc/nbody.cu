@@ -150,13 +150,25 @@ constexpr int kI = kW * kIPT;       // particles per block
 constexpr int kParts = 8;           // j slices per block, one per warp
 constexpr int kJ = 128;             // tile extent (4 records per loading lane)
 
+// 1 / sqrt(x) by the SFU's approximation.  x = |d|^2 + eps^2 >= eps^2 is never
+// subnormal for a softening eps above 1e-19, so the flush-to-zero form is
+// taken: it gives rsqrtf's result bits for every normal x and skips
+// rsqrtf's subnormal-input handling (about 3.5 of 17 instructions per
+// interaction).
+__device__ __forceinline__ float rsqrt_normal(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Interaction of particle p with record b = {x, y, z, m}, summed into t.
 __device__ __forceinline__ void interact(const float4 b, float px, float py, float pz, float eps2, float& tx,
                                          float& ty, float& tz)
 {
     const float dx = b.x - px, dy = b.y - py, dz = b.z - pz;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_normal(r2);
     const float s = b.w * (rinv * rinv * rinv);
     tx = fmaf(dx, s, tx);
     ty = fmaf(dy, s, ty);
