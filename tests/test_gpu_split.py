@@ -1,6 +1,7 @@
 """GPU parity of copies through Null and Split views (Sec. 3) against the
 oracle, byte for byte (every destination blob pre-filled with 0xAB).
 """
+import numpy as np
 import pytest
 
 import oracle
@@ -80,3 +81,17 @@ def test_int_bitpack_float_soa_split_many_tiles():
     # many tiles per CTA at full-size-like tiles: bit streams beside plain arrays
     run_pair({"kind": "soa_mb"}, INT_FLOAT, 400000 + 11)
     run_pair(INT_FLOAT, {"kind": "aos"}, 400000 + 11)
+
+
+def test_particle_cache_view_on_the_gpu():
+    # the subset-field cache view of the n-body consumer, filled by the copy
+    # kernel from a SoA particle view: {x, y, z, m} records, no velocities
+    n = 65536 + 5
+    cols = synth.particles(n, 12)
+    cache = {"kind": "split", "fields": [0, 1, 2, 6], "inner": {"kind": "aos"}, "rest": {"kind": "null"}}
+    src = device_view_of(oracle_view(synth.PARTICLE, {"kind": "soa_mb"}, cols))
+    dst = empty_device_view(synth.PARTICLE, cache, n)
+    llgb.llgb_copy(src, dst)
+    sync_and_check_status()
+    want = np.stack([cols[0], cols[1], cols[2], cols[6]], axis=1).astype(np.float32)
+    assert dst.blob_bytes()[0].tobytes() == want.tobytes()

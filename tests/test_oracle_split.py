@@ -89,3 +89,18 @@ def test_nested_split_and_wrapped_parts():
 def test_split_needs_leaves_on_both_sides(bad):
     with pytest.raises(ValueError):
         oracle.OracleView(REC, bad, 4)
+
+
+def test_particle_cache_view_holds_position_and_mass_records():
+    # A subset-field cache view (Sec. 3, Null with Split): pos and mass as
+    # AoS records, velocities dropped.  Its blob is the array of {x, y, z, m}
+    # records the n-body consumer stages per tile.
+    n = 130
+    cols = synth.particles(n, 4)
+    cache = {"kind": "split", "fields": [0, 1, 2, 6], "inner": {"kind": "aos"}, "rest": {"kind": "null"}}
+    v = oracle_view(synth.PARTICLE, cache, cols)
+    want = np.stack([cols[0], cols[1], cols[2], cols[6]], axis=1).astype(np.float32)
+    assert v.blob_sizes == [16 * n]
+    assert bytes(v.blobs[0]) == want.tobytes()
+    for f in (3, 4, 5):
+        assert not v.field_values(f).any()
