@@ -273,3 +273,53 @@ def test_bitpacked_aosoa_needs_power_of_two_lanes_from_32_to_1024(lanes):
     with pytest.raises(llgb.LlgbError) as err:
         host_view(synth.INT6, {"kind": "bitpack_int", "bits": 12, "lanes": lanes}, 100)
     assert err.value.status == llgb.ERR_UNSUPPORTED
+
+
+def _handle(record, mapping, n):
+    rec = llgb.Record(record)
+    keep = []
+    e = llgb.extents_desc((n,))
+    m = llgb.mapping_desc(mapping, keep)
+    h = ctypes.c_void_p()
+    llgb.check(llgb.lib().llgb_view_create(rec.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(h)))
+    return rec, h
+
+
+def test_nbody_phases_reject_an_unknown_traversal_before_anything_else():
+    L = llgb.lib()
+    rec, h = _handle(synth.PARTICLE, {"kind": "aos"}, 100)
+    assert L.llgb_nbody_move(h, 0.1, 2, None) == llgb.ERR_INVALID_ARG
+    assert L.llgb_nbody_update(h, 0.1, 0.1, -1, None) == llgb.ERR_INVALID_ARG
+    # a known traversal gets as far as the (unbound) view
+    assert L.llgb_nbody_move(h, 0.1, 1, None) == llgb.ERR_UNBOUND
+    L.llgb_view_destroy(h)
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 48, 64])
+def test_nbody_takes_aosoa_views_of_any_lane_count(lanes):
+    L = llgb.lib()
+    rec, h = _handle(synth.PARTICLE, {"kind": "aosoa", "lanes": lanes}, 1000)
+    assert L.llgb_nbody_step(h, 0.01, 1e-4, None) == llgb.ERR_UNBOUND  # accepted, then needs memory
+    L.llgb_view_destroy(h)
+
+
+@pytest.mark.parametrize("m", [{"kind": "bitpack_int", "bits": 12},
+                               {"kind": "split", "fields": [0], "inner": {"kind": "aos"}, "rest": {"kind": "null"}}])
+def test_nbody_rejects_bitpacked_and_split_particle_views(m):
+    L = llgb.lib()
+    rec = [(f"l{k}", "u32") for k in range(7)] if m["kind"] == "bitpack_int" else synth.PARTICLE
+    r, h = _handle(rec, m, 100)
+    assert L.llgb_nbody_step(h, 0.01, 1e-4, None) in (llgb.ERR_INVALID_ARG, llgb.ERR_UNSUPPORTED)
+    L.llgb_view_destroy(h)
+
+
+@pytest.mark.parametrize("lanes", [256, 1024])
+def test_copy_config_tiles_hold_whole_bit_blocks(lanes):
+    L = llgb.lib()
+    _, a = _handle(synth.INT6, {"kind": "soa_mb"}, 1 << 20)
+    _, b = _handle(synth.INT6, {"kind": "bitpack_int", "bits": 12, "lanes": lanes}, 1 << 20)
+    c = llgb.LaunchConfig()
+    llgb.check(L.llgb_copy_config(a, b, ctypes.byref(c)))
+    assert c.tile_records % lanes == 0 and c.tile_records % 128 == 0
+    L.llgb_view_destroy(a)
+    L.llgb_view_destroy(b)
