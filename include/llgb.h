@@ -330,7 +330,9 @@ llgb_status llgb_autotune_clear(void);
  * every i, v_i += dt * sum_j m_j (p_j - p_i) / (|p_j - p_i|^2 + eps^2)^(3/2),
  * j over all particles; then move: p_i += dt * v_i.  FP32 arithmetic; the
  * result bits do not depend on the mapping.  Queued on `stream` (two
- * kernels).  Errors: INVALID_ARG, UNBOUND, UNSUPPORTED, CUDA. */
+ * kernels).  Errors: INVALID_ARG (not the particle record), UNBOUND,
+ * UNSUPPORTED (a bit-packed, Bytesplit, ChangeType or Split view, or
+ * n >= 2^31), CUDA. */
 llgb_status llgb_nbody_step(llgb_view* particles, float eps, float dt, void* stream);
 
 /* The two phases of llgb_nbody_step apart, each with a chosen traversal of
