@@ -245,7 +245,8 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
         if ((job->src.img_bytes <= side_cap && job->dst.img_bytes <= side_cap) || tile <= q) break;
         tile -= q;
     }
-    *mode = job->ntiles <= kFewTiles ? 0 : job_mode(*job, threads);
+    // few-tile jobs take the value loops; run-addressed bit jobs need mode 1 for them
+    *mode = job->ntiles <= kFewTiles ? (job->seg ? 1 : 0) : job_mode(*job, threads);
     return LLGB_OK;
 }
 

@@ -139,9 +139,20 @@ def test_batched_with_plain_pairs(noalloc):
     # AoSoA-organised bit jobs (kernel mode 1, and mode 0 where the fast
     # loops cover them) batched beside plain re-layouts (modes 0 and 2/4)
     cases = []
+    # the 1- and 100-record jobs are few-tile jobs (planned straight into the value loops)
     for k, (m, n) in enumerate([(INT_MAPS[0], 3001), (INT_MAPS[2], 777), ({"kind": "aos"}, 5000),
                                 ({"kind": "bitpack_int", "bits": 12, "lanes": 256}, 4099),
-                                ({"kind": "aosoa", "lanes": 32}, 1200)]):
+                                ({"kind": "aosoa", "lanes": 32}, 1200), (INT_MAPS[0], 100), (INT_MAPS[4], 1),
+                                (FLOAT_MAPS[3], 0)]):
+        if m["kind"] == "bitpack_float":
+            f = float_fields(max(n, 1), 40)
+            f = [c[:n] for c in f]
+            src_o = oracle_view(synth.MIXED_F, {"kind": "soa_mb"}, f)
+            dst_o = oracle.OracleView(synth.MIXED_F, m, n)
+            src_o.copy_to(dst_o)
+            src = device_view_of(src_o) if n else empty_device_view(synth.MIXED_F, {"kind": "soa_mb"}, 0)
+            cases.append((src, empty_device_view(synth.MIXED_F, m, n), dst_o, m))
+            continue
         f = int_fields(n, 30 + k, in_range=False)
         src_o = oracle_view(synth.INT6, {"kind": "soa_mb"}, f)
         dst_o = oracle.OracleView(synth.INT6, m, n)
