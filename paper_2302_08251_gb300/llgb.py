@@ -159,7 +159,16 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
 
 
 def mapping_desc(m: dict, keep: list) -> MappingDesc:
-    """Build an llgb_mapping_desc from the plain-dict mapping description."""
+    """Build an llgb_mapping_desc from the plain-dict mapping description:
+    {"kind": "aos", "packed": 0|1}, {"kind": "soa_sb", "subarray_align": a},
+    {"kind": "soa_mb"}, {"kind": "aosoa", "lanes": L},
+    {"kind": "bitpack_int", "bits": b, "field_bits": [...], "lanes": L},
+    {"kind": "bitpack_float", "exp": E, "man": M, "field_exp": [...],
+    "field_man": [...], "lanes": L} (bit-packed "lanes": 0 or absent = SoA
+    streams, L = the AoSoA organisation), {"kind": "bytesplit", "inner": m},
+    {"kind": "changetype", "ct": [(from, to), ...], "inner": m},
+    {"kind": "null"}, {"kind": "split", "fields": [...], "inner": m,
+    "rest": m}.  `keep` collects the ctypes objects the descriptor points to."""
     c = MappingDesc()
     c.kind = KIND_ID[m["kind"]]
     c.aos_packed = int(m.get("packed", 0))
