@@ -229,6 +229,23 @@ def profiled_traffic():
         return None
 
 
+def max_over_ranks(ms, world):
+    """The slowest rank's time: what the whole job waited for (all-reduce
+    MAX over the process group; the value itself when world == 1)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank, world, ms_per_step):
+    """Whole-job GB/s: every rank moves bytes_per_rank per step (weak
+    scaling), and the step lasts as long as the slowest rank."""
+    return bytes_per_rank * world / (ms_per_step * 1e-3) / 1e9
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -367,12 +384,9 @@ def run_gpu(args):
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [[events[s][k][0].elapsed_time(events[s][k][1]) for k in range(nrows)]
                  for s in range(args.steps)]
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / args.steps
-    value = wl.bytes * world / (ms_per_step * 1e-3) / 1e9
+    value = job_throughput(wl.bytes, world, ms_per_step)
 
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
