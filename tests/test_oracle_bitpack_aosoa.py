@@ -13,7 +13,6 @@ import os
 import numpy as np
 import pytest
 
-import oracle
 from paper_2302_08251_gb300 import synth
 from helpers import bits_of, oracle_view
 
