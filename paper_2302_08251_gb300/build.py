@@ -2,7 +2,7 @@
 
 Translation units are compiled in parallel, then linked into
 ``paper_2302_08251_gb300/_build/libllgb.so`` (static CUDA runtime, so the
-library needs nothing beyond the driver at run time).
+library needs nothing beyond the NVIDIA driver at run time).
 """
 from __future__ import annotations
 
