@@ -255,6 +255,29 @@ typedef struct llgb_launch_config {
 llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst,
                              llgb_launch_config* out);
 
+/* What llgb_copy (with cfg, or the library's shape when cfg is NULL or all
+ * zero) and a batch entry would run for this pair, planned on the host only:
+ * no memory need be bound, nothing is launched.
+ *   kernel_mode, batch_kernel_mode: 0 value loops; 1 value loops with
+ *     AoSoA-organised bit leaves in the generic loop; 2 / 4 gather programs
+ *     of 2 / 4 source words (a single copy, and the same pair in a batch);
+ *   tile_records, tiles: the tiling; items: work items per tile, of which
+ *     generic_items convert values record by record (the others run loops
+ *     specialised at compile time, or move bytes).
+ * All zero for n = 0.  Errors: INVALID_ARG, MISMATCH, UNSUPPORTED. */
+typedef struct llgb_plan_info {
+    int32_t kernel_mode;
+    int32_t batch_kernel_mode;
+    int32_t tile_records;
+    int32_t items;
+    int32_t generic_items;
+    int32_t reserved;
+    uint64_t tiles;
+} llgb_plan_info;
+
+llgb_status llgb_copy_plan(const llgb_view* src, const llgb_view* dst, const llgb_launch_config* cfg,
+                           llgb_plan_info* out);
+
 /* llgb_copy with an explicit launch shape.  Errors as llgb_copy, plus
  * INVALID_ARG for a shape that does not fit the pair. */
 llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst,

@@ -259,6 +259,17 @@ llgb_status check_pair(const llgb_view* src, const llgb_view* dst)
     return LLGB_OK;
 }
 
+// Kernel mode of a single copy's job under launch shape c on `grid` CTAs.
+int copy_mode(const JobDesc& J, const llgb_launch_config& c, int grid)
+{
+    int mode = c.engine == LLGB_ENGINE_VALUE ? (J.seg ? 1 : 0) : job_mode(J, c.threads);
+    // a gather program is built once per job by every CTA: with at most two
+    // tiles per CTA that costs more than it saves, and the value loops
+    // (whole-element moves) need no program
+    if (c.engine == LLGB_ENGINE_AUTO && mode >= 2 && J.ntiles <= 2u * (uint32_t)grid) mode = 0;
+    return mode;
+}
+
 llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_config* cfg_in, void* stream)
 {
     llgb_status st = check_pair(src, dst);
@@ -294,11 +305,7 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     args.dst_stages = (uint16_t)c.dst_stages;
     const int sms = dev.sms > 0 ? dev.sms : 152;
     const int grid = (int)std::min<uint64_t>(args.total_tiles, (uint64_t)sms * c.ctas_per_sm);
-    int mode = c.engine == LLGB_ENGINE_VALUE ? (args.job.seg ? 1 : 0) : job_mode(args.job, c.threads);
-    // a gather program is built once per job by every CTA: with at most two
-    // tiles per CTA that costs more than it saves, and the value loops
-    // (whole-element moves) need no program
-    if (c.engine == LLGB_ENGINE_AUTO && mode >= 2 && args.total_tiles <= 2u * (uint32_t)grid) mode = 0;
+    const int mode = copy_mode(args.job, c, grid);
     if (c.threads / 32 <= (int)producer_warps(mode))
         return fail(LLGB_ERR_INVALID_ARG, "launch config leaves no consumer warp");
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
@@ -598,6 +605,45 @@ llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst, llgb_la
         return fail(LLGB_ERR_MISMATCH, "views differ in record or count");
     if (tuned_config(src, dst, out)) return LLGB_OK;
     return default_config(src, dst, out);
+}
+
+llgb_status llgb_copy_plan(const llgb_view* src, const llgb_view* dst, const llgb_launch_config* cfg,
+                           llgb_plan_info* out)
+{
+    try {
+        if (!src || !dst || !out) return fail(LLGB_ERR_INVALID_ARG, "null argument");
+        if (!same_record(src->plan, dst->plan) || src->plan.n != dst->plan.n)
+            return fail(LLGB_ERR_MISMATCH, "views differ in record or count");
+        *out = llgb_plan_info{};
+        if (src->plan.n == 0) return LLGB_OK;
+        llgb_launch_config c{};
+        if (cfg && cfg->tile_records != 0) {
+            c = *cfg;
+        } else if (!tuned_config(src, dst, &c)) {
+            const llgb_status st = default_config(src, dst, &c);
+            if (st != LLGB_OK) return st;
+        }
+        static thread_local JobDesc J;
+        std::string why;
+        llgb_status st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, (uint32_t)c.tile_records, &J, &why);
+        if (st != LLGB_OK) return fail(st, why);
+        const DeviceInfo dev = device_info();
+        const int sms = dev.sms > 0 ? dev.sms : 152;
+        const int grid = (int)std::min<uint64_t>(J.ntiles, (uint64_t)sms * c.ctas_per_sm);
+        out->kernel_mode = copy_mode(J, c, grid);
+        out->tile_records = (int32_t)J.tile;
+        out->tiles = J.ntiles;
+        out->items = J.nitems;
+        for (int k = 0; k < J.nitems; ++k)
+            if (J.items[k].op == ITEM_VALUE && J.items[k].fast == FK_GENERIC) ++out->generic_items;
+        int bmode = 0;
+        st = plan_batch_job(src, dst, &J, &bmode, 256);
+        if (st != LLGB_OK) return st;
+        out->batch_kernel_mode = bmode;
+        return LLGB_OK;
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
 }
 
 llgb_status llgb_pack(const llgb_view* plain, llgb_view* packed, void* stream)

@@ -47,6 +47,12 @@ class Extents(ctypes.Structure):
                 ("ext", ctypes.c_uint64 * 4)]
 
 
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("kernel_mode", ctypes.c_int32), ("batch_kernel_mode", ctypes.c_int32),
+                ("tile_records", ctypes.c_int32), ("items", ctypes.c_int32),
+                ("generic_items", ctypes.c_int32), ("reserved", ctypes.c_int32), ("tiles", ctypes.c_uint64)]
+
+
 class MappingDesc(ctypes.Structure):
     pass
 
@@ -89,7 +95,7 @@ EXPORTS = [
     "llgb_view_bind", "llgb_copy", "llgb_pack", "llgb_unpack", "llgb_copy_config",
     "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
     "llgb_batch_create", "llgb_batch_launch", "llgb_batch_info", "llgb_batch_destroy",
-    "llgb_autotune", "llgb_autotune_clear", "llgb_batch_copy_noalloc",
+    "llgb_autotune", "llgb_autotune_clear", "llgb_batch_copy_noalloc", "llgb_copy_plan",
 ]
 
 _lib = None
@@ -127,6 +133,7 @@ def lib():
         for name in ("llgb_copy", "llgb_pack", "llgb_unpack"):
             getattr(L, name).argtypes = [p, p, p]
         L.llgb_copy_config.argtypes = [p, p, ctypes.POINTER(LaunchConfig)]
+        L.llgb_copy_plan.argtypes = [p, p, ctypes.POINTER(LaunchConfig), ctypes.POINTER(PlanInfo)]
         L.llgb_copy_with.argtypes = [p, p, ctypes.POINTER(LaunchConfig), p]
         L.llgb_nbody_step.argtypes = [p, ctypes.c_float, ctypes.c_float, p]
         L.llgb_nbody_step_instrumented.argtypes = [p, ctypes.c_float, ctypes.c_float, p, i32, p, u64, p]
@@ -313,6 +320,25 @@ def llgb_pack(plain: View, packed: View, stream=None) -> None:
 
 def llgb_unpack(packed: View, plain: View, stream=None) -> None:
     check(lib().llgb_unpack(packed.handle, plain.handle, _stream_ptr(stream)))
+
+
+def llgb_copy_plan(src: View, dst: View, cfg: dict | None = None) -> dict:
+    """Host-only plan of llgb_copy(src, dst) (and of the pair as a batch
+    entry): kernel modes, tiling and item counts; nothing is launched."""
+    return plan_info(src.handle, dst.handle, cfg)
+
+
+def plan_info(src_handle, dst_handle, cfg: dict | None = None) -> dict:
+    """llgb_copy_plan on raw view handles (bound or not)."""
+    info = PlanInfo()
+    c = None
+    if cfg is not None:
+        c = LaunchConfig()
+        for k, v in cfg.items():
+            setattr(c, k, ENGINES[v] if k == "engine" else int(v))
+    check(lib().llgb_copy_plan(src_handle, dst_handle, ctypes.byref(c) if c is not None else None,
+                               ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in PlanInfo._fields_ if k != "reserved"}
 
 
 def llgb_copy_config(src: View, dst: View) -> dict:

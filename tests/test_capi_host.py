@@ -323,3 +323,58 @@ def test_copy_config_tiles_hold_whole_bit_blocks(lanes):
     assert c.tile_records % lanes == 0 and c.tile_records % 128 == 0
     L.llgb_view_destroy(a)
     L.llgb_view_destroy(b)
+
+
+# ---- planner decisions, read with llgb_copy_plan (host only) ----
+
+def plan_of(record, src_map, dst_map, n, cfg=None):
+    _, a = _handle(record, src_map, n)
+    _, b = _handle(record, dst_map, n)
+    try:
+        return llgb.plan_info(a, b, cfg)
+    finally:
+        llgb.lib().llgb_view_destroy(a)
+        llgb.lib().llgb_view_destroy(b)
+
+
+def test_plan_affine_pairs_take_gather_programs():
+    for src, dst in (({"kind": "aos"}, {"kind": "soa_mb"}), ({"kind": "soa_mb"}, {"kind": "aos"})):
+        p = plan_of(synth.CFD, src, dst, 1 << 24)
+        assert p["kernel_mode"] in (2, 4), (src, dst)
+        assert p["generic_items"] == 0 and p["tiles"] * p["tile_records"] >= 1 << 24
+    # as a batch entry (programs sized for 256-thread CTAs) SoA -> AoS keeps
+    # its gather programs; AoS -> SoA keeps its 1152-record tile, which 256
+    # threads cannot cover, and moves bytes in the value loops
+    assert plan_of(synth.CFD, {"kind": "soa_mb"}, {"kind": "aos"}, 1 << 24)["batch_kernel_mode"] in (2, 4)
+    assert plan_of(synth.CFD, {"kind": "aos"}, {"kind": "soa_mb"}, 1 << 24)["batch_kernel_mode"] == 0
+
+
+def test_plan_few_tiles_take_the_value_loops():
+    p = plan_of(synth.CFD, {"kind": "aos"}, {"kind": "soa_mb"}, 300)
+    assert p["kernel_mode"] == 0 and p["batch_kernel_mode"] == 0
+
+
+def test_plan_bit_streams_run_specialised_loops_in_mode_0():
+    for m in ({"kind": "bitpack_int", "bits": 12}, {"kind": "bitpack_int", "bits": 12, "lanes": 256}):
+        p = plan_of(synth.INT6, {"kind": "soa_mb"}, m, 1 << 20)
+        assert p["kernel_mode"] == 0 and p["generic_items"] == 0 and p["items"] == 6, m
+
+
+@pytest.mark.parametrize("n", [1, 100, 1 << 20])
+def test_plan_short_bit_runs_take_mode_1_also_in_batches(n):
+    # 32-lane runs hold a quarter of a 128-record super-group: generic loop,
+    # kernel mode 1, however few the tiles
+    p = plan_of(synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12, "lanes": 32}, n)
+    assert p["kernel_mode"] == 1 and p["batch_kernel_mode"] == 1 and p["generic_items"] == 6
+
+
+def test_plan_engine_value_keeps_run_addressed_jobs_in_mode_1():
+    cfg = {"tile_records": 1024, "src_stages": 2, "dst_stages": 2, "threads": 512, "ctas_per_sm": 1,
+           "engine": "value"}
+    p = plan_of(synth.INT6, {"kind": "bitpack_int", "bits": 7, "lanes": 64}, {"kind": "aos"}, 50000, cfg)
+    assert p["kernel_mode"] == 1 and p["tile_records"] == 1024
+
+
+def test_plan_of_an_empty_pair_is_zero():
+    assert plan_of(synth.INT6, {"kind": "aos"}, {"kind": "soa_mb"}, 0) == {
+        "kernel_mode": 0, "batch_kernel_mode": 0, "tile_records": 0, "items": 0, "generic_items": 0, "tiles": 0}
