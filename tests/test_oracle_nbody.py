@@ -146,6 +146,84 @@ def test_access_counts_match_the_enumerated_schedule(n):
     assert np.array_equal(oracle.nbody_access_counts(n), want)
 
 
+def plain_loop_accesses(n):
+    """Every access of the paper's plain update loop (Sec. 5, Fig. 2: for each
+    particle i, its position, then every particle j's position and mass, then
+    i's velocity loaded, updated and stored) followed by the move (each
+    particle's position and velocity loaded, its position stored).  Written
+    as the nested i / j loop itself, with no notion of a tile or block."""
+    ev = []
+    for i in range(n):
+        ev += [(i, f, False) for f in (0, 1, 2)]
+        for j in range(n):
+            ev += [(j, f, False) for f in (0, 1, 2, 6)]
+        ev += [(i, f, False) for f in (3, 4, 5)] + [(i, f, True) for f in (3, 4, 5)]
+    for i in range(n):
+        ev += [(i, f, False) for f in range(6)] + [(i, f, True) for f in (0, 1, 2)]
+    return ev
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 5, 17])
+def test_one_particle_blocks_count_the_plain_fig2_loop(n):
+    # a block of one particle is the untiled loop: j runs over all particles
+    # once per i, so positions are read n + n^2 + n times and masses n^2
+    want = np.zeros(14, dtype=np.uint64)
+    for _, f, w in plain_loop_accesses(n):
+        want[f + (7 if w else 0)] += 1
+    assert np.array_equal(oracle.nbody_access_counts(n, block=1), want)
+    assert int(want[0]) == 2 * n + n * n and int(want[6]) == n * n
+
+
+@pytest.mark.parametrize("block", [1, 2, 7, 64, 100, 1000])
+@pytest.mark.parametrize("n", [1, 63, 100, 257])
+def test_counts_that_every_schedule_shares(n, block):
+    # whatever the tiling: each velocity leaf is read in the update and in the
+    # move and written once; each position leaf is written once (by the move);
+    # mass is never written; the j loop reads positions and mass equally often
+    c = oracle.nbody_access_counts(n, block=block).astype(np.int64)
+    reads, writes = c[:7], c[7:]
+    assert np.all(reads[3:6] == 2 * n)
+    assert np.all(writes[3:6] == n) and np.all(writes[0:3] == n) and writes[6] == 0
+    assert np.all(reads[0:3] == reads[0]) and reads[0] == reads[6] + 2 * n
+    # the j loop runs once per block of the update: ceil(n / block) passes of n
+    assert reads[6] == -(-n // block) * n
+    # fewer, larger blocks never read more
+    if block > 1:
+        assert np.all(c <= oracle.nbody_access_counts(n, block=block - 1).astype(np.int64))
+
+
+@pytest.mark.parametrize("block", [1, 3, 64])
+@pytest.mark.parametrize("mapping", [{"kind": "aos"}, {"kind": "soa_mb"}, {"kind": "aosoa", "lanes": 8}],
+                         ids=lambda m: m["kind"])
+def test_byte_heatmap_holds_four_counts_per_access_for_any_block(mapping, block):
+    n = 45
+    heat = oracle.nbody_heatmap(mapping, n, 1, block=block)
+    counts = oracle.nbody_access_counts(n, block=block)
+    assert int(heat.sum()) == 4 * int(counts.sum())
+    # per leaf: its bytes' counters add up to 4 x (its reads + writes)
+    sizes = oracle.blob_sizes(synth.PARTICLE, mapping, n)
+    start = np.cumsum([0] + sizes)
+    per_leaf = np.zeros(7, dtype=np.int64)
+    for i in range(n):
+        for f in range(7):
+            b, off = element_offset(mapping, n, i, f)
+            per_leaf[f] += int(heat[start[b] + off:start[b] + off + 4].sum())
+    assert np.array_equal(per_leaf, 4 * n * ((counts[:7] + counts[7:]) // n).astype(np.int64))
+
+
+def test_heatmap_of_one_particle_blocks_matches_the_plain_loop():
+    n, g = 23, 4
+    mapping = {"kind": "aosoa", "lanes": 8}
+    sizes = oracle.blob_sizes(synth.PARTICLE, mapping, n)
+    start = np.cumsum([0] + [(s + g - 1) // g for s in sizes])
+    want = np.zeros(start[-1], dtype=np.uint64)
+    for i, f, _ in plain_loop_accesses(n):
+        b, off = element_offset(mapping, n, i, f)
+        for k in range(off // g, (off + 3) // g + 1):
+            want[start[b] + k] += 1
+    assert np.array_equal(oracle.nbody_heatmap(mapping, n, g, block=1), want)
+
+
 def element_offset(mapping, n, i, f):
     """(blob, byte) of leaf f of record i for the particle record, from the
     mapping formulas (28-byte record of 7 f32 leaves)."""
