@@ -95,7 +95,7 @@ def test_cfd_512_cubed_relayouts(maps):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("b", [1, 12, 31])
+@pytest.mark.parametrize("b", [1, 3, 7, 12, 17, 31])
 def test_int6_2_to_26_pack_and_unpack(b):
     n = 1 << 26
     fields = synth.device_fields("int6", n, seed=b, bits=b)
@@ -116,7 +116,7 @@ def test_int6_2_to_26_pack_and_unpack(b):
     check_windows(rnd, out, synth.INT6, packed_map, {"kind": "aos"}, n, seed=b + 1)
 
 
-@pytest.mark.parametrize("em", [(5, 2), (8, 23), (11, 52), (5, 10), (11, 10)],
+@pytest.mark.parametrize("em", [(e, m) for e in (5, 8, 11) for m in (2, 10, 23, 52)],
                          ids=lambda x: f"E{x[0]}M{x[1]}")
 def test_mixed_f_2_to_25_float_pack(em):
     n = 1 << 25
@@ -127,6 +127,12 @@ def test_mixed_f_2_to_25_float_pack(em):
     llgb.llgb_pack(src, dst)
     sync_and_check_status()
     check_windows(src, dst, synth.MIXED_F, {"kind": "soa_mb"}, m, n, seed=em[1])
+    # unpacking the packed values gives the oracle's loads of them
+    back = empty_device_view(synth.MIXED_F, {"kind": "soa_mb"}, n)
+    llgb.llgb_unpack(dst, back)
+    sync_and_check_status()
+    check_windows(dst, back, synth.MIXED_F, m, {"kind": "soa_mb"}, n, seed=em[0] * 7)
+    del back
     rnd = random_view(synth.MIXED_F, m, (n,), seed=em[0])
     out = empty_device_view(synth.MIXED_F, {"kind": "soa_mb"}, n)
     llgb.llgb_unpack(rnd, out)
