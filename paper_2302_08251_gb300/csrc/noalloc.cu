@@ -10,6 +10,7 @@
 // descriptor table from a fixed array in this library's static device
 // memory, which every GPU that loads the library holds until the process
 // exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -39,42 +40,115 @@ constexpr int kMaxDevices = 64;
 constexpr size_t kTableBytes = (size_t)kNoallocPairs * sizeof(JobDesc);
 constexpr size_t kStartsBytes = (size_t)kModes * (kNoallocPairs + 1) * sizeof(uint32_t);
 constexpr size_t kScratchBytes = (kTableBytes + kStartsBytes + 255) / 256 * 256;
+static_assert(kTableBytes % 16 == 0 && sizeof(JobDesc) % 8 == 0, "tables are moved in 16-byte words");
 
 // The descriptor tables and tile starts of the current call (about 370 KB).
 // Shared by every call on a device; see llgb_batch_copy_noalloc.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex setup_mu;
-void* device_scratch[kMaxDevices];  // device address of g_noalloc_scratch, per device
+// One piece of a call's descriptors, carried to the device as kernel
+// parameters: `words` 16-byte words for the scratch array from word `at` on.
+// Parameters are copied when the kernel is queued, so the host memory they
+// came from is free again as soon as the launch returns.
+constexpr uint32_t kUploadWords = 1984;  // 31,744 bytes: within the 32 KB parameter limit
+struct UploadArgs {
+    uint32_t at;
+    uint32_t words;
+    uint32_t pad[2];
+    uint4 data[kUploadWords];
+};
 
-// Device address of the scratch array on the current device.  In host code
-// the array's name only stands in for the symbol, so the address is asked
-// for once per device, with that device current.
+__global__ void noalloc_upload(const __grid_constant__ UploadArgs a)
+{
+    uint4* dst = reinterpret_cast<uint4*>(g_noalloc_scratch) + a.at;
+    for (uint32_t k = threadIdx.x; k < a.words; k += blockDim.x) dst[k] = a.data[k];
+}
+
+// Identity of the CUDA context current on this thread (0 if none can be
+// read): a device reset or a context re-creation gives a new identity, and
+// with it a new copy of the scratch array at a new address.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+uint64_t current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+struct ScratchEntry {
+    void* ptr = nullptr;     // device address of g_noalloc_scratch
+    uint64_t context = 0;    // the context it belongs to
+};
+std::mutex setup_mu;
+ScratchEntry device_scratch[kMaxDevices];
+
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name only stands in for the symbol, so the address
+// is asked for once per device and context, with that device current.
 llgb_status scratch_address(void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return internal_fail(LLGB_ERR_UNSUPPORTED, "device ordinal out of range");
+    const uint64_t ctx = current_context_id();
     std::lock_guard<std::mutex> lock(setup_mu);
-    if (!device_scratch[dev]) {
+    ScratchEntry& s = device_scratch[dev];
+    if (!s.ptr || ctx == 0 || s.context != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return internal_fail(LLGB_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-        device_scratch[dev] = p;
+        s.ptr = p;
+        s.context = current_context_id();  // the lookup made the device's context current if it was not
     }
-    *out = device_scratch[dev];
+    *out = s.ptr;
     return LLGB_OK;
 }
 
-// Host staging of one call: the tables of all groups back to back, then the
-// tile starts of all groups.  Pageable host memory; cudaMemcpyAsync has
-// consumed it by the time it returns.
+// A call's descriptors as they go to the scratch array: the tables of all
+// groups back to back, then the tile starts of all groups.
 struct Staging {
     JobDesc jobs[kNoallocPairs];
     uint32_t starts[kModes][kNoallocPairs + 1];
 };
+static_assert(offsetof(Staging, starts) == kTableBytes, "staging mirrors the scratch array");
 thread_local Staging staging;
+thread_local UploadArgs upload;
+
+// Queue uploads of staging bytes [from, to) (multiples of 16) to the same
+// offsets of the scratch array.
+cudaError_t upload_range(size_t from, size_t to, cudaStream_t s)
+{
+    const uint4* words = reinterpret_cast<const uint4*>(&staging);
+    for (size_t w = from / 16; w < to / 16; w += kUploadWords) {
+        const size_t k = to / 16 - w < kUploadWords ? to / 16 - w : kUploadWords;
+        upload.at = (uint32_t)w;
+        upload.words = (uint32_t)k;
+        memcpy(upload.data, words + w, k * 16);
+        noalloc_upload<<<1, 256, 0, s>>>(upload);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -171,12 +245,10 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
         first += count[g];
     }
 
-    // One copy of the descriptors into the static array, then the launches,
-    // all in stream order.
-    cudaError_t e = cudaMemcpyAsync(scratch, staging.jobs, (size_t)njobs * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(static_cast<unsigned char*>(scratch) + kTableBytes, staging.starts, sizeof staging.starts,
-                            cudaMemcpyHostToDevice, s);
+    // The descriptors go into the static array by kernel parameters, then
+    // the copy kernels run, all in stream order.
+    cudaError_t e = upload_range(0, (size_t)njobs * sizeof(JobDesc), s);
+    if (e == cudaSuccess) e = upload_range(kTableBytes, kTableBytes + sizeof staging.starts, s);
     if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     for (int g = 0; g < kModes; ++g) {
         if (launch[g].grid == 0) continue;

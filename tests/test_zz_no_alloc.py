@@ -14,6 +14,7 @@ process and after the rest of the suite.
 import ctypes
 
 import numpy as np
+import torch
 import pytest
 
 from paper_2302_08251_gb300 import llgb, synth
@@ -113,3 +114,36 @@ def test_noalloc_batch_of_large_jobs_with_opposite_image_sizes():
     for (_, d), r in zip(views, ref):
         for got, exp in zip(d.blob_bytes(), r.blob_bytes()):
             assert np.array_equal(got, exp)
+
+
+def test_two_calls_with_different_pairs_queued_back_to_back_on_one_stream():
+    # no wait between the calls: the second call's descriptors must reach the
+    # shared array only after the first call's kernels have read theirs, so
+    # both outputs equal the regular copy
+    ensure_library()
+    first = build_pairs(seed=7)[:9]
+    second = build_pairs(seed=8)[9:20]
+    assert [p[1] for p in first] != [p[1] for p in second]
+    refs = []
+    for group in (first, second):
+        ref = []
+        for rec, dm, n, src in group:
+            d = empty_device_view(rec, dm, n, fill=0x11)
+            llgb.llgb_copy(src, d)
+            ref.append(d.blob_bytes())
+        refs.append(ref)
+    sync_and_check_status()
+    outs = [[empty_device_view(rec, dm, n, fill=0x5A) for rec, dm, n, _ in group] for group in (first, second)]
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    for group, out in zip((first, second), outs):
+        n = len(group)
+        srcs = (ctypes.c_void_p * n)(*[p[3].handle for p in group])
+        dsts = (ctypes.c_void_p * n)(*[d.handle for d in out])
+        llgb.check(llgb.lib().llgb_batch_copy_noalloc(n, srcs, dsts, llgb._stream_ptr(stream)))
+    stream.synchronize()
+    sync_and_check_status()
+    for g, (group, out) in enumerate(zip((first, second), outs)):
+        for k, d in enumerate(out):
+            for got, exp in zip(d.blob_bytes(), refs[g][k]):
+                assert np.array_equal(got, exp), (g, k, group[k][1])
