@@ -203,7 +203,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("copy.cu", "fconv.cuh", "job.h"):
+    for f in ("copy_kernel.cuh", "copy.cu", "copy_mode0.cu", "copy_mode1.cu", "copy_gather.cu", "fconv.cuh", "job.h"):
         with open(os.path.join(ROOT, "paper_2302_08251_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -476,16 +476,58 @@ def nbody_bench(device, args):
         ms = a.elapsed_time(b) / reps
         flops = 20.0 * n * n
         out[name] = {"ms_per_step": round(ms, 4), "TFLOP/s": round(flops / (ms * 1e-3) / 1e12, 2)}
-    # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop x clock (2.07 GHz max)
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    best = max(x["TFLOP/s"] for x in out.values())
+    roofline = nbody_roofline(device, base, rec, n)
     instrumented = nbody_instrumentation_bench(device, base, rec, n, args)
     traversal = nbody_traversal_bench(device, base, rec, n)
     return {"n": n, "flop_per_interaction": 20, "views": out, "instrumented": instrumented,
-            "traversal": traversal,
-            "roofline": {"bound": "alu", "achieved": best, "peak": round(peak, 1),
-                         "unit": "TFLOP/s", "frac": round(best / peak, 4),
-                         "peak_source": "152 SM x 128 FP32 lanes x 2 x 2.07 GHz (nominal)"}}
+            "traversal": traversal, "roofline": roofline}
+
+
+def nbody_roofline(device, base, rec, n, seconds=1.0):
+    """The n-body update is FP32-ALU-bound: its TFLOP/s against the FP32 FMA
+    throughput probe (llgb_fma_probe, 2 FLOP per FMA), each run for about
+    `seconds` with nvidia-smi sampling the SM clock, so that both are stated
+    at the clock they ran at."""
+    import torch
+    from paper_2302_08251_gb300 import llgb
+    sink = torch.zeros(1, dtype=torch.float32, device=device)
+    gpu = device.index if device.index is not None else 0
+
+    def timed_loop(fn, seconds):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        reps = max(3, int(seconds / max(a.elapsed_time(b) * 1e-3, 1e-6)))
+        clk = ClockSampler(gpu)
+        clk.start()
+        time.sleep(0.3)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, clk.stop()
+
+    fmas = []
+    probe_ms, probe_clk = timed_loop(lambda: fmas.append(llgb.llgb_fma_probe(100000, sink)), seconds)
+    peak = 2.0 * fmas[-1] / (probe_ms * 1e-3) / 1e12
+    v = llgb.View(rec, {"kind": "soa_mb"}, (n,))
+    llgb.llgb_copy(base, v)
+    step_ms, step_clk = timed_loop(lambda: llgb.llgb_nbody_step(v, 0.01, 1e-4), seconds)
+    achieved = 20.0 * n * n / (step_ms * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
+           "frac": round(achieved / peak, 4), "view": "SoA",
+           "peak_source": "FP32 FMA throughput probe (llgb_fma_probe), measured in this run",
+           "sm_mhz": {"nbody": step_clk.get("sm_mhz"), "probe": probe_clk.get("sm_mhz")},
+           "reasons": sorted(set(step_clk.get("reasons", [])) | set(probe_clk.get("reasons", []))),
+           "nominal_peak_max_clock": round(152 * 128 * 2 * 2.07e9 / 1e12, 1)}
+    if step_clk.get("sm_mhz") and probe_clk.get("sm_mhz"):
+        out["frac_at_equal_clock"] = round(achieved / peak * probe_clk["sm_mhz"] / step_clk["sm_mhz"], 4)
+    return out
 
 
 TRAVERSAL_VIEWS = [("AoS", {"kind": "aos"}), ("SoA", {"kind": "soa_mb"}),

@@ -240,6 +240,19 @@ llgb_status llgb_unpack(const llgb_view* packed, llgb_view* plain, void* stream)
  *           moves, within the CTA's program capacity), else value loops. */
 typedef enum llgb_engine { LLGB_ENGINE_AUTO = 0, LLGB_ENGINE_VALUE = 1, LLGB_ENGINE_GATHER = 2 } llgb_engine;
 
+/* How tiles move between global and shared memory: the TMA engine (bulk
+ * copies issued by one producer warp per direction) or plain coalesced loads
+ * and stores by the consumer threads.  Both move the same bytes; which one is
+ * faster depends on the pair (many small runs per tile favour plain stores).
+ * The last tile of a view, and runs that are not 16-byte aligned, always take
+ * plain accesses. */
+typedef enum llgb_staging {
+    LLGB_STAGING_TMA = 0,         /* TMA loads and stores (default)            */
+    LLGB_STAGING_PLAIN_STORE = 1, /* TMA loads, plain stores                   */
+    LLGB_STAGING_PLAIN_LOAD = 2,  /* plain loads, TMA stores                   */
+    LLGB_STAGING_PLAIN = 3        /* plain loads and stores                    */
+} llgb_staging;
+
 /* Launch shape of the copy kernel.  All zero = the library's choice. */
 typedef struct llgb_launch_config {
     int32_t tile_records;   /* records per tile; multiple of 128 and of lanes */
@@ -248,7 +261,8 @@ typedef struct llgb_launch_config {
     int32_t threads;        /* threads per CTA: 128, 256 or 512                */
     int32_t ctas_per_sm;    /* resident CTAs per SM (1..8)                      */
     int32_t engine;         /* llgb_engine                                     */
-    int32_t reserved[2];    /* must be 0                                       */
+    int32_t staging;        /* llgb_staging                                    */
+    int32_t reserved;       /* must be 0                                       */
 } llgb_launch_config;
 
 /* The launch shape llgb_copy uses for this pair (after autotuning, if any). */
@@ -263,7 +277,12 @@ llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst,
  *     of 2 / 4 source words (a single copy, and the same pair in a batch);
  *   tile_records, tiles: the tiling; items: work items per tile, of which
  *     generic_items convert values record by record (the others run loops
- *     specialised at compile time, or move bytes).
+ *     specialised at compile time, or move bytes), and stream_items pack or
+ *     unpack a SoA bit stream whose width and float format are compile-time
+ *     constants of one of the library's specialised loops (integer widths 1,
+ *     3, 7, 12, 17, 31 of 4-byte leaves; f64 and f32 leaves in the (E, M)
+ *     formats E in {5, 8, 11}, M in {2, 10, 23, 52}); they run so in kernel
+ *     mode 0.
  * All zero for n = 0.  Errors: INVALID_ARG, MISMATCH, UNSUPPORTED. */
 typedef struct llgb_plan_info {
     int32_t kernel_mode;
@@ -271,7 +290,7 @@ typedef struct llgb_plan_info {
     int32_t tile_records;
     int32_t items;
     int32_t generic_items;
-    int32_t reserved;
+    int32_t stream_items;
     uint64_t tiles;
 } llgb_plan_info;
 
@@ -309,6 +328,31 @@ llgb_status llgb_batch_info(const llgb_batch* b, int32_t* launches, uint64_t* ti
 /* Waits for the batch's last queued launch, then frees it. */
 void llgb_batch_destroy(llgb_batch* b);
 
+/* Batch arena: batched copies for a loop that submits new pairs all the
+ * time (a request loop).  llgb_batch_create allocates and fills device tables
+ * (cudaMalloc, a blocking cudaMemcpy) and llgb_batch_destroy frees them
+ * (cudaFree): calls that can synchronise the whole device.  An arena
+ * allocates, once, descriptor tables for `slots` copies of at most
+ * `max_pairs` pairs each, in device memory and in pinned host memory, on the
+ * current device.  llgb_batch_arena_copy then moves src[k] -> dst[k] for
+ * k < n exactly as llgb_copy does (same bytes), queued on `stream`: it plans
+ * the pairs, writes their tables into the next slot's pinned staging and
+ * queues one cudaMemcpyAsync of them and the copy kernels (one per kernel
+ * mode) on `stream`.  Nothing synchronises the device; the host waits only
+ * when the slot it takes is still in use by a copy `slots` calls back.
+ * Calls may use different streams; the views' blobs must stay alive until
+ * the work queued on them has finished.  An arena is used from any thread
+ * (calls are serialised) on the device it was made on.
+ * Errors: create -- INVALID_ARG (max_pairs 1..65536, slots 1..64), OOM, CUDA;
+ * copy -- as llgb_copy, plus INVALID_ARG (n > max_pairs, another device). */
+typedef struct llgb_batch_arena llgb_batch_arena;
+
+llgb_status llgb_batch_arena_create(int32_t max_pairs, int32_t slots, llgb_batch_arena** out);
+llgb_status llgb_batch_arena_copy(llgb_batch_arena* a, int32_t n, const llgb_view* const* src,
+                                  llgb_view* const* dst, void* stream);
+/* Waits for the arena's queued copies, then frees it. */
+void llgb_batch_arena_destroy(llgb_batch_arena* a);
+
 /* Batched copy that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device
  * memory while they run -- cudaMalloc/cudaFree may synchronise the whole
@@ -320,29 +364,48 @@ void llgb_batch_destroy(llgb_batch* b);
  * queued on `stream`, with no cudaMalloc, cudaFree or other allocating call.
  * The descriptor tables live in one static device array of this library
  * (about 370 KB, holding at most 64 view pairs), which every GPU that loads
- * the library keeps until the process exits.
+ * the library keeps until the process exits.  They reach that array as the
+ * parameters of small upload kernels queued on `stream` ahead of the copy
+ * kernels, so no host memory is read after the call returns.
  *   - n <= 64; larger n returns LLGB_ERR_INVALID_ARG (split the work).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *     before any stream capture on the device.  The address is kept per
+ *     device and CUDA context: after a device reset (a new context) the next
+ *     call looks it up again, and is then again a first call.
  *   - Every call on a device shares the array and overwrites all of it that
- *     the call uses (no state survives between calls).  Calls that overlap on
- *     the GPU -- on different streams, or from different host threads --
- *     race on the array; order them (one stream, or events).
+ *     the call uses (no state survives between calls).  Calls queued on one
+ *     stream run one after the other.  Calls that overlap on the GPU -- on
+ *     different streams, or from different host threads -- race on the
+ *     array; order them (one stream, or events).
  * Errors: as llgb_copy. */
 llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const* src, llgb_view* const* dst,
                                     void* stream);
 
-/* Autotuner: time candidate launch shapes (tile records, stages, threads,
- * CTAs per SM) of llgb_copy(src, dst) on `stream` (each candidate runs the
- * copy 4 times; dst is written), keep the fastest for this mapping pair and
- * power-of-two record count, and use it in later llgb_copy / llgb_batch_create
- * calls of this process.  *best (may be NULL) receives it.  Synchronizes the
+/* Autotuner: time candidate launch shapes of llgb_copy(src, dst) on `stream`
+ * (each candidate runs the copy 4 times; dst is written) -- first tile
+ * records, stages, threads and CTAs per SM with TMA staging, then the staging
+ * schemes (llgb_staging) of the fastest shape -- keep the fastest for this
+ * mapping pair and power-of-two record count, and use it in later llgb_copy,
+ * llgb_batch_create, llgb_batch_arena_copy and llgb_batch_copy_noalloc calls
+ * of this process.  *best (may be NULL) receives it.  Synchronizes the
  * stream. */
 llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, llgb_launch_config* best);
 
 /* Forget every tuned launch shape. */
 llgb_status llgb_autotune_clear(void);
+
+/* Persist the tuned launch shapes: save writes every shape of this process
+ * to the JSON file `path` ({"llgb_autotune": 1, "entries": {key: [tile_records,
+ * src_stages, dst_stages, threads, ctas_per_sm, engine, staging]}}, keyed by
+ * mapping pair and power-of-two record count); load adds a file's shapes to
+ * those of this process (an entry of the file replaces one with its key), so
+ * that a later process skips the tuning.  A shape that no longer fits a pair
+ * makes its copies fail with INVALID_ARG: files belong to one build of the
+ * library.  Errors: INVALID_ARG (null path, unreadable or malformed file,
+ * a value out of range), OOM. */
+llgb_status llgb_autotune_save(const char* path);
+llgb_status llgb_autotune_load(const char* path);
 
 /* -------------------------------------------------------------- n-body -- */
 
@@ -383,6 +446,15 @@ llgb_status llgb_nbody_update(llgb_view* particles, float eps, float dt, int32_t
 
 /* Move only: p_i += dt * v_i (one fused multiply-add per leaf). */
 llgb_status llgb_nbody_move(llgb_view* particles, float dt, int32_t traversal, void* stream);
+
+/* FP32 throughput probe, the roofline of the n-body update (an FP32 ALU-bound
+ * loop).  The paper has no counterpart: it measures the peak the n-body's
+ * TFLOP/s are divided by.  Queues one kernel on `stream` whose threads fill
+ * every warp slot of every SM and each run 16 independent fused
+ * multiply-add chains for `iters` rounds; *fmas (host) receives the number of
+ * FMAs it performs (2 FLOP each).  Time it with events on `stream`.  `sink`:
+ * one device float the kernel may write.  Errors: INVALID_ARG, CUDA. */
+llgb_status llgb_fma_probe(uint32_t iters, float* sink, uint64_t* fmas, void* stream);
 
 /* --------------------------------------------- access instrumentation -- */
 
@@ -425,6 +497,18 @@ llgb_status llgb_heatmap_counters(const llgb_view* view, uint64_t granularity, u
  * (LLGB_ERR_TIMEOUT); 0 when none did.  Synchronizes the current device.
  * reset != 0 clears the word. */
 llgb_status llgb_device_status(int32_t* code, int32_t reset);
+
+/* Self-test of the failure detection of the copy kernels.  Every wait of a
+ * copy kernel on one of its pipeline barriers is bounded (2 s); when one runs
+ * out, the kernel stops its CTA's work, records LLGB_ERR_TIMEOUT in the device
+ * status word and returns, so that the CUDA context stays usable.  This call
+ * queues one small kernel on `stream` that takes that same bounded wait on a
+ * barrier no thread ever arrives on, with the limit `limit_ns` (1 us .. 10 s)
+ * instead of 2 s: it gives up after limit_ns, records LLGB_ERR_TIMEOUT and
+ * returns.  `waited_ns` (a device uint64, 8-byte aligned, or NULL) receives the
+ * time the wait took.  Read the status with llgb_device_status.
+ * Errors: INVALID_ARG (limit out of range, misaligned pointer), CUDA. */
+llgb_status llgb_wait_selftest(uint64_t limit_ns, uint64_t* waited_ns, void* stream);
 
 #ifdef __cplusplus
 }

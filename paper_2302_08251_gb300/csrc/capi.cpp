@@ -5,9 +5,11 @@
 // thread-local message.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -21,15 +23,34 @@
 #include "llgb.h"
 #include "plan.h"
 
+// A planned copy into a view, kept so that repeated llgb_copy calls of the
+// same pair skip the host planning: valid while the source view, both views'
+// bound blobs, the current device and the tuned launch shapes are unchanged.
+struct CopyPlanCache {
+    bool valid = false;
+    uint64_t src_id = 0, src_bind = 0, dst_bind = 0, tune_gen = 0;
+    int device = -1;
+    int mode = 0, grid = 0, threads = 0;
+    size_t smem = 0;
+    llgb::CopyArgs args;
+};
+
 struct llgb_view {
     llgb::ViewPlan plan;
     std::vector<void*> ptrs;
     bool bound = false;
+    uint64_t id = 0;         // unique over the process, never reused
+    uint64_t bind_gen = 0;   // counts llgb_view_bind calls
+    std::mutex cache_mu;
+    CopyPlanCache cache;     // the last copy planned into this view
 };
 
 using namespace llgb;
 
 namespace {
+
+std::atomic<uint64_t> g_view_ids{1};
+std::atomic<uint64_t> g_tune_gen{1};  // bumped whenever a tuned launch shape changes
 
 thread_local std::string t_error;
 
@@ -89,6 +110,15 @@ size_t smem_needed(const JobDesc& J, const llgb_launch_config& c)
 }
 
 bool valid_threads(int t) { return t == 128 || t == 256 || t == 512; }
+
+// Plain consumer loads and / or stores instead of TMA bulk copies
+// (llgb_staging): the kernel then moves every tile of that side the way it
+// moves unaligned runs.
+void apply_staging(JobDesc* job, int staging)
+{
+    if (staging & LLGB_STAGING_PLAIN_STORE) job->dst.bulk_ok = 0;
+    if (staging & LLGB_STAGING_PLAIN_LOAD) job->src.bulk_ok = 0;
+}
 
 // Kernel mode of a planned job under a launch shape: its gather form when the
 // gather programs cover the destination image with the consumer threads,
@@ -245,6 +275,7 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
         if ((job->src.img_bytes <= side_cap && job->dst.img_bytes <= side_cap) || tile <= q) break;
         tile -= q;
     }
+    apply_staging(job, c.staging);
     // few-tile jobs take the value loops; run-addressed bit jobs need mode 1 for them
     *mode = job->ntiles <= kFewTiles ? (job->seg ? 1 : 0) : job_mode(*job, threads);
     return LLGB_OK;
@@ -275,8 +306,21 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     llgb_status st = check_pair(src, dst);
     if (st != LLGB_OK) return st;
     if (src->plan.n == 0) return LLGB_OK;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool library_shape = !(cfg_in && cfg_in->tile_records != 0);
+    int device = 0;
+    cudaGetDevice(&device);
+    const uint64_t tune_gen = g_tune_gen.load();
+    std::lock_guard<std::mutex> lock(dst->cache_mu);
+    CopyPlanCache& C = dst->cache;
+    if (library_shape && C.valid && C.src_id == src->id && C.src_bind == src->bind_gen &&
+        C.dst_bind == dst->bind_gen && C.device == device && C.tune_gen == tune_gen) {
+        const cudaError_t e = launch_copy(C.args, C.mode, C.grid, C.threads, C.smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+        return LLGB_OK;
+    }
     llgb_launch_config c{};
-    if (cfg_in && cfg_in->tile_records != 0) {
+    if (!library_shape) {
         c = *cfg_in;
     } else if (!tuned_config(src, dst, &c)) {
         st = default_config(src, dst, &c);
@@ -290,6 +334,7 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     std::string why;
     st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, (uint32_t)c.tile_records, &args.job, &why);
     if (st != LLGB_OK) return fail(st, why);
+    apply_staging(&args.job, c.staging);
     const DeviceInfo dev = device_info();
     const size_t smem = smem_needed(args.job, c);
     if (!smem_fits(smem, c.ctas_per_sm))
@@ -308,8 +353,23 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     const int mode = copy_mode(args.job, c, grid);
     if (c.threads / 32 <= (int)producer_warps(mode))
         return fail(LLGB_ERR_INVALID_ARG, "launch config leaves no consumer warp");
-    cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+    if (library_shape) {
+        C.args = args;
+        C.mode = mode;
+        C.grid = grid;
+        C.threads = c.threads;
+        C.smem = smem;
+        C.src_id = src->id;
+        C.src_bind = src->bind_gen;
+        C.dst_bind = dst->bind_gen;
+        C.device = device;
+        C.tune_gen = tune_gen;
+        C.valid = true;
+    } else {
+        C.valid = false;
+    }
     return LLGB_OK;
 }
 
@@ -345,57 +405,36 @@ bool internal_smem_fits(size_t smem, int ctas) { return smem_fits(smem, ctas); }
 
 }  // namespace llgb
 
-// A batch: every job planned once, grouped by kernel mode; each group is one
-// launch of the copy kernel over a device descriptor table.
-struct llgb_batch {
-    struct Group {
-        int mode = 0;
-        int threads = 256;
-        int grid = 0;
-        size_t smem = 0;
-        std::vector<JobDesc> jobs;
-        std::vector<uint32_t> starts;  // first tile of each job, then the total
-        JobDesc* d_table = nullptr;
-        uint32_t* d_starts = nullptr;
-        CopyArgs args;
-    };
-    std::vector<Group> groups;
-    uint64_t bytes = 0;
-    uint64_t tiles = 0;
-    int device = 0;
-    cudaStream_t capture = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t done = nullptr;
-
-    ~llgb_batch()
-    {
-        if (done) {
-            cudaEventSynchronize(done);
-            cudaEventDestroy(done);
-        }
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        if (capture) cudaStreamDestroy(capture);
-        for (Group& g : groups) {
-            if (g.d_table) cudaFree(g.d_table);
-            if (g.d_starts) cudaFree(g.d_starts);
-        }
-    }
-};
-
 namespace {
 
-llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch* b)
+// A group of a batch: the jobs of one kernel mode, run by one launch of the
+// copy kernel over a descriptor table (args.table / args.tile_start are set
+// once the tables have a device address).
+struct BatchGroup {
+    int mode = 0;
+    int threads = 256;
+    int grid = 0;
+    size_t smem = 0;
+    std::vector<JobDesc> jobs;
+    std::vector<uint32_t> starts;  // first tile of each job, then the total
+    CopyArgs args;
+};
+
+// Plan every (src[k], dst[k]) pair once and group the jobs by kernel mode;
+// each group gets its launch shape: stages sized for the largest images of
+// the group, two 256-thread CTAs per SM where they fit, else one of 512.
+llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const* dst, std::vector<BatchGroup>* out,
+                        uint64_t* bytes, uint64_t* tiles)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
-    cudaGetDevice(&b->device);
-    llgb_batch::Group groups[4];
+    BatchGroup groups[4];
     groups[0].mode = 0;
     groups[1].mode = 2;
     groups[2].mode = 4;
     groups[3].mode = 1;
+    *bytes = 0;
+    *tiles = 0;
     for (int32_t k = 0; k < n; ++k) {
         llgb_status st = check_pair(src[k], dst[k]);
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
@@ -404,20 +443,21 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         int mode = 0;
         st = plan_batch_job(src[k], dst[k], &J, &mode, 256);
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
-        llgb_batch::Group& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : (mode == 4 ? 2 : 3))];
-        g.starts.push_back((uint32_t)b->tiles);
+        BatchGroup& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : (mode == 4 ? 2 : 3))];
         g.jobs.push_back(J);
-        for (uint64_t s : src[k]->plan.blob_sizes) b->bytes += s;
-        for (uint64_t s : dst[k]->plan.blob_sizes) b->bytes += s;
-        b->tiles += J.ntiles;
+        for (uint64_t s : src[k]->plan.blob_sizes) *bytes += s;
+        for (uint64_t s : dst[k]->plan.blob_sizes) *bytes += s;
+        *tiles += J.ntiles;
     }
-    for (llgb_batch::Group& g : groups) {
+    out->clear();
+    for (BatchGroup& g : groups) {
         if (g.jobs.empty()) continue;
         // tile numbers are per group, starting at 0
         uint64_t total = 0;
         uint32_t src_bytes = 0, dst_bytes = 0;
+        g.starts.clear();
         for (size_t q = 0; q < g.jobs.size(); ++q) {
-            g.starts[q] = (uint32_t)total;
+            g.starts.push_back((uint32_t)total);
             total += g.jobs[q].ntiles;
             src_bytes = std::max(src_bytes, g.jobs[q].src.img_bytes);
             dst_bytes = std::max(dst_bytes, g.jobs[q].dst.img_bytes);
@@ -439,19 +479,6 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         g.smem = need();
         g.grid = (int)std::min<uint64_t>(total, (uint64_t)sms * ctas);
         memset(&g.args, 0, sizeof g.args);
-        cudaError_t e = cudaMalloc(&g.d_table, g.jobs.size() * sizeof(JobDesc));
-        if (e == cudaSuccess) e = cudaMalloc(&g.d_starts, g.starts.size() * sizeof(uint32_t));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_table, g.jobs.data(), g.jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_starts, g.starts.data(), g.starts.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            b->groups.push_back(std::move(g));  // freed by the destructor
-            return e == cudaErrorMemoryAllocation ? fail(LLGB_ERR_OOM, "batch descriptor table")
-                                                  : cuda_fail(e, "batch descriptor table");
-        }
-        g.args.table = g.d_table;
-        g.args.tile_start = g.d_starts;
         g.args.njobs = (uint32_t)g.jobs.size();
         g.args.total_tiles = (uint32_t)total;
         g.args.src_stage_bytes = src_bytes + kStageZeroBytes;
@@ -460,19 +487,114 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
         g.args.src_stages = ns;
         g.args.dst_stages = nd;
         g.args.chunk = (uint32_t)((total + g.grid - 1) / g.grid);
-        b->groups.push_back(std::move(g));
+        out->push_back(std::move(g));
     }
     return LLGB_OK;
 }
 
-llgb_status batch_enqueue(llgb_batch* b, cudaStream_t stream)
+llgb_status enqueue_groups(const std::vector<BatchGroup>& groups, cudaStream_t stream)
 {
-    for (const llgb_batch::Group& g : b->groups) {
+    for (const BatchGroup& g : groups) {
         const cudaError_t e = launch_copy(g.args, g.mode, g.grid, g.threads, g.smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
     }
     return LLGB_OK;
 }
+
+}  // namespace
+
+// A batch: every job planned once, grouped by kernel mode; each group is one
+// launch of the copy kernel over a device descriptor table of its own.
+struct llgb_batch {
+    std::vector<BatchGroup> groups;
+    std::vector<void*> device_tables;  // per group: its jobs, then its tile starts
+    uint64_t bytes = 0;
+    uint64_t tiles = 0;
+    int device = 0;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+
+    ~llgb_batch()
+    {
+        if (done) {
+            cudaEventSynchronize(done);
+            cudaEventDestroy(done);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (capture) cudaStreamDestroy(capture);
+        for (void* p : device_tables)
+            if (p) cudaFree(p);
+    }
+};
+
+// A batch arena: descriptor tables for `slots` batched copies of up to
+// max_pairs pairs each, in device memory and in pinned host staging, both
+// allocated once at creation.  A copy takes the next slot (waiting, on the
+// host, only until that slot's previous copy has finished on the device),
+// writes its tables into the slot's staging, and queues one asynchronous
+// table copy and its kernels on the caller's stream.
+struct llgb_batch_arena {
+    int32_t max_pairs = 0;
+    int32_t nslots = 0;
+    size_t slot_bytes = 0;
+    uint8_t* d_mem = nullptr;
+    uint8_t* h_mem = nullptr;
+    std::vector<cudaEvent_t> done;  // per slot: its last copy's kernels are done
+    int next = 0;
+    int device = 0;
+    std::mutex mu;
+    std::vector<BatchGroup> groups;  // scratch of the current call
+
+    ~llgb_batch_arena()
+    {
+        for (cudaEvent_t e : done) {
+            cudaEventSynchronize(e);
+            cudaEventDestroy(e);
+        }
+        if (d_mem) cudaFree(d_mem);
+        if (h_mem) cudaFreeHost(h_mem);
+    }
+};
+
+namespace {
+
+// Groups of at most 4 kernel modes: a slot holds max_pairs jobs, then the
+// tile starts of every group (max_pairs + 4 entries).
+constexpr int kArenaGroups = 4;
+
+size_t arena_slot_bytes(int32_t max_pairs)
+{
+    const size_t starts = ((size_t)max_pairs + kArenaGroups) * sizeof(uint32_t);
+    return ((size_t)max_pairs * sizeof(JobDesc) + starts + 255) / 256 * 256;
+}
+
+llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch* b)
+{
+    cudaGetDevice(&b->device);
+    llgb_status st = plan_groups(n, src, dst, &b->groups, &b->bytes, &b->tiles);
+    if (st != LLGB_OK) return st;
+    for (BatchGroup& g : b->groups) {
+        const size_t table_bytes = g.jobs.size() * sizeof(JobDesc);
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, table_bytes + g.starts.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) b->device_tables.push_back(p);
+        if (e == cudaSuccess) e = cudaMemcpy(p, g.jobs.data(), table_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(static_cast<uint8_t*>(p) + table_bytes, g.starts.data(), g.starts.size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(LLGB_ERR_OOM, "batch descriptor table")
+                                                  : cuda_fail(e, "batch descriptor table");
+        g.args.table = static_cast<const JobDesc*>(p);
+        g.args.tile_start = reinterpret_cast<const uint32_t*>(static_cast<uint8_t*>(p) + table_bytes);
+    }
+    return LLGB_OK;
+}
+
+llgb_status batch_enqueue(llgb_batch* b, cudaStream_t stream) { return enqueue_groups(b->groups, stream); }
 
 }  // namespace
 
@@ -538,6 +660,7 @@ llgb_status llgb_view_create(const llgb_record* rec, const llgb_extents* ext, co
             return fail(st, why);
         }
         v->ptrs.assign(v->plan.blob_sizes.size(), nullptr);
+        v->id = g_view_ids.fetch_add(1);
         *out = v;
         return LLGB_OK;
     } catch (const std::bad_alloc&) {
@@ -571,6 +694,7 @@ llgb_status llgb_view_bind(llgb_view* view, void* const* dev_ptrs, int32_t n)
     }
     for (int k = 0; k < n; ++k) view->ptrs[k] = dev_ptrs[k];
     view->bound = true;
+    ++view->bind_gen;
     return LLGB_OK;
 }
 
@@ -587,10 +711,11 @@ llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst, const llgb_laun
 {
     try {
         if (!cfg) return fail(LLGB_ERR_INVALID_ARG, "null launch config");
-        for (int k = 0; k < 2; ++k)
-            if (cfg->reserved[k]) return fail(LLGB_ERR_INVALID_ARG, "reserved fields must be 0");
+        if (cfg->reserved) return fail(LLGB_ERR_INVALID_ARG, "reserved field must be 0");
         if (cfg->engine < LLGB_ENGINE_AUTO || cfg->engine > LLGB_ENGINE_GATHER)
             return fail(LLGB_ERR_INVALID_ARG, "unknown engine");
+        if (cfg->staging < LLGB_STAGING_TMA || cfg->staging > LLGB_STAGING_PLAIN)
+            return fail(LLGB_ERR_INVALID_ARG, "unknown staging");
         if (cfg->tile_records <= 0) return fail(LLGB_ERR_INVALID_ARG, "tile_records must be positive");
         return run_copy(src, dst, cfg, stream);
     } catch (...) {
@@ -634,8 +759,10 @@ llgb_status llgb_copy_plan(const llgb_view* src, const llgb_view* dst, const llg
         out->tile_records = (int32_t)J.tile;
         out->tiles = J.ntiles;
         out->items = J.nitems;
-        for (int k = 0; k < J.nitems; ++k)
+        for (int k = 0; k < J.nitems; ++k) {
             if (J.items[k].op == ITEM_VALUE && J.items[k].fast == FK_GENERIC) ++out->generic_items;
+            if (J.items[k].spec) ++out->stream_items;
+        }
         int bmode = 0;
         st = plan_batch_job(src, dst, &J, &bmode, 256);
         if (st != LLGB_OK) return st;
@@ -866,7 +993,7 @@ llgb_status llgb_batch_launch(llgb_batch* b, void* stream, int32_t use_graph)
         if (st != LLGB_OK) return st;
     } else {
         if (!b->exec) {
-            for (const llgb_batch::Group& g : b->groups)
+            for (const BatchGroup& g : b->groups)
                 if ((e = prepare_copy(g.mode, g.smem)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
             if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
                 return cuda_fail(e, "capture stream");
@@ -895,6 +1022,82 @@ llgb_status llgb_batch_info(const llgb_batch* b, int32_t* launches, uint64_t* ti
 
 void llgb_batch_destroy(llgb_batch* b) { delete b; }
 
+llgb_status llgb_batch_arena_create(int32_t max_pairs, int32_t slots, llgb_batch_arena** out)
+{
+    try {
+        if (!out || max_pairs < 1 || max_pairs > 65536 || slots < 1 || slots > 64)
+            return fail(LLGB_ERR_INVALID_ARG, "arena needs 1..65536 pairs and 1..64 slots");
+        auto* a = new llgb_batch_arena;
+        a->max_pairs = max_pairs;
+        a->nslots = slots;
+        a->slot_bytes = arena_slot_bytes(max_pairs);
+        cudaGetDevice(&a->device);
+        cudaError_t e = cudaMalloc(&a->d_mem, a->slot_bytes * (size_t)slots);
+        if (e == cudaSuccess) e = cudaMallocHost(&a->h_mem, a->slot_bytes * (size_t)slots);
+        for (int k = 0; e == cudaSuccess && k < slots; ++k) {
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) a->done.push_back(ev);
+        }
+        if (e != cudaSuccess) {
+            delete a;
+            return e == cudaErrorMemoryAllocation ? fail(LLGB_ERR_OOM, "arena tables") : cuda_fail(e, "arena tables");
+        }
+        *out = a;
+        return LLGB_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+llgb_status llgb_batch_arena_copy(llgb_batch_arena* a, int32_t n, const llgb_view* const* src,
+                                  llgb_view* const* dst, void* stream)
+{
+    try {
+        if (!a || n < 0 || (n > 0 && (!src || !dst))) return fail(LLGB_ERR_INVALID_ARG, "bad arena arguments");
+        if (n > a->max_pairs) return fail(LLGB_ERR_INVALID_ARG, "more pairs than the arena was made for");
+        int device = 0;
+        cudaGetDevice(&device);
+        if (device != a->device) return fail(LLGB_ERR_INVALID_ARG, "arena used on another device than it was made on");
+        std::lock_guard<std::mutex> lock(a->mu);
+        uint64_t bytes = 0, tiles = 0;
+        llgb_status st = plan_groups(n, src, dst, &a->groups, &bytes, &tiles);
+        if (st != LLGB_OK || a->groups.empty()) return st;
+        const int slot = a->next;
+        a->next = (a->next + 1) % a->nslots;
+        // the slot's previous copy must have read its tables
+        cudaError_t e = cudaEventSynchronize(a->done[slot]);
+        if (e != cudaSuccess) return cuda_fail(e, "arena slot wait");
+        uint8_t* h = a->h_mem + (size_t)slot * a->slot_bytes;
+        uint8_t* d = a->d_mem + (size_t)slot * a->slot_bytes;
+        size_t at = 0;
+        for (BatchGroup& g : a->groups) {
+            memcpy(h + at, g.jobs.data(), g.jobs.size() * sizeof(JobDesc));
+            g.args.table = reinterpret_cast<const JobDesc*>(d + at);
+            at += g.jobs.size() * sizeof(JobDesc);
+        }
+        for (BatchGroup& g : a->groups) {
+            memcpy(h + at, g.starts.data(), g.starts.size() * sizeof(uint32_t));
+            g.args.tile_start = reinterpret_cast<const uint32_t*>(d + at);
+            at += g.starts.size() * sizeof(uint32_t);
+        }
+        const cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if ((e = cudaMemcpyAsync(d, h, at, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "arena table copy");
+        st = enqueue_groups(a->groups, s);
+        if ((e = cudaEventRecord(a->done[slot], s)) != cudaSuccess) return cuda_fail(e, "arena event record");
+        return st;
+    } catch (const std::bad_alloc&) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(LLGB_ERR_INVALID_ARG, "unexpected error");
+    }
+}
+
+void llgb_batch_arena_destroy(llgb_batch_arena* a) { delete a; }
+
 llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, llgb_launch_config* best)
 {
     try {
@@ -913,6 +1116,27 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
         uint32_t cb = 0;
         bytes_per_record(src->plan, dst->plan, &sb, &db, &cb);
         const double per_rec = std::max(std::max(sb, db), 1.0);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            return cuda_fail(e, "autotune events");
+        }
+        // time one shape: a warm-up copy (which also rejects shapes that do
+        // not fit the pair), then three timed copies
+        auto time_shape = [&](const llgb_launch_config& c) -> float {
+            if (run_copy(src, dst, &c, stream) != LLGB_OK) return -1.0f;
+            cudaEventRecord(e0, s);
+            bool ok = true;
+            for (int r = 0; r < 3 && ok; ++r) ok = run_copy(src, dst, &c, stream) == LLGB_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || !ok) return -1.0f;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            return ms;
+        };
+        // 1. tile size, threads and CTAs per SM, pipeline depths (TMA staging)
         std::vector<llgb_launch_config> cands{base};
         for (double target : {6144.0, 12288.0, 24576.0, 49152.0, 73728.0})
             for (int threads : {256, 512})
@@ -926,21 +1150,21 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
                         c.dst_stages = nd;
                         cands.push_back(c);
                     }
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
         float best_ms = 1e30f;
         llgb_launch_config winner = base;
         for (const llgb_launch_config& c : cands) {
-            if (run_copy(src, dst, &c, stream) != LLGB_OK) continue;  // shape does not fit this pair
-            cudaEventRecord(e0, s);
-            bool ok = true;
-            for (int r = 0; r < 3 && ok; ++r) ok = run_copy(src, dst, &c, stream) == LLGB_OK;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess || !ok) continue;
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
+            const float ms = time_shape(c);
+            if (ms >= 0.0f && ms < best_ms) {
+                best_ms = ms;
+                winner = c;
+            }
+        }
+        // 2. the staging scheme of the winning shape
+        for (int staging : {LLGB_STAGING_PLAIN_STORE, LLGB_STAGING_PLAIN_LOAD, LLGB_STAGING_PLAIN}) {
+            llgb_launch_config c = winner;
+            c.staging = staging;
+            const float ms = time_shape(c);
+            if (ms >= 0.0f && ms < best_ms) {
                 best_ms = ms;
                 winner = c;
             }
@@ -952,6 +1176,7 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
             std::lock_guard<std::mutex> lock(tune_mu);
             tune_cache[tune_key(src, dst)] = winner;
         }
+        g_tune_gen.fetch_add(1);
         if (best) *best = winner;
         return LLGB_OK;
     } catch (...) {
@@ -959,10 +1184,120 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
     }
 }
 
+// The tuned shapes as JSON: {"llgb_autotune": 1, "entries": {"<pair key>":
+// [tile_records, src_stages, dst_stages, threads, ctas_per_sm, engine,
+// staging], ...}}.  Keys are the mapping pair and record-count bucket that
+// llgb_autotune files a shape under (letters, digits and , : / { } |).
+llgb_status llgb_autotune_save(const char* path)
+{
+    try {
+        if (!path) return fail(LLGB_ERR_INVALID_ARG, "null path");
+        std::string out = "{\"llgb_autotune\": 1, \"entries\": {";
+        {
+            std::lock_guard<std::mutex> lock(tune_mu);
+            bool first = true;
+            for (const auto& kv : tune_cache) {
+                const llgb_launch_config& c = kv.second;
+                out += first ? "\n  \"" : ",\n  \"";
+                first = false;
+                out += kv.first + "\": [" + std::to_string(c.tile_records) + ", " + std::to_string(c.src_stages) +
+                       ", " + std::to_string(c.dst_stages) + ", " + std::to_string(c.threads) + ", " +
+                       std::to_string(c.ctas_per_sm) + ", " + std::to_string(c.engine) + ", " +
+                       std::to_string(c.staging) + "]";
+            }
+        }
+        out += "\n}}\n";
+        FILE* f = fopen(path, "wb");
+        if (!f) return fail(LLGB_ERR_INVALID_ARG, std::string("cannot write ") + path);
+        const bool ok = fwrite(out.data(), 1, out.size(), f) == out.size();
+        if (fclose(f) != 0 || !ok) return fail(LLGB_ERR_INVALID_ARG, std::string("cannot write ") + path);
+        return LLGB_OK;
+    } catch (...) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    }
+}
+
+llgb_status llgb_autotune_load(const char* path)
+{
+    try {
+        if (!path) return fail(LLGB_ERR_INVALID_ARG, "null path");
+        FILE* f = fopen(path, "rb");
+        if (!f) return fail(LLGB_ERR_INVALID_ARG, std::string("cannot read ") + path);
+        std::string text;
+        char buf[4096];
+        size_t got;
+        while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+        fclose(f);
+        if (text.find("\"llgb_autotune\": 1") == std::string::npos)
+            return fail(LLGB_ERR_INVALID_ARG, "not an llgb autotune file");
+        size_t at = text.find("\"entries\"");
+        if (at == std::string::npos) return fail(LLGB_ERR_INVALID_ARG, "autotune file has no entries");
+        at = text.find('{', at);
+        std::map<std::string, llgb_launch_config> parsed;
+        while (at != std::string::npos) {
+            const size_t k0 = text.find('"', at + 1);
+            if (k0 == std::string::npos) break;
+            const size_t k1 = text.find('"', k0 + 1);
+            const size_t l0 = text.find('[', k1);
+            const size_t l1 = text.find(']', l0);
+            if (k1 == std::string::npos || l0 == std::string::npos || l1 == std::string::npos)
+                return fail(LLGB_ERR_INVALID_ARG, "malformed autotune entry");
+            int v[7];
+            if (sscanf(text.c_str() + l0, "[%d , %d , %d , %d , %d , %d , %d ]", &v[0], &v[1], &v[2], &v[3], &v[4],
+                       &v[5], &v[6]) != 7)
+                return fail(LLGB_ERR_INVALID_ARG, "malformed autotune entry");
+            llgb_launch_config c{};
+            c.tile_records = v[0];
+            c.src_stages = v[1];
+            c.dst_stages = v[2];
+            c.threads = v[3];
+            c.ctas_per_sm = v[4];
+            c.engine = v[5];
+            c.staging = v[6];
+            if (c.tile_records <= 0 || !valid_threads(c.threads) || c.src_stages < 1 || c.src_stages > 8 ||
+                c.dst_stages < 1 || c.dst_stages > 4 || c.ctas_per_sm < 1 || c.ctas_per_sm > 8 ||
+                c.engine < LLGB_ENGINE_AUTO || c.engine > LLGB_ENGINE_GATHER || c.staging < LLGB_STAGING_TMA ||
+                c.staging > LLGB_STAGING_PLAIN)
+                return fail(LLGB_ERR_INVALID_ARG, "autotune entry out of range");
+            parsed[text.substr(k0 + 1, k1 - k0 - 1)] = c;
+            at = text.find(',', l1);
+            if (at != std::string::npos && text.find('"', at) == std::string::npos) break;
+        }
+        {
+            std::lock_guard<std::mutex> lock(tune_mu);
+            for (const auto& kv : parsed) tune_cache[kv.first] = kv.second;
+        }
+        g_tune_gen.fetch_add(1);
+        return LLGB_OK;
+    } catch (...) {
+        return fail(LLGB_ERR_OOM, "out of host memory");
+    }
+}
+
 llgb_status llgb_autotune_clear(void)
 {
     std::lock_guard<std::mutex> lock(tune_mu);
     tune_cache.clear();
+    g_tune_gen.fetch_add(1);
+    return LLGB_OK;
+}
+
+llgb_status llgb_fma_probe(uint32_t iters, float* sink, uint64_t* fmas, void* stream)
+{
+    if (!sink || !fmas || iters == 0) return fail(LLGB_ERR_INVALID_ARG, "null argument or zero rounds");
+    const cudaError_t e = launch_fma_probe(iters, sink, fmas, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "FMA probe launch");
+    return LLGB_OK;
+}
+
+llgb_status llgb_wait_selftest(uint64_t limit_ns, uint64_t* waited_ns, void* stream)
+{
+    if (limit_ns < 1000ull || limit_ns > 10000000000ull)
+        return fail(LLGB_ERR_INVALID_ARG, "limit_ns must be 1 us .. 10 s");
+    if (reinterpret_cast<uintptr_t>(waited_ns) & 7u) return fail(LLGB_ERR_INVALID_ARG, "waited_ns must be 8-byte aligned");
+    const cudaError_t e = launch_wait_selftest(limit_ns, reinterpret_cast<unsigned long long*>(waited_ns),
+                                               static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test launch");
     return LLGB_OK;
 }
 

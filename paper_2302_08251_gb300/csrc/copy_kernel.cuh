@@ -1,4 +1,4 @@
-// copy.cu -- the layout-aware copy kernel (Sec. 1 of the paper: layout-aware
+// copy_kernel.cuh -- the layout-aware copy kernel (Sec. 1 of the paper: layout-aware
 // copies between views with different mappings; Sec. 3: pack on store,
 // unpack on load, ChangeType, Bytesplit).
 //
@@ -28,6 +28,13 @@
 // plain coalesced loads and stores instead of TMA.  Every wait on an mbarrier
 // is bounded; on expiry the kernel records LLGB_ERR_TIMEOUT in the device
 // status word and returns.
+//
+// Each kernel mode is compiled in a translation unit of its own
+// (copy_mode0.cu, copy_mode1.cu, copy_gather.cu), so that the modes build in
+// parallel; every unit holds its own device status word, and the host reads
+// them all (copy.cu).
+#pragma once
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,7 +47,9 @@
 
 namespace llgb {
 
-__device__ unsigned int g_device_status;
+// Status word of this translation unit's kernels (LLGB_ERR_TIMEOUT when a
+// bounded wait gave up).
+static __device__ unsigned int g_device_status;
 
 // ------------------------------------------------------------------ PTX --
 
@@ -107,14 +116,18 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
     return done != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete, for at most ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// Longest wait of a copy kernel on one mbarrier phase.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Wait for phase `parity` of `bar` to complete, for at most limit_ns (and at
+// most 2^30 suspended polls of up to 20 us each).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t spin = 0; spin < (1u << 30); ++spin) {
         if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-        if (global_timer_ns() - t0 > 2000000000ull) break;
+        if (global_timer_ns() - t0 > limit_ns) break;
     }
     return false;
 }
@@ -1075,8 +1088,14 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
 #undef LLGB_FAST_V
 }
 
+}  // namespace llgb
+
+#include "stream_loops.cuh"
+
+namespace llgb {
+
 // Zero the bit streams that generic items OR their codes into.
-__device__ __noinline__ void zero_streams(const JobDesc& J, uint8_t* dimg)
+static __device__ __noinline__ void zero_streams(const JobDesc& J, uint8_t* dimg)
 {
     for (int k = 0; k < J.npacks; ++k) {
         const PackDesc& P = J.packs[k];
@@ -1101,6 +1120,10 @@ __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc&
                                                uint8_t* dimg, uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
     const Span sp{128u * q0 + (threadIdx.x & 31u), 128u * q1, 32u};
+    // kernel mode 0 holds the loops of the compile-time stream formats
+    if constexpr (!SEGOK) {
+        if (I.spec && run_spec(I, J, simg, dimg, q0, q1, nvalid)) return;
+    }
     if (I.op == ITEM_MOVE && I.fast != FK_GENERIC && run_fast(I, J, simg, dimg, q0, q1, nvalid)) return;
     if (I.op == ITEM_MOVE) {
         const LeafRegs A = leaf_regs(J.src.leaves[I.src_leaf]);
@@ -1342,7 +1365,7 @@ __device__ __forceinline__ void run_gather(const GatherProgram<FORM>& G, const u
 }
 
 // Plain copy of `bytes` between global and shared memory by the consumers.
-__device__ void plain_copy(uint8_t* dst, const uint8_t* src, uint32_t bytes)
+static __device__ void plain_copy(uint8_t* dst, const uint8_t* src, uint32_t bytes)
 {
     const uint32_t c0 = ctid(), cn = cnum();
     const uintptr_t both = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src);
@@ -1418,7 +1441,7 @@ __device__ __forceinline__ void lane_runs_load(LaneRuns& L, const SideDesc& S, c
 // After an abort the consumers may have left: wait (bounded) for the loads
 // of the last src_stages issued tiles, which may still be landing in shared
 // memory, before the CTA exits.
-__device__ void drain_loads(const CopyArgs& a, CopyShared& H, uint32_t first, uint32_t issued)
+static __device__ void drain_loads(const CopyArgs& a, CopyShared& H, uint32_t first, uint32_t issued)
 {
     const uint32_t NS = a.src_stages;
     for (uint32_t k = issued > NS ? issued - NS : 0u; k < issued; ++k) {
@@ -1433,7 +1456,7 @@ __device__ void drain_loads(const CopyArgs& a, CopyShared& H, uint32_t first, ui
 // One warp for both directions (gather kernels, whose consumers are cheap
 // per byte and need every warp): TMA loads `src_stages` tiles ahead, bulk
 // stores as the consumers finish each destination stage.
-__device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint8_t* dst_stage, uint32_t first,
+static __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint8_t* dst_stage, uint32_t first,
                          uint32_t count)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -1498,7 +1521,7 @@ __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
 
 // Load warp: brings tile k into source stage k % NS with TMA bulk loads as
 // soon as the consumers have released the stage's previous tile.
-__device__ void load_producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint32_t first, uint32_t count)
+static __device__ void load_producer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, uint32_t first, uint32_t count)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t NS = a.src_stages;
@@ -1538,7 +1561,7 @@ __device__ void load_producer(const CopyArgs& a, CopyShared& H, uint8_t* src_sta
 // the consumers have finished tile k, and releases the stage for tile k+ND
 // as soon as the store has read it.  Loads and stores are issued by two
 // warps so that neither waits behind the other's (serial) issue.
-__device__ void store_producer(const CopyArgs& a, CopyShared& H, uint8_t* dst_stage, uint32_t first, uint32_t count)
+static __device__ void store_producer(const CopyArgs& a, CopyShared& H, uint8_t* dst_stage, uint32_t first, uint32_t count)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t ND = a.dst_stages;
@@ -1762,12 +1785,8 @@ __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ Co
     if (H.abort && threadIdx.x == 0) atomicOr(&g_device_status, (unsigned)LLGB_ERR_TIMEOUT);
 }
 
-// ------------------------------------------------------------ launcher --
-
-size_t copy_shared_header_bytes() { return (sizeof(CopyShared) + 15u) & ~size_t(15); }
-
-int gather_words_per_thread(int mode) { return mode == 2 ? GatherMax<2>::value : (mode == 4 ? GatherMax<4>::value : 0); }
-
+// Host side of one translation unit: its kernels' shared-memory limit and
+// launch, and its status word.
 template <int MODE>
 static cudaError_t prepare_mode(size_t smem_bytes)
 {
@@ -1785,16 +1804,6 @@ static cudaError_t prepare_mode(size_t smem_bytes)
     return cudaSuccess;
 }
 
-cudaError_t prepare_copy(int mode, size_t smem_bytes)
-{
-    switch (mode) {
-    case 1: return prepare_mode<1>(smem_bytes);
-    case 2: return prepare_mode<2>(smem_bytes);
-    case 4: return prepare_mode<4>(smem_bytes);
-    default: return prepare_mode<0>(smem_bytes);
-    }
-}
-
 template <int MODE>
 static cudaError_t launch_mode(const CopyArgs& args, int grid, int threads, size_t smem_bytes, cudaStream_t stream)
 {
@@ -1804,24 +1813,15 @@ static cudaError_t launch_mode(const CopyArgs& args, int grid, int threads, size
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, size_t smem_bytes,
-                        cudaStream_t stream)
+// OR this unit's status word into *out (after the caller synchronised the
+// device); reset clears it.
+static cudaError_t unit_status(unsigned* out, bool reset)
 {
-    switch (mode) {
-    case 1: return launch_mode<1>(args, grid, threads, smem_bytes, stream);
-    case 2: return launch_mode<2>(args, grid, threads, smem_bytes, stream);
-    case 4: return launch_mode<4>(args, grid, threads, smem_bytes, stream);
-    default: return launch_mode<0>(args, grid, threads, smem_bytes, stream);
-    }
-}
-
-cudaError_t read_device_status(unsigned* out, bool reset)
-{
-    cudaError_t e = cudaDeviceSynchronize();
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_status, sizeof(unsigned));
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyFromSymbol(out, g_device_status, sizeof(unsigned));
-    if (e != cudaSuccess) return e;
-    if (reset) {
+    *out |= v;
+    if (reset && v) {
         const unsigned zero = 0;
         e = cudaMemcpyToSymbol(g_device_status, &zero, sizeof(unsigned));
     }

@@ -25,7 +25,7 @@ __device__ __forceinline__ uint64_t low_bits64(int w)
 }
 
 // General conversion with integer operations only.
-__device__ __noinline__ uint64_t fconv_general(uint64_t x, int se, int sm, int de, int dm)
+static __device__ __noinline__ uint64_t fconv_general(uint64_t x, int se, int sm, int de, int dm)
 {
     const uint32_t s_all = (1u << se) - 1u;
     const uint32_t d_all = (1u << de) - 1u;

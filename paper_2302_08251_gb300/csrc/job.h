@@ -84,7 +84,7 @@ struct ItemDesc {
     uint8_t fast;        // FastKind of the specialised loop, FK_GENERIC if none
     uint8_t vpl;         // specialised loop: consecutive records per lane (1, 2, 4)
     uint8_t runs;        // specialised loop: a bit leaf of the item is AoSoA-organised
-    uint8_t pad;
+    uint8_t spec;        // id of the item's compile-time stream format (stream_specs.h), 0 if none
 };
 
 // Specialised VALUE loops (element sizes and conversion fixed at compile time).

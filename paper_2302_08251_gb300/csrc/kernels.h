@@ -20,6 +20,9 @@ int gather_words_per_thread(int mode);
 cudaError_t prepare_copy(int mode, size_t smem_bytes);
 size_t copy_shared_header_bytes();
 cudaError_t read_device_status(unsigned* out, bool reset);
+// The bounded-wait self-test kernel (one CTA waits limit_ns on an mbarrier
+// nothing arrives on, then records LLGB_ERR_TIMEOUT).
+cudaError_t launch_wait_selftest(uint64_t limit_ns, unsigned long long* waited_ns, cudaStream_t stream);
 
 // nbody.cu: a particle view.  Leaf f of record i lies at base[f] + off(i),
 //   AoS     off(i) = 28 i                       (lanes 1,  bstride 28)
@@ -73,6 +76,8 @@ cudaError_t launch_nbody_update(const ParticleView& v, int kind, int traversal, 
 cudaError_t launch_nbody_move(const ParticleView& v, int kind, int layout, int traversal, float dt,
                               cudaStream_t stream);
 // div: the view is AoSoA with a lane count that is not a power of two.
+// FP32 FMA throughput probe: *fmas receives the FMAs the launch performs.
+cudaError_t launch_fma_probe(uint32_t iters, float* sink, uint64_t* fmas, cudaStream_t stream);
 cudaError_t launch_nbody_instrumented(const ParticleView& v, bool div, const NbodyInstr& ins, float eps, float dt,
                                       cudaStream_t stream);
 

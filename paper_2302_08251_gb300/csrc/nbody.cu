@@ -505,4 +505,37 @@ cudaError_t launch_nbody_move(const ParticleView& v, int kind, int layout, int t
     }
 }
 
+// FP32 fused multiply-add throughput probe: the roofline of the n-body
+// update, which is bound by its FP32 arithmetic.  Every thread runs 16
+// independent FMA chains for `iters` rounds (16 iters FMAs per thread); the
+// chains' sum is stored only when it is exactly -1, which the inputs never
+// give but the compiler cannot rule out, so no FMA is removed.
+__global__ void __launch_bounds__(256) fma_probe_kernel(uint32_t iters, float* sink)
+{
+    float a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = (float)(threadIdx.x + k) * 1e-6f;
+    const float b = 0.9999999f, c = 1e-7f;
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = fmaf(a[k], b, c);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s += a[k];
+    if (s == -1.0f) *sink = s;
+}
+
+cudaError_t launch_fma_probe(uint32_t iters, float* sink, uint64_t* fmas, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const uint32_t grid = (uint32_t)sms * 8u;  // 8 x 256 threads: every warp slot of an SM
+    fma_probe_kernel<<<grid, 256, 0, stream>>>(iters, sink);
+    *fmas = (uint64_t)grid * 256u * 16u * iters;
+    return cudaGetLastError();
+}
+
 }  // namespace llgb

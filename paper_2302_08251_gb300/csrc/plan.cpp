@@ -14,6 +14,7 @@
 // contiguous run per blob region, and inside a tile image the same affine
 // form holds with 32-bit tile-local offsets.
 #include "plan.h"
+#include "stream_specs.h"
 
 #include <string.h>
 
@@ -680,8 +681,35 @@ static bool affine_for(const LeafDesc& L, int V)
     return L.lshift != 0xFF && L.lanes % (uint32_t)V == 0 && L.lanes <= 32u * (uint32_t)V;
 }
 
+// Id of the compile-time stream format (stream_specs.h) of a VALUE item that
+// packs a 4- or 8-byte affine leaf into a SoA bit stream, or unpacks one, or
+// 0: the leaf's type and the stream's width (and float format) must match an
+// entry, and the affine leaf must allow the entry's records per lane.
+static int stream_spec_id(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
+{
+    const bool pack = it.lop == L_DIRECT && (it.sop == S_BITS_INT || it.sop == S_BITS_FLOAT);
+    const bool unpack = (it.lop == L_BITS_INT || it.lop == L_BITS_FLOAT) && it.sop == S_DIRECT;
+    if (!pack && !unpack) return 0;
+    const LeafDesc& P = pack ? A : B;  // the affine leaf
+    const LeafDesc& S = pack ? B : A;  // the bit stream
+    if (P.kind != LEAF_AFFINE || S.kind != LEAF_BITS || S.lanes != 0) return 0;
+    const int is_float = (pack ? it.sop == S_BITS_FLOAT : it.lop == L_BITS_FLOAT) ? 1 : 0;
+    const int size = it.size;
+    for (const StreamSpecInfo& sp : kStreamSpecs) {
+        if (sp.is_float != is_float || sp.leaf_bytes != size || sp.bits != (int)S.bits) continue;
+        if (is_float) {
+            if (it.l_e != (size == 8 ? 11 : 8) || it.l_m != (size == 8 ? 52 : 23)) continue;
+            if ((pack ? it.d_e : it.s_e) != sp.exp || (pack ? it.d_m : it.s_m) != sp.man) continue;
+        }
+        if ((int)P.align < size || !affine_for(P, stream_vpl(size, sp.bits))) return 0;
+        return sp.id;
+    }
+    return 0;
+}
+
 static void set_fast_kind(ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
 {
+    it.spec = (uint8_t)stream_spec_id(it, A, B);
     const int k = fast_kind(it, A, B);
     int V = 0;
     switch (k) {

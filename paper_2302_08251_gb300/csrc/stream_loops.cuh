@@ -1,0 +1,303 @@
+// stream_loops.cuh -- pack and unpack loops of SoA bit streams whose format
+// is known at compile time (the formats of stream_specs.h).  Included by
+// copy_kernel.cuh after the shared-memory and lane helpers it uses.
+//
+// Pack (Sec. 3: values are packed when stored).  A warp takes super-groups of
+// 32 V records; lane l holds records V l .. V l + V - 1 of each:
+//   1. the lane loads its V leaf elements with one vector access and turns
+//      them into w-bit codes (the low w bits of an integer; a float rounded
+//      to (E, M), nearest even, by constant-shift integer arithmetic);
+//   2. the codes form the lane's chunk of C = V w bits (code v at bit v w);
+//   3. narrow chunks (C < 32) are merged over T = 2, 4 or 8 neighbouring
+//      lanes (a shuffle per doubling), so that every merged chunk has
+//      CC = T C bits with 32 <= CC <= 64;
+//   4. output word k of the super-group takes bits [32 k, 32 k + 32) of the
+//      merged chunks: at most two of them reach it, fetched with shuffles from
+//      lanes j0 T and (j0 + 1) T (j0 = floor(32 k / CC)); lane k builds and
+//      stores word k (two rounds when the super-group has more than 32 words).
+// Unpack (values are unpacked when loaded): lane l reads its C-bit chunk at
+// bit l C of the super-group (two or three words and funnel shifts), splits
+// it into V codes, converts them and stores its V elements with one vector
+// access.
+// Records at or past the tile's valid count are taken as zero (and so written
+// as zero).  Float values whose result is not a normal number of the target
+// (zero aside), and NaN and INF inputs, are redone by fconv_general; the
+// warp votes on whether any lane has one, so the common case pays one vote.
+#pragma once
+
+#include "stream_specs.h"
+
+namespace llgb {
+
+// Rounding conversion of a normal number between binary formats (SE, SM) ->
+// (DE, DM), by integer operations on the bit pattern: the magnitude bits
+// (exponent and mantissa) are shifted by SM - DM with rounding to nearest,
+// ties to even (add 2^(k-1) - 1 plus the lowest kept bit, then drop k bits: a
+// carry moves into the exponent, and past the largest exponent it gives the
+// INF code), then the exponent is rebiased by adding a constant.  `bad` is set
+// for inputs this does not cover: source exponents whose target exponent is
+// out of range (subnormal or overflowing results, subnormal inputs, INF, NaN).
+// Zero maps to zero.
+template <int SE, int SM, int DE, int DM>
+__device__ __forceinline__ uint64_t conv_fast(uint64_t x, bool& bad)
+{
+    constexpr int SB = (1 << (SE - 1)) - 1, DB = (1 << (DE - 1)) - 1;
+    constexpr int K = SM - DM;
+    constexpr int E_LO = (SB - DB + 1) > 1 ? (SB - DB + 1) : 1;
+    constexpr int E_HI = ((1 << DE) - 2 + SB - DB) < ((1 << SE) - 2) ? ((1 << DE) - 2 + SB - DB) : ((1 << SE) - 2);
+    constexpr uint64_t AMASK = (SE + SM >= 64) ? ~0ull : ((1ull << (SE + SM)) - 1ull);
+    constexpr uint64_t REBIAS = (uint64_t)((int64_t)(DB - SB) * (int64_t)(1ll << DM));
+    const uint32_t e = (uint32_t)(x >> SM) & ((1u << SE) - 1u);
+    const uint64_t a = x & AMASK;
+    uint64_t r;
+    if constexpr (K > 0)
+        r = (a + ((1ull << (K - 1)) - 1ull) + ((a >> K) & 1ull)) >> K;
+    else
+        r = a << (-K);
+    r += REBIAS;
+    const bool zero = a == 0ull;
+    bad = !zero && (e - (uint32_t)E_LO) > (uint32_t)(E_HI - E_LO);
+    const uint64_t sign = ((x >> (SE + SM)) & 1ull) << (DE + DM);
+    return sign | (zero ? 0ull : r);
+}
+
+// One entry of stream_specs.h: leaf type, code format and loop shape.
+template <int FL, int SZ_, int E_, int M_, int W_>
+struct StreamSpec {
+    static constexpr bool FLOAT = FL != 0;
+    static constexpr int SZ = SZ_;                  // leaf bytes
+    static constexpr int E = E_, M = M_, W = W_;    // code format
+    static constexpr int LE = SZ == 8 ? 11 : 8;     // leaf float format
+    static constexpr int LM = SZ == 8 ? 52 : 23;
+    static constexpr int V = stream_vpl(SZ, W);     // records per lane per super-group
+    static constexpr int C = V * W;                 // chunk bits per lane = words per super-group
+    static constexpr int T = C >= 32 ? 1 : (2 * C >= 32 ? 2 : (4 * C >= 32 ? 4 : 8));
+    static constexpr int CC = T * C;                // merged chunk bits (32 .. 64)
+    static constexpr int ROUNDS = (C + 31) / 32;    // output words per lane per super-group
+    static constexpr int B = 4 / V;                 // super-groups per iteration (4 records per lane)
+    using Elem = typename std::conditional<SZ == 8, uint64_t, uint32_t>::type;
+    static constexpr uint64_t CODE_MASK = W >= 64 ? ~0ull : ((1ull << W) - 1ull);
+    static_assert(CC >= 32 && CC <= 64, "merged chunks hold 32 to 64 bits");
+};
+
+// Words a lane reads for its chunk in unpack: its chunk starts at bit
+// (l C) mod 32 of its first word.
+template <int C>
+constexpr int chunk_read_words()
+{
+    int most = 0;
+    for (int l = 0; l < 32; ++l) {
+        const int need = ((l * C) % 32 + C + 31) / 32;
+        most = need > most ? need : most;
+    }
+    return most;
+}
+
+template <class S>
+__device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                         uint32_t g0, uint32_t g1, uint32_t nvalid)
+{
+    constexpr int V = S::V, W = S::W, C = S::C, T = S::T, CC = S::CC, ROUNDS = S::ROUNDS, B = S::B;
+    constexpr bool WIDE = CC > 32;              // merged chunks have a high word
+    constexpr bool NEXT = (CC % 32) != 0;       // a word can reach into the next merged chunk
+    using Elem = typename S::Elem;
+    using Chunk = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    const LaneRun RA = affine_run<V, S::SZ>(J.src.leaves[I.src_leaf], lane);
+    const uint32_t sa = smem_addr(simg) + RA.off;
+    const uint32_t da = smem_addr(dimg) + J.dst.leaves[I.dst_leaf].sbase + 4u * lane;
+    // word k = lane + 32 m: merged chunk j0 from bit r on (lane src0), and the
+    // next merged chunk (lane src1) from bit 0 on, shifted up by CC - r
+    uint32_t src0[ROUNDS], src1[ROUNDS], sh[ROUNDS], up[ROUNDS];
+    bool hisel[ROUNDS], mine[ROUNDS];
+#pragma unroll
+    for (int m = 0; m < ROUNDS; ++m) {
+        const uint32_t k = lane + 32u * m;
+        const uint32_t j0 = 32u * k / CC;
+        const uint32_t r = 32u * k - j0 * CC;
+        src0[m] = (j0 * T) & 31u;
+        src1[m] = ((j0 + 1u) * T) & 31u;
+        hisel[m] = r >= 32u;
+        sh[m] = r & 31u;
+        up[m] = CC - r;
+        mine[m] = k < (uint32_t)C;
+    }
+
+    auto body = [&](uint32_t g, auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
+        Elem x[B][V];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const uint32_t gg = g + b;
+            const uint32_t rec0 = 32u * V * gg + (uint32_t)V * lane;
+            if (CHECK) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[b][v] = 0;
+                if (gg >= g1 || rec0 >= nvalid) continue;
+                if (rec0 + V > nvalid) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        x[b][v] = rec0 + v < nvalid ? (Elem)lds<S::SZ>(sa + gg * RA.step + v * RA.vstride) : (Elem)0;
+                    continue;
+                }
+            }
+            ld_run<V, S::SZ, Elem>(sa + gg * RA.step, RA, x[b]);
+        }
+        uint64_t c[B][V];
+        if constexpr (S::FLOAT) {
+            uint32_t bad = 0;
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    bool bd;
+                    c[b][v] = conv_fast<S::LE, S::LM, S::E, S::M>((uint64_t)x[b][v], bd);
+                    bad |= (uint32_t)bd << (b * V + v);
+                }
+            if (__any_sync(0xFFFFFFFFu, bad != 0u)) {
+#pragma unroll
+                for (int b = 0; b < B; ++b)
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if ((bad >> (b * V + v)) & 1u) c[b][v] = fconv_general((uint64_t)x[b][v], S::LE, S::LM, S::E, S::M);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int v = 0; v < V; ++v) c[b][v] = (uint64_t)x[b][v] & S::CODE_MASK;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const uint32_t gg = g + b;
+            if (CHECK && gg >= g1) break;
+            Chunk ch = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) ch |= (Chunk)c[b][v] << (v * W);
+#pragma unroll
+            for (int d = 1; d < T; d *= 2) {
+                const uint32_t p = __shfl_down_sync(0xFFFFFFFFu, (uint32_t)ch, d);
+                ch |= (Chunk)p << (C * d);
+            }
+            const uint32_t lo = (uint32_t)ch;
+            const uint32_t hi = WIDE ? (uint32_t)((uint64_t)ch >> 32) : 0u;
+            const uint32_t q = da + gg * (uint32_t)(4 * C);
+#pragma unroll
+            for (int m = 0; m < ROUNDS; ++m) {
+                const uint32_t a_lo = __shfl_sync(0xFFFFFFFFu, lo, src0[m]);
+                const uint32_t a_hi = WIDE ? __shfl_sync(0xFFFFFFFFu, hi, src0[m]) : 0u;
+                const uint32_t nx = NEXT ? __shfl_sync(0xFFFFFFFFu, lo, src1[m]) : 0u;
+                uint32_t word = __funnelshift_r(hisel[m] ? a_hi : a_lo, hisel[m] ? 0u : a_hi, sh[m]);
+                if (NEXT) word |= shl_c(nx, up[m]);
+                if (mine[m]) sts<4>(q + 128u * m, word);
+            }
+        }
+    };
+    const uint32_t gfull = min(g1, max(g0, nvalid / (32u * V)));  // super-groups below hold valid records only
+    uint32_t g = g0;
+    for (; g + B <= gfull; g += B) body(g, std::false_type{});
+    for (; g < g1; g += B) body(g, std::true_type{});
+}
+
+template <class S>
+__device__ __noinline__ void stream_unpack(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                           uint32_t g0, uint32_t g1, uint32_t nvalid)
+{
+    constexpr int V = S::V, W = S::W, C = S::C, B = S::B;
+    constexpr int NW = chunk_read_words<C>();
+    static_assert(NW >= 1 && NW <= 3, "a chunk spans at most three words");
+    using Elem = typename S::Elem;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t bit = lane * (uint32_t)C;
+    const uint32_t sa = smem_addr(simg) + J.src.leaves[I.src_leaf].sbase + 4u * (bit >> 5);
+    const uint32_t sh = bit & 31u;
+    const LaneRun RB = affine_run<V, S::SZ>(J.dst.leaves[I.dst_leaf], lane);
+    const uint32_t da = smem_addr(dimg) + RB.off;
+    const bool sgn = I.is_signed != 0;
+
+    auto body = [&](uint32_t g, auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
+        uint64_t c[B][V];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (CHECK && g + b >= g1) {  // past the share: nothing to read
+#pragma unroll
+                for (int v = 0; v < V; ++v) c[b][v] = 0;
+                continue;
+            }
+            const uint32_t p = sa + (g + b) * (uint32_t)(4 * C);
+            const uint32_t w0 = (uint32_t)lds<4>(p);
+            const uint32_t w1 = NW > 1 ? (uint32_t)lds<4>(p + 4u) : 0u;
+            const uint32_t w2 = NW > 2 ? (uint32_t)lds<4>(p + 8u) : 0u;
+            const uint64_t chunk = ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
+#pragma unroll
+            for (int v = 0; v < V; ++v) c[b][v] = (chunk >> (v * W)) & S::CODE_MASK;
+        }
+        Elem x[B][V];
+        if constexpr (S::FLOAT) {
+            uint32_t bad = 0;
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    bool bd;
+                    x[b][v] = (Elem)conv_fast<S::E, S::M, S::LE, S::LM>(c[b][v], bd);
+                    bad |= (uint32_t)bd << (b * V + v);
+                }
+            if (__any_sync(0xFFFFFFFFu, bad != 0u)) {
+#pragma unroll
+                for (int b = 0; b < B; ++b)
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if ((bad >> (b * V + v)) & 1u) x[b][v] = (Elem)fconv_general(c[b][v], S::E, S::M, S::LE, S::LM);
+            }
+        } else {
+            constexpr uint32_t UP = 32u - (uint32_t)W;
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t u = (uint32_t)c[b][v];
+                    x[b][v] = sgn ? (uint32_t)(((int32_t)(u << UP)) >> UP) : u;
+                }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const uint32_t gg = g + b;
+            if (CHECK && gg >= g1) break;
+            const uint32_t rec0 = 32u * V * gg + (uint32_t)V * lane;
+            if (CHECK && rec0 + V > nvalid) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (rec0 + v >= nvalid) x[b][v] = 0;
+            }
+            st_run<V, S::SZ, Elem>(da + gg * RB.step, RB, x[b]);
+        }
+    };
+    const uint32_t gfull = min(g1, max(g0, nvalid / (32u * V)));
+    uint32_t g = g0;
+    for (; g + B <= gfull; g += B) body(g, std::false_type{});
+    for (; g < g1; g += B) body(g, std::true_type{});
+}
+
+// Runs a VALUE item over quads [q0, q1) (128 records each) in the loop of its
+// compile-time format (ItemDesc::spec); false when it has none.
+__device__ __forceinline__ bool run_spec(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                         uint32_t q0, uint32_t q1, uint32_t nvalid)
+{
+    const bool pack = I.sop == S_BITS_INT || I.sop == S_BITS_FLOAT;
+    switch (I.spec) {
+#define LLGB_SPEC_CASE(id, fl, sz, e, m, w)                                                                \
+    case id: {                                                                                             \
+        using S = StreamSpec<fl, sz, e, m, w>;                                                             \
+        if (pack) stream_pack<S>(I, J, simg, dimg, q0 * (4u / S::V), q1 * (4u / S::V), nvalid);          \
+        else stream_unpack<S>(I, J, simg, dimg, q0 * (4u / S::V), q1 * (4u / S::V), nvalid);             \
+        return true;                                                                                       \
+    }
+        LLGB_STREAM_SPECS(LLGB_SPEC_CASE)
+#undef LLGB_SPEC_CASE
+    default: return false;
+    }
+}
+
+}  // namespace llgb

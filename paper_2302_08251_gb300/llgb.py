@@ -50,7 +50,7 @@ class Extents(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("kernel_mode", ctypes.c_int32), ("batch_kernel_mode", ctypes.c_int32),
                 ("tile_records", ctypes.c_int32), ("items", ctypes.c_int32),
-                ("generic_items", ctypes.c_int32), ("reserved", ctypes.c_int32), ("tiles", ctypes.c_uint64)]
+                ("generic_items", ctypes.c_int32), ("stream_items", ctypes.c_int32), ("tiles", ctypes.c_uint64)]
 
 
 class MappingDesc(ctypes.Structure):
@@ -74,17 +74,18 @@ MappingDesc._fields_ = [
 
 
 ENGINES = {"auto": 0, "value": 1, "gather": 2}
+STAGING = {"tma": 0, "plain_store": 1, "plain_load": 2, "plain": 3}
 
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("tile_records", ctypes.c_int32), ("src_stages", ctypes.c_int32),
                 ("dst_stages", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("staging", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k in
-                ("tile_records", "src_stages", "dst_stages", "threads", "ctas_per_sm")}
+                ("tile_records", "src_stages", "dst_stages", "threads", "ctas_per_sm", "staging")}
 
 
 EXPORTS = [
@@ -96,6 +97,7 @@ EXPORTS = [
     "llgb_copy_with", "llgb_nbody_step", "llgb_device_status",
     "llgb_batch_create", "llgb_batch_launch", "llgb_batch_info", "llgb_batch_destroy",
     "llgb_autotune", "llgb_autotune_clear", "llgb_batch_copy_noalloc", "llgb_copy_plan",
+    "llgb_wait_selftest", "llgb_fma_probe", "llgb_autotune_save", "llgb_autotune_load", "llgb_batch_arena_create", "llgb_batch_arena_copy", "llgb_batch_arena_destroy",
 ]
 
 _lib = None
@@ -147,6 +149,13 @@ def lib():
         L.llgb_batch_destroy.argtypes = [p]
         L.llgb_autotune.argtypes = [p, p, p, ctypes.POINTER(LaunchConfig)]
         L.llgb_batch_copy_noalloc.argtypes = [i32, ctypes.POINTER(p), ctypes.POINTER(p), p]
+        L.llgb_wait_selftest.argtypes = [u64, p, p]
+        L.llgb_autotune_save.argtypes = [ctypes.c_char_p]
+        L.llgb_autotune_load.argtypes = [ctypes.c_char_p]
+        L.llgb_fma_probe.argtypes = [ctypes.c_uint32, p, ctypes.POINTER(u64), p]
+        L.llgb_batch_arena_create.argtypes = [i32, i32, ctypes.POINTER(p)]
+        L.llgb_batch_arena_copy.argtypes = [p, i32, ctypes.POINTER(p), ctypes.POINTER(p), p]
+        L.llgb_batch_arena_destroy.argtypes = [p]
         _lib = L
     return _lib
 
@@ -322,6 +331,18 @@ def llgb_unpack(packed: View, plain: View, stream=None) -> None:
     check(lib().llgb_unpack(packed.handle, plain.handle, _stream_ptr(stream)))
 
 
+def launch_config(cfg: dict) -> LaunchConfig:
+    """An llgb_launch_config from a dict; "engine" and "staging" may be names."""
+    c = LaunchConfig()
+    for k, v in cfg.items():
+        if k == "engine" and isinstance(v, str):
+            v = ENGINES[v]
+        elif k == "staging" and isinstance(v, str):
+            v = STAGING[v]
+        setattr(c, k, int(v))
+    return c
+
+
 def llgb_copy_plan(src: View, dst: View, cfg: dict | None = None) -> dict:
     """Host-only plan of llgb_copy(src, dst) (and of the pair as a batch
     entry): kernel modes, tiling and item counts; nothing is launched."""
@@ -331,14 +352,10 @@ def llgb_copy_plan(src: View, dst: View, cfg: dict | None = None) -> dict:
 def plan_info(src_handle, dst_handle, cfg: dict | None = None) -> dict:
     """llgb_copy_plan on raw view handles (bound or not)."""
     info = PlanInfo()
-    c = None
-    if cfg is not None:
-        c = LaunchConfig()
-        for k, v in cfg.items():
-            setattr(c, k, ENGINES[v] if k == "engine" else int(v))
+    c = launch_config(cfg) if cfg is not None else None
     check(lib().llgb_copy_plan(src_handle, dst_handle, ctypes.byref(c) if c is not None else None,
                                ctypes.byref(info)))
-    return {k: getattr(info, k) for k, _ in PlanInfo._fields_ if k != "reserved"}
+    return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
 
 
 def llgb_copy_config(src: View, dst: View) -> dict:
@@ -350,9 +367,7 @@ def llgb_copy_config(src: View, dst: View) -> dict:
 def llgb_copy_with(src: View, dst: View, cfg: dict, stream=None) -> None:
     """llgb_copy with an explicit launch shape; cfg may also hold
     "engine": "auto" | "value" | "gather"."""
-    c = LaunchConfig()
-    for k, v in cfg.items():
-        setattr(c, k, ENGINES[v] if k == "engine" else int(v))
+    c = launch_config(cfg)
     check(lib().llgb_copy_with(src.handle, dst.handle, ctypes.byref(c), _stream_ptr(stream)))
 
 
@@ -393,6 +408,21 @@ def llgb_nbody_step_instrumented(view: View, eps: float, dt: float, field_counts
                                              ht, int(granularity), _stream_ptr(stream)))
 
 
+def llgb_wait_selftest(limit_ns: int, waited=None, stream=None) -> None:
+    """Queue the bounded-wait self-test kernel (include/llgb.h); `waited`: an
+    int64 device tensor of one element that receives the wait's length in ns."""
+    w = ctypes.c_void_p(waited.data_ptr()) if waited is not None else None
+    check(lib().llgb_wait_selftest(int(limit_ns), w, _stream_ptr(stream)))
+
+
+def llgb_fma_probe(iters: int, sink, stream=None) -> int:
+    """Queue the FP32 FMA throughput probe; returns the FMAs it performs.
+    `sink`: a float32 device tensor of at least one element."""
+    fmas = ctypes.c_uint64()
+    check(lib().llgb_fma_probe(int(iters), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fmas), _stream_ptr(stream)))
+    return fmas.value
+
+
 def llgb_device_status(reset: bool = False) -> int:
     code = ctypes.c_int32()
     check(lib().llgb_device_status(ctypes.byref(code), int(reset)))
@@ -429,6 +459,32 @@ class Batch:
         self.close()
 
 
+class Arena:
+    """Descriptor tables for `slots` batched copies of up to `max_pairs` pairs,
+    allocated once; copy() queues one batched copy without allocating."""
+
+    def __init__(self, max_pairs: int = 256, slots: int = 8):
+        h = ctypes.c_void_p()
+        check(lib().llgb_batch_arena_create(int(max_pairs), int(slots), ctypes.byref(h)))
+        self.handle = h
+        self.max_pairs = int(max_pairs)
+
+    def copy(self, pairs, stream=None) -> None:
+        pairs = list(pairs)
+        n = len(pairs)
+        srcs = (ctypes.c_void_p * max(1, n))(*[s.handle for s, _ in pairs])
+        dsts = (ctypes.c_void_p * max(1, n))(*[d.handle for _, d in pairs])
+        check(lib().llgb_batch_arena_copy(self.handle, n, srcs, dsts, _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.llgb_batch_arena_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
 def llgb_batch_create(pairs) -> Batch:
     return Batch(pairs)
 
@@ -456,6 +512,14 @@ def llgb_batch_copy_noalloc(pairs, stream=None) -> None:
 
 def llgb_autotune_clear() -> None:
     check(lib().llgb_autotune_clear())
+
+
+def llgb_autotune_save(path: str) -> None:
+    check(lib().llgb_autotune_save(os.fsencode(path)))
+
+
+def llgb_autotune_load(path: str) -> None:
+    check(lib().llgb_autotune_load(os.fsencode(path)))
 
 
 copy = llgb_copy

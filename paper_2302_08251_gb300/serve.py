@@ -166,10 +166,13 @@ class Server:
 # ---------------------------------------------------------------- device --
 
 class GpuExecutor:
-    """Runs request batches through the CUDA library on k streams.  Source
-    blobs are filled on the request's stream at admission (seeded bytes)."""
+    """Runs request batches through the CUDA library on k streams, each batch
+    one llgb_batch_arena_copy (fused launches over descriptor tables allocated
+    once).  Source blobs are filled on the request's stream at admission
+    (seeded bytes)."""
 
-    def __init__(self, streams: int = 4, device=None, seed: int = 1, keep: bool = False):
+    def __init__(self, streams: int = 4, device=None, seed: int = 1, keep: bool = False,
+                 max_batch: int = 256):
         import torch
         from . import llgb
         self.torch = torch
@@ -177,6 +180,11 @@ class GpuExecutor:
         self.device = device if device is not None else torch.device("cuda")
         self.streams = streams
         self._streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        # descriptor tables for every batch, allocated once: launching a batch
+        # then neither allocates nor frees device memory, and nothing in the
+        # loop synchronises the device
+        with torch.cuda.device(self.device):
+            self._arena = llgb.Arena(max_pairs=max_batch, slots=2 * streams + 2)
         self._records = {}
         self._sizes = {}
         self.seed = seed
@@ -221,11 +229,10 @@ class GpuExecutor:
         s = self._streams[stream_index]
         for r in reqs:                     # sources were filled on their own streams
             s.wait_stream(r.views[2])
-        batch = self.llgb.Batch([(r.views[0], r.views[1]) for r in reqs])
-        batch.launch(stream=s)
+        self._arena.copy([(r.views[0], r.views[1]) for r in reqs], stream=s)
         ev = torch.cuda.Event()
         ev.record(s)
-        return (ev, batch, s)
+        return (ev, s)
 
     def done(self, handle) -> bool:
         return handle[0].query()

@@ -223,7 +223,10 @@ def test_copy_with_rejects_an_unknown_engine():
     c = llgb.LaunchConfig(tile_records=128, src_stages=2, dst_stages=2, threads=256, ctas_per_sm=1, engine=7)
     assert L.llgb_copy_with(hs[0], hs[1], ctypes.byref(c), None) == llgb.ERR_INVALID_ARG
     c.engine = 1
-    c.reserved[1] = 5
+    c.reserved = 5
+    assert L.llgb_copy_with(hs[0], hs[1], ctypes.byref(c), None) == llgb.ERR_INVALID_ARG
+    c.reserved = 0
+    c.staging = 4
     assert L.llgb_copy_with(hs[0], hs[1], ctypes.byref(c), None) == llgb.ERR_INVALID_ARG
     for h in hs:
         L.llgb_view_destroy(h)
@@ -377,4 +380,83 @@ def test_plan_engine_value_keeps_run_addressed_jobs_in_mode_1():
 
 def test_plan_of_an_empty_pair_is_zero():
     assert plan_of(synth.INT6, {"kind": "aos"}, {"kind": "soa_mb"}, 0) == {
-        "kernel_mode": 0, "batch_kernel_mode": 0, "tile_records": 0, "items": 0, "generic_items": 0, "tiles": 0}
+        "kernel_mode": 0, "batch_kernel_mode": 0, "tile_records": 0, "items": 0, "generic_items": 0,
+        "stream_items": 0, "tiles": 0}
+
+
+@pytest.mark.parametrize("bits", [1, 3, 7, 12, 17, 31])
+def test_plan_configured_integer_widths_run_compile_time_stream_loops(bits):
+    m = {"kind": "bitpack_int", "bits": bits}
+    for src, dst in (({"kind": "soa_mb"}, m), (m, {"kind": "soa_mb"}), ({"kind": "aos"}, m), (m, {"kind": "aos"})):
+        p = plan_of(synth.INT6, src, dst, 1 << 20)
+        assert p["kernel_mode"] == 0 and p["stream_items"] == 6, (src, dst)
+
+
+@pytest.mark.parametrize("e,m", [(e, m) for e in (5, 8, 11) for m in (2, 10, 23, 52)])
+def test_plan_configured_float_formats_run_compile_time_stream_loops(e, m):
+    fmt = {"kind": "bitpack_float", "exp": e, "man": m}
+    # x, y, z are f64 and w is f32: f64 as E8M23 / E11M52 and f32 as E8M23 are
+    # plain element moves with loops of their own
+    want = 3 * ((e, m) not in ((8, 23), (11, 52))) + ((e, m) != (8, 23))
+    for src, dst in (({"kind": "soa_mb"}, fmt), (fmt, {"kind": "soa_mb"})):
+        p = plan_of(synth.MIXED_F, src, dst, 1 << 20)
+        assert p["kernel_mode"] == 0 and p["stream_items"] == want and p["generic_items"] == 0, (src, dst)
+
+
+def test_plan_other_widths_and_organisations_keep_the_run_time_loops():
+    for m in ({"kind": "bitpack_int", "bits": 5}, {"kind": "bitpack_int", "bits": 12, "lanes": 256},
+              {"kind": "bitpack_int", "bits": 12, "field_bits": [12, 12, 12, 12, 12, 9]}):
+        p = plan_of(synth.INT6, {"kind": "soa_mb"}, m, 1 << 20)
+        assert p["stream_items"] == (5 if "field_bits" in m else 0), m
+    p = plan_of(synth.MIXED_F, {"kind": "soa_mb"}, {"kind": "bitpack_float", "exp": 6, "man": 9}, 1 << 20)
+    assert p["stream_items"] == 0 and p["generic_items"] == 0
+
+
+def test_wait_selftest_rejects_limits_out_of_range():
+    L = llgb.lib()
+    for limit in (0, 999, 10_000_000_001):
+        assert L.llgb_wait_selftest(limit, None, None) == llgb.ERR_INVALID_ARG
+    assert L.llgb_wait_selftest(1_000_000, ctypes.c_void_p(12), None) == llgb.ERR_INVALID_ARG
+
+
+def test_batch_arena_rejects_bad_sizes_before_touching_the_device():
+    L = llgb.lib()
+    h = ctypes.c_void_p()
+    for pairs, slots in ((0, 4), (65537, 4), (16, 0), (16, 65)):
+        assert L.llgb_batch_arena_create(pairs, slots, ctypes.byref(h)) == llgb.ERR_INVALID_ARG
+    assert L.llgb_batch_arena_copy(None, 1, None, None, None) == llgb.ERR_INVALID_ARG
+
+
+def test_fma_probe_rejects_bad_arguments_before_launching():
+    L = llgb.lib()
+    fmas = ctypes.c_uint64()
+    assert L.llgb_fma_probe(0, ctypes.c_void_p(256), ctypes.byref(fmas), None) == llgb.ERR_INVALID_ARG
+    assert L.llgb_fma_probe(10, None, ctypes.byref(fmas), None) == llgb.ERR_INVALID_ARG
+
+
+def test_autotune_file_round_trip_and_rejects(tmp_path):
+    L = llgb.lib()
+    llgb.llgb_autotune_clear()
+    good = tmp_path / "tune.json"
+    good.write_text('{"llgb_autotune": 1, "entries": {\n'
+                    '  "w0b2p0:10,10,:x|w0b6p0:10,10,:y|20": [2048, 4, 2, 512, 1, 0, 1],\n'
+                    '  "w0b0p0:2,2,:a|w0b2p0:2,2,:b|12": [640, 2, 3, 256, 2, 2, 0]\n}}\n')
+    llgb.llgb_autotune_load(str(good))
+    out = tmp_path / "again.json"
+    llgb.llgb_autotune_save(str(out))
+    text = out.read_text()
+    assert '"w0b2p0:10,10,:x|w0b6p0:10,10,:y|20": [2048, 4, 2, 512, 1, 0, 1]' in text
+    assert '"w0b0p0:2,2,:a|w0b2p0:2,2,:b|12": [640, 2, 3, 256, 2, 2, 0]' in text
+    for bad in ('{"something": 1}', '{"llgb_autotune": 1, "entries": {"k": [1, 2]}}',
+                '{"llgb_autotune": 1, "entries": {"k": [128, 2, 2, 300, 1, 0, 0]}}',
+                '{"llgb_autotune": 1, "entries": {"k": [128, 2, 2, 256, 1, 0, 9]}}'):
+        p = tmp_path / "bad.json"
+        p.write_text(bad)
+        with pytest.raises(llgb.LlgbError) as err:
+            llgb.llgb_autotune_load(str(p))
+        assert err.value.status == llgb.ERR_INVALID_ARG
+    with pytest.raises(llgb.LlgbError):
+        llgb.llgb_autotune_load(str(tmp_path / "missing.json"))
+    llgb.llgb_autotune_clear()
+    llgb.llgb_autotune_save(str(out))
+    assert '"entries": {\n}}' in out.read_text()

@@ -12,46 +12,18 @@ Sources are drawn by the seeded generators: leaf arrays with the benchmark's
 value distributions, or raw random bytes for whole blobs (so padding and
 NaN/INF codes occur too).
 """
-import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2302_08251_gb300 import llgb, synth
-from gpu_util import empty_device_view, ensure_library, sync_and_check_status
+from gpu_util import check_windows, empty_device_view, ensure_library, sync_and_check_status
 
 pytestmark = pytest.mark.gpu
-
-W = 4096
-
 
 @pytest.fixture(scope="module", autouse=True)
 def lib():
     return ensure_library()
-
-
-def windows(n, seed, count=4):
-    g = synth.rng(seed)
-    starts = {0, (n - W) // 256 * 256}
-    starts.update(int(x) // 256 * 256 for x in g.integers(0, n - W, count))
-    return sorted(starts)
-
-
-def window_of(view, record, mapping, a, w):
-    lo = oracle.blob_sizes(record, mapping, a)
-    hi = oracle.blob_sizes(record, mapping, a + w)
-    return [b[x:y].cpu().numpy() for b, x, y in zip(view.blobs, lo, hi)]
-
-
-def check_windows(src, dst, record, src_map, dst_map, n, seed):
-    for a in windows(n, seed):
-        w = min(W, n - a)
-        src_o = oracle.OracleView(record, src_map, w, blobs=window_of(src, record, src_map, a, w))
-        dst_o = oracle.OracleView(record, dst_map, w)
-        src_o.copy_to(dst_o)
-        got = window_of(dst, record, dst_map, a, w)
-        for k, (g, e) in enumerate(zip(got, dst_o.blobs)):
-            assert np.array_equal(g, e), (src_map, dst_map, a, k)
 
 
 def random_view(record, mapping, extents, seed, **kw):

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2302_08251_gb300 import llgb, serve
-from gpu_util import ensure_library, sync_and_check_status
+from gpu_util import check_windows, ensure_library, sync_and_check_status
 
 pytestmark = pytest.mark.gpu
 
@@ -56,3 +56,40 @@ def test_budget_holds_on_the_device():
     sync_and_check_status()
     assert stats.max_in_flight_bytes <= budget
     assert stats.done + stats.rejected == len(reqs)
+
+
+def test_batches_from_different_ticks_overlap_on_the_device():
+    # requests arrive faster than large copies finish: later ticks launch
+    # their batches while earlier ones still run (no call in the loop
+    # synchronises the device), and every result still equals the oracle's
+    ensure_library()
+    reqs = serve.workload(count=32, rate_hz=100000.0, n_lo=3e6, n_hi=1e7, seed=29)
+    ex = serve.GpuExecutor(streams=4, seed=9, keep=True)
+    srv = serve.Server(ex, budget_bytes=32 * serve.GB, deadline_s=60.0, max_batch=2)
+    stats = srv.run(reqs)
+    sync_and_check_status()
+    assert stats.done == len(reqs) and stats.failed == 0
+    assert stats.max_overlap >= 2, stats.summary()
+    for r in reqs:
+        src, dst = r.result
+        check_windows(src, dst, r.record, r.src_map, r.dst_map, r.n, seed=r.rid)
+
+
+def test_arena_copies_on_several_streams_match_the_oracle():
+    ensure_library()
+    reqs = serve.workload(count=30, rate_hz=1e6, n_lo=1e3, n_hi=1e5, seed=41)
+    ex = serve.GpuExecutor(streams=1, seed=3, keep=True)
+    arena = llgb.Arena(max_pairs=8, slots=3)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    for r in reqs:
+        ex.allocate(r)
+    torch.cuda.synchronize()
+    for k in range(0, len(reqs), 5):     # 6 calls over 3 streams and 3 slots: slots are reused
+        arena.copy([(r.views[0], r.views[1]) for r in reqs[k:k + 5]], stream=streams[(k // 5) % 3])
+    torch.cuda.synchronize()
+    arena.close()
+    sync_and_check_status()
+    for r in reqs:
+        src, dst, _ = r.views
+        for k, (m, e) in enumerate(zip(dst.blob_bytes(), oracle_result(r, src))):
+            assert np.array_equal(m, e), (r.rid, r.src_map, r.dst_map, r.n, k)
