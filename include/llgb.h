@@ -274,7 +274,8 @@ llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst,
  * no memory need be bound, nothing is launched.
  *   kernel_mode, batch_kernel_mode: 0 value loops; 1 value loops with
  *     AoSoA-organised bit leaves in the generic loop; 2 / 4 gather programs
- *     of 2 / 4 source words (a single copy, and the same pair in a batch);
+ *     of 2 / 4 source words (a single copy, and the same pair in a batch or
+ *     an arena copy);
  *   tile_records, tiles: the tiling; items: work items per tile, of which
  *     generic_items convert values record by record (the others run loops
  *     specialised at compile time, or move bytes), and stream_items pack or

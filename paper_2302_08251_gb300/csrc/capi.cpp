@@ -170,7 +170,9 @@ bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config
 //    destination stages of the largest tile that fits (at most 4096
 //    records): per-tile costs are then spread over the most records.
 // Small views keep at least two tiles per CTA.
-llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
+// for_batch: the pair is one entry of a batch, whose other entries keep the
+// SMs busy, so a small view keeps its full-size tile.
+llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out, bool for_batch = false)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
@@ -212,10 +214,12 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
         tile = std::min<uint64_t>(tile, 4096 / q * q);
     }
     if (tile < q) tile = q;
-    const uint64_t n = src->plan.n;
-    const uint64_t want = (n + 2ull * sms * c.ctas_per_sm - 1) / (2ull * sms * c.ctas_per_sm);
-    const uint64_t small = std::max<uint64_t>(q, (want + q - 1) / q * q);
-    tile = std::min(tile, small);
+    if (!for_batch) {
+        const uint64_t n = src->plan.n;
+        const uint64_t want = (n + 2ull * sms * c.ctas_per_sm - 1) / (2ull * sms * c.ctas_per_sm);
+        const uint64_t small = std::max<uint64_t>(q, (want + q - 1) / q * q);
+        tile = std::min(tile, small);
+    }
     for (;;) {
         if (plan_job(src->plan, none_s, dst->plan, none_d, (uint32_t)tile, &probe, &why) != LLGB_OK)
             return fail(LLGB_ERR_UNSUPPORTED, why);
@@ -256,11 +260,16 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
 // repay.
 constexpr uint32_t kFewTiles = 4;
 
-llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads)
+// fit_gather: a job made of byte moves keeps its gather programs by running
+// in CTAs of its own launch shape's thread count (*threads_out), its tile
+// shrunk until those CTAs' programs cover it; otherwise (fit_gather false)
+// its mode is judged for `threads`-thread CTAs as planned.
+llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* job, int* mode, int threads,
+                           bool fit_gather = false, int* threads_out = nullptr)
 {
     llgb_launch_config c{};
     if (!tuned_config(src, dst, &c)) {
-        const llgb_status st = default_config(src, dst, &c);
+        const llgb_status st = default_config(src, dst, &c, fit_gather);
         if (st != LLGB_OK) return st;
     }
     const DeviceInfo dev = device_info();
@@ -275,9 +284,18 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
         if ((job->src.img_bytes <= side_cap && job->dst.img_bytes <= side_cap) || tile <= q) break;
         tile -= q;
     }
+    if (fit_gather && job->gather && job->ntiles > kFewTiles) {
+        threads = c.threads;
+        while (job_mode(*job, threads) == 0 && tile > q) {
+            tile -= q;
+            const llgb_status st = plan_job(src->plan, src->ptrs, dst->plan, dst->ptrs, tile, job, &why);
+            if (st != LLGB_OK) return fail(st, why);
+        }
+    }
     apply_staging(job, c.staging);
     // few-tile jobs take the value loops; run-addressed bit jobs need mode 1 for them
     *mode = job->ntiles <= kFewTiles ? (job->seg ? 1 : 0) : job_mode(*job, threads);
+    if (threads_out) *threads_out = *mode >= 2 ? threads : 0;
     return LLGB_OK;
 }
 
@@ -416,23 +434,55 @@ struct BatchGroup {
     int grid = 0;
     size_t smem = 0;
     std::vector<JobDesc> jobs;
-    std::vector<uint32_t> starts;  // first tile of each job, then the total
+    std::vector<uint32_t> starts;     // first tile of each job, then the total
+    std::vector<uint32_t> cta_tiles;  // first tile of each CTA, then the total
     CopyArgs args;
 };
 
-// Plan every (src[k], dst[k]) pair once and group the jobs by kernel mode;
-// each group gets its launch shape: stages sized for the largest images of
-// the group, two 256-thread CTAs per SM where they fit, else one of 512.
+// Tiles of a group split over its CTAs by bytes rather than by count: a tile
+// weighs its job's source and destination image bytes plus a fixed cost, and
+// CTA b takes the tiles whose weight falls into the b-th equal part.  Jobs of
+// one group differ several-fold in bytes per tile.
+constexpr double kTileFixedBytes = 8192.0;
+
+void balance_ctas(BatchGroup& g)
+{
+    const size_t nj = g.jobs.size();
+    std::vector<double> w(nj);
+    double total = 0.0;
+    for (size_t j = 0; j < nj; ++j) {
+        w[j] = (double)g.jobs[j].src.img_bytes + (double)g.jobs[j].dst.img_bytes + kTileFixedBytes;
+        total += w[j] * (double)g.jobs[j].ntiles;
+    }
+    const uint32_t grid = (uint32_t)g.grid;
+    g.cta_tiles.assign(grid + 1u, 0u);
+    size_t j = 0;
+    double before = 0.0;  // weight of the tiles of jobs 0 .. j-1
+    for (uint32_t b = 1; b < grid; ++b) {
+        const double target = total * (double)b / (double)grid;
+        while (j + 1 < nj && before + w[j] * (double)g.jobs[j].ntiles <= target) {
+            before += w[j] * (double)g.jobs[j].ntiles;
+            ++j;
+        }
+        double into = std::ceil((target - before) / w[j]);
+        if (into < 0.0) into = 0.0;
+        uint32_t t = g.starts[j] + (uint32_t)std::min<double>(into, (double)g.jobs[j].ntiles);
+        g.cta_tiles[b] = std::max(t, g.cta_tiles[b - 1]);
+    }
+    g.cta_tiles[grid] = g.starts[nj];
+}
+
+// Plan every (src[k], dst[k]) pair once and group the jobs by kernel mode
+// and, for gather jobs, the CTA size their programs were sized for.  Each
+// group gets its launch shape: stages sized for the largest images of the
+// group; value groups run two 256-thread CTAs per SM where they fit, else one
+// of 512; 256-thread gather groups two CTAs, 512-thread ones one.
 llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const* dst, std::vector<BatchGroup>* out,
                         uint64_t* bytes, uint64_t* tiles)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
-    BatchGroup groups[4];
-    groups[0].mode = 0;
-    groups[1].mode = 2;
-    groups[2].mode = 4;
-    groups[3].mode = 1;
+    std::vector<BatchGroup> groups;
     *bytes = 0;
     *tiles = 0;
     for (int32_t k = 0; k < n; ++k) {
@@ -440,18 +490,25 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
         if (src[k]->plan.n == 0) continue;
         JobDesc J;
-        int mode = 0;
-        st = plan_batch_job(src[k], dst[k], &J, &mode, 256);
+        int mode = 0, threads = 0;
+        st = plan_batch_job(src[k], dst[k], &J, &mode, 256, true, &threads);
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
-        BatchGroup& g = groups[mode == 0 ? 0 : (mode == 2 ? 1 : (mode == 4 ? 2 : 3))];
-        g.jobs.push_back(J);
+        BatchGroup* g = nullptr;
+        for (BatchGroup& x : groups)
+            if (x.mode == mode && (mode < 2 || x.threads == threads)) g = &x;
+        if (!g) {
+            groups.emplace_back();
+            g = &groups.back();
+            g->mode = mode;
+            g->threads = mode >= 2 ? threads : 0;
+        }
+        g->jobs.push_back(J);
         for (uint64_t s : src[k]->plan.blob_sizes) *bytes += s;
         for (uint64_t s : dst[k]->plan.blob_sizes) *bytes += s;
         *tiles += J.ntiles;
     }
     out->clear();
     for (BatchGroup& g : groups) {
-        if (g.jobs.empty()) continue;
         // tile numbers are per group, starting at 0
         uint64_t total = 0;
         uint32_t src_bytes = 0, dst_bytes = 0;
@@ -464,8 +521,9 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
         }
         if (total > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
         g.starts.push_back((uint32_t)total);
-        int ctas = 2;
-        uint16_t ns = g.mode >= 2 ? 4 : 2, nd = g.mode >= 2 ? 3 : 2;
+        const bool wide_gather = g.mode >= 2 && g.threads == 512;
+        int ctas = wide_gather ? 1 : 2;
+        uint16_t ns = g.mode >= 2 ? 4 : 2, nd = g.mode >= 2 ? (wide_gather ? 2 : 3) : 2;
         auto need = [&]() {
             return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
         };
@@ -475,7 +533,8 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
             else ctas = 1;
         }
         if (!smem_fits(need(), 1)) return fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
-        g.threads = ctas == 1 ? 512 : 256;  // one CTA per SM: a full-size one
+        if (g.mode < 2 || g.threads == 0) g.threads = ctas == 1 ? 512 : 256;  // one CTA per SM: a full-size one
+        // a 256-thread gather group that fell to one CTA per SM keeps its 256 threads (its programs' size)
         g.smem = need();
         g.grid = (int)std::min<uint64_t>(total, (uint64_t)sms * ctas);
         memset(&g.args, 0, sizeof g.args);
@@ -487,6 +546,7 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
         g.args.src_stages = ns;
         g.args.dst_stages = nd;
         g.args.chunk = (uint32_t)((total + g.grid - 1) / g.grid);
+        balance_ctas(g);
         out->push_back(std::move(g));
     }
     return LLGB_OK;
@@ -512,6 +572,8 @@ struct llgb_batch {
     uint64_t tiles = 0;
     int device = 0;
     cudaStream_t capture = nullptr;
+    std::vector<cudaStream_t> branches;  // one per group after the first, while capturing
+    std::vector<cudaEvent_t> joins;      // fork / join events of the capture
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
@@ -524,6 +586,8 @@ struct llgb_batch {
         }
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t e : joins) cudaEventDestroy(e);
+        for (cudaStream_t st : branches) cudaStreamDestroy(st);
         if (capture) cudaStreamDestroy(capture);
         for (void* p : device_tables)
             if (p) cudaFree(p);
@@ -561,14 +625,17 @@ struct llgb_batch_arena {
 
 namespace {
 
-// Groups of at most 4 kernel modes: a slot holds max_pairs jobs, then the
-// tile starts of every group (max_pairs + 4 entries).
-constexpr int kArenaGroups = 4;
+// Groups of at most 4 kernel modes, gather modes in two CTA sizes: a slot
+// holds max_pairs jobs, then the tile starts of every group (max_pairs + 6
+// entries).
+constexpr int kArenaGroups = 6;
 
-size_t arena_slot_bytes(int32_t max_pairs)
+// ... and the CTA ranges of every group (at most 2 CTAs per SM, plus one).
+size_t arena_slot_bytes(int32_t max_pairs, int sms)
 {
     const size_t starts = ((size_t)max_pairs + kArenaGroups) * sizeof(uint32_t);
-    return ((size_t)max_pairs * sizeof(JobDesc) + starts + 255) / 256 * 256;
+    const size_t ctas = (size_t)kArenaGroups * (2 * (size_t)sms + 1) * sizeof(uint32_t);
+    return ((size_t)max_pairs * sizeof(JobDesc) + starts + ctas + 255) / 256 * 256;
 }
 
 llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch* b)
@@ -578,18 +645,22 @@ llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const
     if (st != LLGB_OK) return st;
     for (BatchGroup& g : b->groups) {
         const size_t table_bytes = g.jobs.size() * sizeof(JobDesc);
+        const size_t starts_bytes = g.starts.size() * sizeof(uint32_t);
+        const size_t cta_bytes = g.cta_tiles.size() * sizeof(uint32_t);
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, table_bytes + g.starts.size() * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&p, table_bytes + starts_bytes + cta_bytes);
         if (e == cudaSuccess) b->device_tables.push_back(p);
-        if (e == cudaSuccess) e = cudaMemcpy(p, g.jobs.data(), table_bytes, cudaMemcpyHostToDevice);
+        uint8_t* d = static_cast<uint8_t*>(p);
+        if (e == cudaSuccess) e = cudaMemcpy(d, g.jobs.data(), table_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d + table_bytes, g.starts.data(), starts_bytes, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(static_cast<uint8_t*>(p) + table_bytes, g.starts.data(), g.starts.size() * sizeof(uint32_t),
-                           cudaMemcpyHostToDevice);
+            e = cudaMemcpy(d + table_bytes + starts_bytes, g.cta_tiles.data(), cta_bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess)
             return e == cudaErrorMemoryAllocation ? fail(LLGB_ERR_OOM, "batch descriptor table")
                                                   : cuda_fail(e, "batch descriptor table");
-        g.args.table = static_cast<const JobDesc*>(p);
-        g.args.tile_start = reinterpret_cast<const uint32_t*>(static_cast<uint8_t*>(p) + table_bytes);
+        g.args.table = reinterpret_cast<const JobDesc*>(d);
+        g.args.tile_start = reinterpret_cast<const uint32_t*>(d + table_bytes);
+        g.args.cta_tiles = reinterpret_cast<const uint32_t*>(d + table_bytes + starts_bytes);
     }
     return LLGB_OK;
 }
@@ -763,8 +834,8 @@ llgb_status llgb_copy_plan(const llgb_view* src, const llgb_view* dst, const llg
             if (J.items[k].op == ITEM_VALUE && J.items[k].fast == FK_GENERIC) ++out->generic_items;
             if (J.items[k].spec) ++out->stream_items;
         }
-        int bmode = 0;
-        st = plan_batch_job(src, dst, &J, &bmode, 256);
+        int bmode = 0, bthreads = 0;
+        st = plan_batch_job(src, dst, &J, &bmode, 256, true, &bthreads);
         if (st != LLGB_OK) return st;
         out->batch_kernel_mode = bmode;
         return LLGB_OK;
@@ -997,9 +1068,39 @@ llgb_status llgb_batch_launch(llgb_batch* b, void* stream, int32_t use_graph)
                 if ((e = prepare_copy(g.mode, g.smem)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
             if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
                 return cuda_fail(e, "capture stream");
+            // the groups touch disjoint views: each becomes its own branch of
+            // the graph (forked from and joined back into the capture stream),
+            // so one group's last CTAs overlap the next group's first
+            const size_t ng = b->groups.size();
+            for (size_t k = 1; k < ng; ++k) {
+                cudaStream_t br = nullptr;
+                cudaEvent_t fork = nullptr, join = nullptr;
+                if ((e = cudaStreamCreateWithFlags(&br, cudaStreamNonBlocking)) == cudaSuccess) b->branches.push_back(br);
+                if (e == cudaSuccess && (e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) == cudaSuccess)
+                    b->joins.push_back(fork);
+                if (e == cudaSuccess && (e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) == cudaSuccess)
+                    b->joins.push_back(join);
+                if (e != cudaSuccess) return cuda_fail(e, "graph branches");
+            }
             if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(e, "begin capture");
-            const llgb_status st = batch_enqueue(b, b->capture);
+            llgb_status st = LLGB_OK;
+            for (size_t k = 1; k < ng && st == LLGB_OK && e == cudaSuccess; ++k) {
+                e = cudaEventRecord(b->joins[2 * (k - 1)], b->capture);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(b->branches[k - 1], b->joins[2 * (k - 1)], 0);
+                if (e == cudaSuccess) {
+                    const BatchGroup& g = b->groups[k];
+                    e = launch_copy(g.args, g.mode, g.grid, g.threads, g.smem, b->branches[k - 1]);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(b->joins[2 * (k - 1) + 1], b->branches[k - 1]);
+            }
+            if (e == cudaSuccess && ng > 0) {
+                const BatchGroup& g = b->groups[0];
+                e = launch_copy(g.args, g.mode, g.grid, g.threads, g.smem, b->capture);
+            }
+            for (size_t k = 1; k < ng && e == cudaSuccess; ++k)
+                e = cudaStreamWaitEvent(b->capture, b->joins[2 * (k - 1) + 1], 0);
+            if (e != cudaSuccess) st = cuda_fail(e, "batch capture");
             e = cudaStreamEndCapture(b->capture, &b->graph);
             if (st != LLGB_OK) return st;
             if (e != cudaSuccess) return cuda_fail(e, "end capture");
@@ -1030,7 +1131,8 @@ llgb_status llgb_batch_arena_create(int32_t max_pairs, int32_t slots, llgb_batch
         auto* a = new llgb_batch_arena;
         a->max_pairs = max_pairs;
         a->nslots = slots;
-        a->slot_bytes = arena_slot_bytes(max_pairs);
+        const DeviceInfo dev = device_info();
+        a->slot_bytes = arena_slot_bytes(max_pairs, dev.sms > 0 ? dev.sms : 152);
         cudaGetDevice(&a->device);
         cudaError_t e = cudaMalloc(&a->d_mem, a->slot_bytes * (size_t)slots);
         if (e == cudaSuccess) e = cudaMallocHost(&a->h_mem, a->slot_bytes * (size_t)slots);
@@ -1082,6 +1184,13 @@ llgb_status llgb_batch_arena_copy(llgb_batch_arena* a, int32_t n, const llgb_vie
             memcpy(h + at, g.starts.data(), g.starts.size() * sizeof(uint32_t));
             g.args.tile_start = reinterpret_cast<const uint32_t*>(d + at);
             at += g.starts.size() * sizeof(uint32_t);
+        }
+        for (BatchGroup& g : a->groups) {
+            if (at + g.cta_tiles.size() * sizeof(uint32_t) > a->slot_bytes)
+                return fail(LLGB_ERR_UNSUPPORTED, "arena slot too small for the CTA ranges");
+            memcpy(h + at, g.cta_tiles.data(), g.cta_tiles.size() * sizeof(uint32_t));
+            g.args.cta_tiles = reinterpret_cast<const uint32_t*>(d + at);
+            at += g.cta_tiles.size() * sizeof(uint32_t);
         }
         const cudaStream_t s = static_cast<cudaStream_t>(stream);
         if ((e = cudaMemcpyAsync(d, h, at, cudaMemcpyHostToDevice, s)) != cudaSuccess)

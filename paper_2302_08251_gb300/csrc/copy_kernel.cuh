@@ -1146,32 +1146,56 @@ __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc&
     }
 }
 
-// The tile's work is nitems x (tile / 128) quads, laid out item by item, cut
-// into cnum/32 equal contiguous shares (sizes differ by one quad at most);
-// consumer warp w takes share w of every tile of a job.
+// The tile's work is nitems x (tile / 128) quads, laid out item by item; a
+// quad of item i costs ItemDesc::weight units (an item of 8-byte elements
+// about twice one of 4-byte elements).  The weighted quads are cut into
+// cnum/32 equal contiguous shares; consumer warp w takes share w of every tile
+// of a job: quads [quad, Q) of `item`, the whole items after it, and quads
+// [0, end_quad) of end_item.
 struct ItemShare {
-    uint32_t item, quad, count;  // first item and quad, quads in the share
+    uint32_t item, quad, end_item, end_quad;
 };
+
+// The (item, quad) at which weighted position p falls: the first quad whose
+// weighted start is at or past p.
+__device__ __forceinline__ void weighted_quad(const JobDesc& J, uint32_t Q, uint32_t p, uint32_t& item, uint32_t& quad)
+{
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < J.nitems; ++i) {
+        const uint32_t w = J.items[i].weight;
+        const uint32_t span = w * Q;
+        if (p < acc + span) {
+            const uint32_t q = (p - acc + w - 1u) / w;
+            item = q < Q ? i : i + 1u;
+            quad = q < Q ? q : 0u;
+            return;
+        }
+        acc += span;
+    }
+    item = J.nitems;
+    quad = 0u;
+}
 
 __device__ __forceinline__ ItemShare item_share(const JobDesc& J)
 {
     const uint32_t w = ctid() >> 5, nw = cnum() >> 5;
     const uint32_t Q = J.tile >> 7;
-    const uint32_t total = (uint32_t)J.nitems * Q;  // <= 64 items x 2^10 quads
-    const uint32_t lo = total * w / nw, hi = total * (w + 1u) / nw;
-    const uint32_t it = Q ? lo / Q : 0u;
-    return ItemShare{it, lo - it * Q, hi - lo};
+    uint32_t total = 0;  // <= 64 items x 8 x 2^10 quads
+    for (uint32_t i = 0; i < J.nitems; ++i) total += J.items[i].weight * Q;
+    ItemShare S;
+    weighted_quad(J, Q, total * w / nw, S.item, S.quad);
+    weighted_quad(J, Q, total * (w + 1u) / nw, S.end_item, S.end_quad);
+    return S;
 }
 
 template <bool SEGOK>
 __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid, ItemShare S)
 {
     const uint32_t Q = J.tile >> 7;
-    uint32_t it = S.item, q0 = S.quad, left = S.count;
-    while (left) {
-        const uint32_t q1 = min(Q, q0 + left);
-        run_item_quads<SEGOK>(J, J.items[it], simg, dimg, q0, q1, nvalid);
-        left -= q1 - q0;
+    uint32_t it = S.item, q0 = S.quad;
+    while (it < S.end_item || (it == S.end_item && q0 < S.end_quad)) {
+        const uint32_t q1 = it == S.end_item ? S.end_quad : Q;
+        if (q1 > q0) run_item_quads<SEGOK>(J, J.items[it], simg, dimg, q0, q1, nvalid);
         ++it;
         q0 = 0;
     }
@@ -1387,7 +1411,7 @@ static __device__ void plain_copy(uint8_t* dst, const uint8_t* src, uint32_t byt
 // Global tile index of this CTA's k-th tile (see CopyArgs::chunk).
 __device__ __forceinline__ uint32_t tile_index(const CopyArgs& a, uint32_t first, uint32_t k)
 {
-    return a.chunk ? first * a.chunk + k : first + k * gridDim.x;
+    return (a.chunk || a.cta_tiles) ? first + k : first + k * gridDim.x;
 }
 
 __device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g)
@@ -1621,7 +1645,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     int cur_job = -1;
     uint32_t s = 0, d = 0;     // stages of tile k: k % NS, k % ND
     uint32_t dround = 0;       // parity of k / ND
-    ItemShare share{0u, 0u, 0u};
+    ItemShare share{0u, 0u, 0u, 0u};
 
     for (uint32_t k = 0; k < count; ++k) {
         const uint32_t g = tile_index(a, first, k);
@@ -1736,14 +1760,20 @@ __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ Co
     uint8_t* codes = dst_stage + a.dst_stages * a.dst_stage_bytes;
 
     const uint32_t G = gridDim.x;
-    const uint32_t first = blockIdx.x;
-    uint32_t count;
-    if (a.chunk) {
-        const uint64_t begin = (uint64_t)first * a.chunk;
+    uint32_t first, count;  // this CTA's tiles: first + k (contiguous) or first + k * grid
+    if (a.cta_tiles) {
+        first = a.cta_tiles[blockIdx.x];
+        const uint32_t end = a.cta_tiles[blockIdx.x + 1];
+        if (first >= end) return;
+        count = end - first;
+    } else if (a.chunk) {
+        const uint64_t begin = (uint64_t)blockIdx.x * a.chunk;
         if (begin >= a.total_tiles) return;
         const uint64_t left = a.total_tiles - begin;
+        first = (uint32_t)begin;
         count = left < a.chunk ? (uint32_t)left : a.chunk;
     } else {
+        first = blockIdx.x;
         if (first >= a.total_tiles) return;
         count = (a.total_tiles - first + G - 1u) / G;
     }

@@ -85,6 +85,7 @@ struct ItemDesc {
     uint8_t vpl;         // specialised loop: consecutive records per lane (1, 2, 4)
     uint8_t runs;        // specialised loop: a bit leaf of the item is AoSoA-organised
     uint8_t spec;        // id of the item's compile-time stream format (stream_specs.h), 0 if none
+    uint8_t weight;      // relative cost of a quad (128 records) of the item, 1..8: warps share tiles by it
 };
 
 // Specialised VALUE loops (element sizes and conversion fixed at compile time).
@@ -198,6 +199,7 @@ struct CopyArgs {
     uint16_t src_stages;
     uint16_t dst_stages;
     uint32_t chunk;              // 0: CTA b takes tiles b, b + grid, ...; else tiles [b*chunk, (b+1)*chunk)
+    const uint32_t* cta_tiles;   // if set (grid + 1 entries): CTA b takes tiles [cta_tiles[b], cta_tiles[b+1])
 };
 
 }  // namespace llgb

@@ -21,8 +21,9 @@
 // access.
 // Records at or past the tile's valid count are taken as zero (and so written
 // as zero).  Float values whose result is not a normal number of the target
-// (zero aside), and NaN and INF inputs, are redone by fconv_general; the
-// warp votes on whether any lane has one, so the common case pays one vote.
+// -- zeros included -- and NaN and INF inputs are redone by fconv_general;
+// the warp votes on whether any lane has one, so the common case pays one
+// vote.
 #pragma once
 
 #include "stream_specs.h"
@@ -31,13 +32,15 @@ namespace llgb {
 
 // Rounding conversion of a normal number between binary formats (SE, SM) ->
 // (DE, DM), by integer operations on the bit pattern: the magnitude bits
-// (exponent and mantissa) are shifted by SM - DM with rounding to nearest,
-// ties to even (add 2^(k-1) - 1 plus the lowest kept bit, then drop k bits: a
-// carry moves into the exponent, and past the largest exponent it gives the
-// INF code), then the exponent is rebiased by adding a constant.  `bad` is set
-// for inputs this does not cover: source exponents whose target exponent is
-// out of range (subnormal or overflowing results, subnormal inputs, INF, NaN).
-// Zero maps to zero.
+// (exponent and mantissa) are shifted by k = SM - DM with rounding to
+// nearest, ties to even (add 2^(k-1) - 1 plus the lowest kept bit, then drop k
+// bits: a carry moves into the exponent, and past the largest exponent it
+// gives the INF code), and the exponent is rebiased by adding a constant --
+// folded into the rounding constant as (DB - SB) 2^SM before the shift.
+// `bad` is set for inputs this does not cover: source exponents whose target
+// exponent is out of range (zero, subnormal or overflowing results,
+// subnormal inputs, INF, NaN); the range test reads only the exponent field's
+// word.
 template <int SE, int SM, int DE, int DM>
 __device__ __forceinline__ uint64_t conv_fast(uint64_t x, bool& bad)
 {
@@ -46,19 +49,22 @@ __device__ __forceinline__ uint64_t conv_fast(uint64_t x, bool& bad)
     constexpr int E_LO = (SB - DB + 1) > 1 ? (SB - DB + 1) : 1;
     constexpr int E_HI = ((1 << DE) - 2 + SB - DB) < ((1 << SE) - 2) ? ((1 << DE) - 2 + SB - DB) : ((1 << SE) - 2);
     constexpr uint64_t AMASK = (SE + SM >= 64) ? ~0ull : ((1ull << (SE + SM)) - 1ull);
-    constexpr uint64_t REBIAS = (uint64_t)((int64_t)(DB - SB) * (int64_t)(1ll << DM));
-    const uint32_t e = (uint32_t)(x >> SM) & ((1u << SE) - 1u);
     const uint64_t a = x & AMASK;
+    if constexpr (SM >= 32) {  // the exponent field lies in the high word
+        const uint32_t ah = (uint32_t)(a >> 32);
+        bad = ah - ((uint32_t)E_LO << (SM - 32)) >= ((uint32_t)(E_HI - E_LO + 1) << (SM - 32));
+    } else {
+        const uint32_t e = (uint32_t)(a >> SM);
+        bad = e - (uint32_t)E_LO > (uint32_t)(E_HI - E_LO);
+    }
     uint64_t r;
-    if constexpr (K > 0)
-        r = (a + ((1ull << (K - 1)) - 1ull) + ((a >> K) & 1ull)) >> K;
-    else
-        r = a << (-K);
-    r += REBIAS;
-    const bool zero = a == 0ull;
-    bad = !zero && (e - (uint32_t)E_LO) > (uint32_t)(E_HI - E_LO);
-    const uint64_t sign = ((x >> (SE + SM)) & 1ull) << (DE + DM);
-    return sign | (zero ? 0ull : r);
+    if constexpr (K > 0) {
+        constexpr uint64_t C = ((1ull << (K - 1)) - 1ull) + (uint64_t)((int64_t)(DB - SB) * (int64_t)(1ll << SM));
+        r = (a + C + ((a >> K) & 1ull)) >> K;
+    } else {
+        r = (a << (-K)) + (uint64_t)((int64_t)(DB - SB) * (int64_t)(1ll << DM));
+    }
+    return (((x >> (SE + SM)) & 1ull) << (DE + DM)) | r;
 }
 
 // One entry of stream_specs.h: leaf type, code format and loop shape.
@@ -76,6 +82,7 @@ struct StreamSpec {
     static constexpr int ROUNDS = (C + 31) / 32;    // output words per lane per super-group
     static constexpr int B = 4 / V;                 // super-groups per iteration (4 records per lane)
     using Elem = typename std::conditional<SZ == 8, uint64_t, uint32_t>::type;
+    using Code = typename std::conditional<(W > 32), uint64_t, uint32_t>::type;
     static constexpr uint64_t CODE_MASK = W >= 64 ? ~0ull : ((1ull << W) - 1ull);
     static_assert(CC >= 32 && CC <= 64, "merged chunks hold 32 to 64 bits");
 };
@@ -101,6 +108,7 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
     constexpr bool WIDE = CC > 32;              // merged chunks have a high word
     constexpr bool NEXT = (CC % 32) != 0;       // a word can reach into the next merged chunk
     using Elem = typename S::Elem;
+    using Code = typename S::Code;
     using Chunk = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
     const uint32_t lane = threadIdx.x & 31u;
     const LaneRun RA = affine_run<V, S::SZ>(J.src.leaves[I.src_leaf], lane);
@@ -143,29 +151,32 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
             }
             ld_run<V, S::SZ, Elem>(sa + gg * RA.step, RA, x[b]);
         }
-        uint64_t c[B][V];
+        Code c[B][V];
         if constexpr (S::FLOAT) {
-            uint32_t bad = 0;
+            bool any_bad = false;
 #pragma unroll
             for (int b = 0; b < B; ++b)
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     bool bd;
-                    c[b][v] = conv_fast<S::LE, S::LM, S::E, S::M>((uint64_t)x[b][v], bd);
-                    bad |= (uint32_t)bd << (b * V + v);
+                    c[b][v] = (Code)conv_fast<S::LE, S::LM, S::E, S::M>((uint64_t)x[b][v], bd);
+                    any_bad |= bd;
                 }
-            if (__any_sync(0xFFFFFFFFu, bad != 0u)) {
+            if (__any_sync(0xFFFFFFFFu, any_bad)) {
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if ((bad >> (b * V + v)) & 1u) c[b][v] = fconv_general((uint64_t)x[b][v], S::LE, S::LM, S::E, S::M);
+                    for (int v = 0; v < V; ++v) {
+                        bool bd;
+                        conv_fast<S::LE, S::LM, S::E, S::M>((uint64_t)x[b][v], bd);
+                        if (bd) c[b][v] = (Code)fconv_general((uint64_t)x[b][v], S::LE, S::LM, S::E, S::M);
+                    }
             }
         } else {
 #pragma unroll
             for (int b = 0; b < B; ++b)
 #pragma unroll
-                for (int v = 0; v < V; ++v) c[b][v] = (uint64_t)x[b][v] & S::CODE_MASK;
+                for (int v = 0; v < V; ++v) c[b][v] = (Code)((uint64_t)x[b][v] & S::CODE_MASK);
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -235,21 +246,24 @@ __device__ __noinline__ void stream_unpack(const ItemDesc& I, const JobDesc& J, 
         }
         Elem x[B][V];
         if constexpr (S::FLOAT) {
-            uint32_t bad = 0;
+            bool any_bad = false;
 #pragma unroll
             for (int b = 0; b < B; ++b)
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     bool bd;
                     x[b][v] = (Elem)conv_fast<S::E, S::M, S::LE, S::LM>(c[b][v], bd);
-                    bad |= (uint32_t)bd << (b * V + v);
+                    any_bad |= bd;
                 }
-            if (__any_sync(0xFFFFFFFFu, bad != 0u)) {
+            if (__any_sync(0xFFFFFFFFu, any_bad)) {
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if ((bad >> (b * V + v)) & 1u) x[b][v] = (Elem)fconv_general(c[b][v], S::E, S::M, S::LE, S::LM);
+                    for (int v = 0; v < V; ++v) {
+                        bool bd;
+                        conv_fast<S::E, S::M, S::LE, S::LM>(c[b][v], bd);
+                        if (bd) x[b][v] = (Elem)fconv_general(c[b][v], S::E, S::M, S::LE, S::LM);
+                    }
             }
         } else {
             constexpr uint32_t UP = 32u - (uint32_t)W;
