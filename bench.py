@@ -8,18 +8,19 @@ full-size synthetic workload, through the C ABI (``llgb_copy``/``pack``/
       index type, static inner extents:
         AoS -> SoA(mb), SoA(mb) -> AoS, SoA(mb) -> AoSoA32,
         AoSoA32 -> SoA(mb), AoSoA8 -> AoSoA32
-  C1  2^26 INT6 records {a..d: u32, e,f: i32}, b = 12:
-        SoA(mb) -> BitpackIntSoA (pack), BitpackIntSoA -> SoA(mb) (unpack)
+  C1  2^26 INT6 records {a..d: u32, e,f: i32}, b in {1, 3, 7, 12, 17, 31}
+      (values drawn for each b): SoA(mb) -> BitpackIntSoA (pack) and back
   C2  2^25 MIXED_F records {x,y,z: f64, w: f32}, N(0, 1e3):
-        SoA(mb) -> BitpackFloatSoA(E8,M23), its unpack,
-        SoA(mb) -> Bytesplit(SoA), SoA(mb) -> ChangeType(f64->f32, SoA)
+        SoA(mb) -> BitpackFloatSoA(E, M) and back for E in {5, 8, 11},
+        M in {2, 10, 23, 52}; SoA(mb) -> Bytesplit(SoA);
+        SoA(mb) -> ChangeType(f64->f32, SoA)
 
 value = algorithmic bytes (every source blob byte read + every destination
 blob byte written) of the step / device time of the step, in GB/s.  Every
 input is larger than L2, so no flush is needed between steps.  The n-body
 consumer (65,536 particles) is timed in its own loop and reported under
-"nbody"; "sweeps" holds the other bit widths and float formats of the
-bit-packing rows and the small 65,536-particle case (warm and cold L2).
+"nbody"; "sweeps" holds the Split / Null and bit-packed AoSoA rows and the
+small 65,536-particle case (warm and cold L2).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs the whole per-GPU workload on its own GPU (weak
@@ -47,38 +48,45 @@ PROFILE = os.path.join(ROOT, "profiles", "copy_kernel_relayout_suite.md")
 # ------------------------------------------------------------ workload --
 
 def rows_spec(only=None, scale=1):
-    """(name, config, source mapping, destination mapping) of every row.
-    `only` keeps rows whose name contains it; `scale` divides the record
-    counts (for small profiling captures)."""
+    """(name, config, source mapping, destination mapping) of every row: the
+    C3 re-layout pairs; C1 pack and unpack at every width b; C2 pack and
+    unpack in every (E, M) format, Bytesplit and ChangeType.  `only` keeps
+    rows whose name contains it; `scale` divides the record counts (for small
+    profiling captures)."""
     from paper_2302_08251_gb300 import synth
-    c3 = dict(record=synth.CFD, n=512 ** 3 // scale, ext=(512 // scale, 512, 512), itype="u32",
+    c3 = dict(name="C3", record=synth.CFD, n=512 ** 3 // scale, ext=(512 // scale, 512, 512), itype="u32",
               static=(False, True, True), fields="cfd")
-    c1 = dict(record=synth.INT6, n=(1 << 26) // scale, ext=((1 << 26) // scale,), itype="u32",
-              static=None, fields="int6")
-    c2 = dict(record=synth.MIXED_F, n=(1 << 25) // scale, ext=((1 << 25) // scale,), itype="u32",
+    c2 = dict(name="C2", record=synth.MIXED_F, n=(1 << 25) // scale, ext=((1 << 25) // scale,), itype="u32",
               static=None, fields="mixed_f")
     soa = {"kind": "soa_mb"}
     aos = {"kind": "aos"}
     a32 = {"kind": "aosoa", "lanes": 32}
     a8 = {"kind": "aosoa", "lanes": 8}
-    bp12 = {"kind": "bitpack_int", "bits": 12}
-    bf = {"kind": "bitpack_float", "exp": 8, "man": 23}
-    bs = {"kind": "bytesplit", "inner": soa}
-    ct = {"kind": "changetype", "ct": [("f64", "f32")], "inner": soa}
     rows = [
         ("C3 AoS->SoA", c3, aos, soa),
         ("C3 SoA->AoS", c3, soa, aos),
         ("C3 SoA->AoSoA32", c3, soa, a32),
         ("C3 AoSoA32->SoA", c3, a32, soa),
         ("C3 AoSoA8->AoSoA32", c3, a8, a32),
-        ("C1 pack b=12", c1, soa, bp12),
-        ("C1 unpack b=12", c1, bp12, soa),
-        ("C2 pack E8M23", c2, soa, bf),
-        ("C2 unpack E8M23", c2, bf, soa),
-        ("C2 bytesplit", c2, soa, bs),
-        ("C2 changetype f64->f32", c2, soa, ct),
+    ]
+    for b in C1_BITS:
+        # values are drawn in [0, 2^b) and [-2^(b-1), 2^(b-1)): a source per width
+        c1 = dict(name=f"C1b{b}", record=synth.INT6, n=(1 << 26) // scale, ext=((1 << 26) // scale,), itype="u32",
+                  static=None, fields="int6", bits=b)
+        bp = {"kind": "bitpack_int", "bits": b}
+        rows += [(f"C1 pack b={b}", c1, soa, bp), (f"C1 unpack b={b}", c1, bp, soa)]
+    for e, m in C2_FORMATS:
+        bf = {"kind": "bitpack_float", "exp": e, "man": m}
+        rows += [(f"C2 pack E{e}M{m}", c2, soa, bf), (f"C2 unpack E{e}M{m}", c2, bf, soa)]
+    rows += [
+        ("C2 bytesplit", c2, soa, {"kind": "bytesplit", "inner": soa}),
+        ("C2 changetype f64->f32", c2, soa, {"kind": "changetype", "ct": [("f64", "f32")], "inner": soa}),
     ]
     return [r for r in rows if only is None or only in r[0]]
+
+
+C1_BITS = (1, 3, 7, 12, 17, 31)
+C2_FORMATS = tuple((e, m) for e in (5, 8, 11) for m in (2, 10, 23, 52))
 
 
 def key(m):
@@ -95,12 +103,12 @@ class Workload:
         self.records = {}
         cache = {}  # (config name, mapping) -> source view
         for name, cfg, src_map, dst_map in rows_spec(only, scale):
-            cname = name.split()[0]
+            cname = cfg["name"]
             rec = self.records.setdefault(cname, llgb.Record(cfg["record"]))
             kw = dict(index_type=cfg["itype"], static=cfg["static"])
             base_key = (cname, key({"kind": "soa_mb"}))
             if base_key not in cache:
-                fields = synth.device_fields(cfg["fields"], cfg["n"], seed, device=device)
+                fields = synth.device_fields(cfg["fields"], cfg["n"], seed, device=device, bits=cfg.get("bits", 12))
                 blobs = [f.contiguous().view(torch.uint8) for f in fields]
                 cache[base_key] = llgb.View(rec, {"kind": "soa_mb"}, cfg["ext"], blobs=blobs, **kw)
             src_key = (cname, key(src_map))
@@ -282,7 +290,7 @@ def oracle_sample(seconds_budget=12.0, seed=1, threads=None):
         while True:
             rec = cfg["record"]
             if cfg["fields"] == "int6":
-                fields = synth.int6(m, 12, seed)
+                fields = synth.int6(m, cfg.get("bits", 12), seed)
             elif cfg["fields"] == "mixed_f":
                 fields = synth.mixed_f(m, seed)
             else:
@@ -331,8 +339,8 @@ def run_reference(args):
             "ms_per_step": statistics.median(times) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bytes/int/f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": "llama re-layout suite (C1 b=12, C2 E8M23/bytesplit/"
-                                   "changetype, C3 512^3 pairs), bounded sample",
+            "config": {"workload": "llama re-layout suite, 43 rows (C1 all widths, C2 all formats, "
+                                   "bytesplit, changetype, C3 512^3 pairs), bounded sample",
                        "parallelism": "host threads over record ranges"},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
                              "single_thread_value": statistics.median(singles), "sample": sample},
@@ -421,10 +429,11 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bytes/int/f64->f32", "data": "synthetic (seeded), resident in HBM",
-            "config": {"workload": "llama re-layout suite: C3 512^3 CFD AoS<->SoA, SoA<->AoSoA32, "
+            "config": {"workload": "llama re-layout suite, 43 rows: C3 512^3 CFD AoS<->SoA, SoA<->AoSoA32, "
                                    "AoSoA8->AoSoA32 (u32, static inner extents); C1 2^26 INT6 "
-                                   "BitpackInt b=12 pack+unpack; C2 2^25 MIXED_F BitpackFloat "
-                                   "E8M23 pack+unpack, Bytesplit, ChangeType f64->f32",
+                                   "BitpackInt pack+unpack at b=1,3,7,12,17,31; C2 2^25 MIXED_F "
+                                   "BitpackFloat pack+unpack at E=5,8,11 x M=2,10,23,52, Bytesplit, "
+                                   "ChangeType f64->f32",
                        "bytes_per_step": step_bytes, "l2": "inputs > L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -711,12 +720,10 @@ def bitpack_aosoa_rows(device, entry):
 
 
 def sweeps_bench(device):
-    """The configurations the suite's step holds one point of: BitpackInt at
-    b in {1, 3, 7, 12, 17, 31} (2^26 INT6 records), BitpackFloat at the 12
-    (E, M) formats (2^25 MIXED_F records), both from / to SoA multi-blob;
-    copies into and out of Split / Null views (2^26 records); the bit-packed
-    AoSoA organisation against SoA; and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose
-    3.7 MB fit L2: its latency is reported warm and with L2 flushed."""
+    """Rows beyond the configurations' step: copies into and out of Split /
+    Null views (2^26 records); the bit-packed AoSoA organisation against SoA;
+    and the small C0 case (65,536 particles AoS -> SoA multi-blob), whose 3.7 MB
+    fit L2: its latency is reported warm and with L2 flushed."""
     import torch
     from paper_2302_08251_gb300 import llgb, synth
     peaks, _ = measured_peaks()
@@ -727,40 +734,6 @@ def sweeps_bench(device):
     def entry(nbytes, ms):
         g = nbytes / (ms * 1e-3) / 1e9
         return {"ms": round(ms, 4), "GB/s": round(g, 1), "frac": round(g / hbm, 4)}
-
-    n = 1 << 26
-    rec = llgb.Record(synth.INT6)
-    c1 = {}
-    for b in (1, 3, 7, 12, 17, 31):
-        fields = synth.device_fields("int6", n, 11 + b, device=device, bits=b)
-        base = llgb.View(rec, soa, (n,), blobs=[f.view(torch.uint8) for f in fields])
-        packed = llgb.View(rec, {"kind": "bitpack_int", "bits": b}, (n,))
-        plain = llgb.View(rec, soa, (n,))
-        nbytes = (sum(llgb.blob_sizes(rec, soa, (n,))) +
-                  sum(llgb.blob_sizes(rec, {"kind": "bitpack_int", "bits": b}, (n,))))
-        c1[f"b={b}"] = {"pack": entry(nbytes, time_copy(base, packed)), "unpack": entry(nbytes, time_copy(packed, plain))}
-        del fields, base, packed, plain
-        torch.cuda.empty_cache()
-    out["C1 BitpackInt, 2^26 INT6 records, SoA-MB <-> BitpackIntSoA"] = c1
-
-    n = 1 << 25
-    rec = llgb.Record(synth.MIXED_F)
-    fields = synth.device_fields("mixed_f", n, 17, device=device)
-    base = llgb.View(rec, soa, (n,), blobs=[f.contiguous().view(torch.uint8) for f in fields])
-    plain = llgb.View(rec, soa, (n,))
-    c2 = {}
-    for e in (5, 8, 11):
-        for m in (2, 10, 23, 52):
-            mp = {"kind": "bitpack_float", "exp": e, "man": m}
-            packed = llgb.View(rec, mp, (n,))
-            nbytes = sum(llgb.blob_sizes(rec, soa, (n,))) + sum(llgb.blob_sizes(rec, mp, (n,)))
-            c2[f"E{e}M{m}"] = {"pack": entry(nbytes, time_copy(base, packed)),
-                               "unpack": entry(nbytes, time_copy(packed, plain))}
-            del packed
-            torch.cuda.empty_cache()
-    out["C2 BitpackFloat, 2^25 MIXED_F records, SoA-MB <-> BitpackFloatSoA"] = c2
-    del fields, base, plain
-    torch.cuda.empty_cache()
 
     out["F2 Split / Null"] = split_rows(device, entry)
     out["F3 bit-packed AoSoA organisation"] = bitpack_aosoa_rows(device, entry)
@@ -791,31 +764,29 @@ def sweeps_bench(device):
     return out
 
 
-def batched_bench(device, args, target_bytes=24 * (1 << 30)):
-    """Config-4 requests (log-uniform record counts, mixed mapping pairs) in
-    arrival order up to ~24 GB of algorithmic bytes: one launch per view
-    (llgb_copy each) against one batched launch replayed from a CUDA graph,
-    same bytes checked on the device."""
+def batched_bench(device, args, chunk_bytes=24 * (1 << 30)):
+    """All 4,096 config-4 requests (log-uniform record counts, mixed mapping
+    pairs), in arrival order, in chunks of at most ~24 GB of algorithmic
+    bytes: one launch per view (llgb_copy each) against one batched launch
+    replayed from a CUDA graph, with identical bytes checked on the device.
+    Before timing, llgb_autotune tunes each mapping pair once on its largest
+    request; batch entries take those shapes."""
     import torch
     from paper_2302_08251_gb300 import llgb, serve
     reqs = serve.workload(count=4096)
     ex = serve.GpuExecutor(streams=1, seed=11)
-    chosen, total = [], 0
+    chunks, cur, cur_bytes = [], [], 0
     for r in reqs:
         nb = ex.nbytes(r)
-        if total + nb > target_bytes:
-            break
-        chosen.append(r)
-        total += nb
-    pairs, alt = [], []
-    for r in chosen:
-        ex.allocate(r)
-        src, dst, _ = r.views
-        pairs.append((src, dst))
-        alt.append(llgb.View(ex._record(r.record), r.dst_map, (r.n,)))
-    torch.cuda.synchronize()
+        if cur and cur_bytes + nb > chunk_bytes:
+            chunks.append(cur)
+            cur, cur_bytes = [], 0
+        cur.append(r)
+        cur_bytes += nb
+    if cur:
+        chunks.append(cur)
     stream = torch.cuda.current_stream()
-    reps = max(2, min(args.steps, 5))
+    reps = max(2, min(args.steps, 3))
 
     def timed(fn):
         fn()
@@ -828,19 +799,57 @@ def batched_bench(device, args, target_bytes=24 * (1 << 30)):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    def per_view():
-        for (src, _), d in zip(pairs, alt):
-            llgb.llgb_copy(src, d, stream)
-    batch = llgb.Batch(pairs)
-    ms_view = timed(per_view)
-    ms_batch = timed(lambda: batch.launch(stream, use_graph=True))
-    same = all(torch.equal(x, y) for (_, d), a in zip(pairs, alt) for x, y in zip(d.blobs, a.blobs))
-    info = batch.info()
-    batch.close()
-    return {"requests": len(chosen), "bytes": total, "kernel_launches_batched": info["launches"],
-            "per_view": {"ms": round(ms_view, 3), "GB/s": round(total / ms_view / 1e6, 1),
-                         "launches": len(chosen)},
-            "batched_graph": {"ms": round(ms_batch, 3), "GB/s": round(total / ms_batch / 1e6, 1)},
+    # tune each mapping pair once, on its largest request
+    llgb.llgb_autotune_clear()
+    largest = {}
+    for r in reqs:
+        k = (tuple(r.record), json.dumps(r.src_map, sort_keys=True), json.dumps(r.dst_map, sort_keys=True))
+        if k not in largest or r.n > largest[k].n:
+            largest[k] = r
+    tuned = {}
+    for k, r in largest.items():
+        ex.allocate(r)
+        src, dst, _ = r.views
+        cfg = llgb.llgb_autotune(src, dst, stream)
+        tuned[f"{r.record[0][0]}: {r.src_map['kind']} -> {r.dst_map['kind']}"] = dict(cfg, n=r.n)
+        ex.release(r)
+        r.views = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    total_bytes, ms_view, ms_batch, same, launches = 0, 0.0, 0.0, True, 0
+    for chunk in chunks:
+        pairs, alt, nbytes = [], [], 0
+        for r in chunk:
+            ex.allocate(r)
+            src, dst, _ = r.views
+            pairs.append((src, dst))
+            alt.append(llgb.View(ex._record(r.record), r.dst_map, (r.n,)))
+            nbytes += ex.nbytes(r)
+        torch.cuda.synchronize()
+
+        def per_view():
+            for (src, _), d in zip(pairs, alt):
+                llgb.llgb_copy(src, d, stream)
+        batch = llgb.Batch(pairs)
+        ms_view += timed(per_view)
+        ms_batch += timed(lambda: batch.launch(stream, use_graph=True))
+        same = same and all(torch.equal(x, y) for (_, d), a in zip(pairs, alt) for x, y in zip(d.blobs, a.blobs))
+        launches = max(launches, batch.info()["launches"])
+        batch.close()
+        total_bytes += nbytes
+        del pairs, alt, batch
+        for r in chunk:
+            r.views = None
+        torch.cuda.empty_cache()
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    gbs = total_bytes / ms_batch / 1e6
+    return {"requests": len(reqs), "chunks": len(chunks), "bytes": total_bytes,
+            "kernel_launches_batched_max": launches, "autotuned": tuned,
+            "per_view": {"ms": round(ms_view, 3), "GB/s": round(total_bytes / ms_view / 1e6, 1),
+                         "launches": len(reqs)},
+            "batched_graph": {"ms": round(ms_batch, 3), "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4)},
             "speedup": round(ms_view / ms_batch, 3), "identical_bytes": bool(same)}
 
 

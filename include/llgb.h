@@ -389,8 +389,10 @@ llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const* src, llgb
  * schemes (llgb_staging) of the fastest shape -- keep the fastest for this
  * mapping pair and power-of-two record count, and use it in later llgb_copy,
  * llgb_batch_create, llgb_batch_arena_copy and llgb_batch_copy_noalloc calls
- * of this process.  *best (may be NULL) receives it.  Synchronizes the
- * stream. */
+ * of this process.  A batch entry whose record count has no tuned shape takes
+ * the pair's shape tuned for the largest count (in a batch, other entries
+ * keep the SMs busy, so a small view needs no small tile).  *best (may be
+ * NULL) receives it.  Synchronizes the stream. */
 llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, llgb_launch_config* best);
 
 /* Forget every tuned launch shape. */

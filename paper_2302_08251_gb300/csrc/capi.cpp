@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -152,13 +153,28 @@ std::string tune_key(const llgb_view* src, const llgb_view* dst)
     return src->plan.sig + "|" + dst->plan.sig + "|" + std::to_string(bucket);
 }
 
-bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out)
+// any_bucket: a batch entry, whose batch keeps the SMs busy, takes the pair's
+// shape tuned for its largest record count when its own count has none.
+bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config* out, bool any_bucket = false)
 {
     std::lock_guard<std::mutex> lock(tune_mu);
     auto it = tune_cache.find(tune_key(src, dst));
-    if (it == tune_cache.end()) return false;
-    *out = it->second;
-    return true;
+    if (it != tune_cache.end()) {
+        *out = it->second;
+        return true;
+    }
+    if (!any_bucket) return false;
+    const std::string prefix = src->plan.sig + "|" + dst->plan.sig + "|";
+    int best_bucket = -1;
+    for (const auto& kv : tune_cache) {
+        if (kv.first.compare(0, prefix.size(), prefix) != 0) continue;
+        const int bucket = atoi(kv.first.c_str() + prefix.size());
+        if (bucket > best_bucket) {
+            best_bucket = bucket;
+            *out = kv.second;
+        }
+    }
+    return best_bucket >= 0;
 }
 
 // Default launch shape (from launch-shape sweeps on GB300).
@@ -259,6 +275,12 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
 // CTA that meets a gather job builds its program, which short jobs do not
 // repay.
 constexpr uint32_t kFewTiles = 4;
+// In a batch a gather job shares its CTAs' time with other jobs, and every
+// CTA that meets it builds its programs again: jobs of at most this many
+// tiles move their bytes in the value loops instead, and a gather group runs
+// at most one CTA per kGatherTilesPerCta of its tiles.
+constexpr uint32_t kFewGatherTiles = 16;
+constexpr uint64_t kGatherTilesPerCta = 8;
 
 // fit_gather: a job made of byte moves keeps its gather programs by running
 // in CTAs of its own launch shape's thread count (*threads_out), its tile
@@ -268,7 +290,7 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
                            bool fit_gather = false, int* threads_out = nullptr)
 {
     llgb_launch_config c{};
-    if (!tuned_config(src, dst, &c)) {
+    if (!tuned_config(src, dst, &c, fit_gather)) {
         const llgb_status st = default_config(src, dst, &c, fit_gather);
         if (st != LLGB_OK) return st;
     }
@@ -294,7 +316,8 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
     }
     apply_staging(job, c.staging);
     // few-tile jobs take the value loops; run-addressed bit jobs need mode 1 for them
-    *mode = job->ntiles <= kFewTiles ? (job->seg ? 1 : 0) : job_mode(*job, threads);
+    const uint32_t few = fit_gather && job->gather ? kFewGatherTiles : kFewTiles;
+    *mode = job->ntiles <= few ? (job->seg ? 1 : 0) : job_mode(*job, threads);
     if (threads_out) *threads_out = *mode >= 2 ? threads : 0;
     return LLGB_OK;
 }
@@ -537,6 +560,8 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
         // a 256-thread gather group that fell to one CTA per SM keeps its 256 threads (its programs' size)
         g.smem = need();
         g.grid = (int)std::min<uint64_t>(total, (uint64_t)sms * ctas);
+        if (g.mode >= 2)
+            g.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.grid, total / kGatherTilesPerCta));
         memset(&g.args, 0, sizeof g.args);
         g.args.njobs = (uint32_t)g.jobs.size();
         g.args.total_tiles = (uint32_t)total;

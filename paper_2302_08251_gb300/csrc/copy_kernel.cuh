@@ -1414,15 +1414,39 @@ __device__ __forceinline__ uint32_t tile_index(const CopyArgs& a, uint32_t first
     return (a.chunk || a.cta_tiles) ? first + k : first + k * gridDim.x;
 }
 
-__device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g)
+// The job of global tile g, for a role that walks its tiles in order: tiles
+// [start, next) belong to `job`; a CTA's tiles are contiguous in batches, so
+// a step past `next` is almost always into the next job (one load), and only
+// the first tile (or a step back) searches the table.
+struct JobCursor {
+    uint32_t job = 0, start = 1, next = 0;  // empty until the first lookup
+};
+
+__device__ __forceinline__ uint32_t job_of(const CopyArgs& a, uint32_t g, JobCursor& c)
 {
-    if (a.table == nullptr) return 0;
+    if (a.table == nullptr) {
+        c.start = 0;
+        return 0;
+    }
+    if (g >= c.start && g < c.next) return c.job;
+    if (c.start <= c.next && g >= c.next && c.job + 1u < a.njobs) {
+        const uint32_t after = a.tile_start[c.job + 2u];
+        if (g < after) {
+            c.job += 1u;
+            c.start = c.next;
+            c.next = after;
+            return c.job;
+        }
+    }
     uint32_t lo = 0, hi = a.njobs;  // tile_start[lo] <= g < tile_start[hi]
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (a.tile_start[mid] <= g) lo = mid;
         else hi = mid;
     }
+    c.job = lo;
+    c.start = a.tile_start[lo];
+    c.next = a.tile_start[lo + 1u];
     return lo;
 }
 
@@ -1468,11 +1492,12 @@ __device__ __forceinline__ void lane_runs_load(LaneRuns& L, const SideDesc& S, c
 static __device__ void drain_loads(const CopyArgs& a, CopyShared& H, uint32_t first, uint32_t issued)
 {
     const uint32_t NS = a.src_stages;
+    JobCursor jc;
     for (uint32_t k = issued > NS ? issued - NS : 0u; k < issued; ++k) {
         const uint32_t g = tile_index(a, first, k);
-        const uint32_t j = job_of(a, g);
+        const uint32_t j = job_of(a, g, jc);
         const JobDesc* J = a.table ? a.table + j : &a.job;
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t t = g - jc.start;
         if (t < J->nfull && J->src.bulk_ok) (void)mbar_wait_bounded(&H.full[k % NS], (k / NS) & 1u);
     }
 }
@@ -1487,12 +1512,13 @@ static __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_s
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
     volatile int* abort_flag = &H.abort;
     LaneRuns in, out;
+    JobCursor in_c, out_c;
     uint32_t issued = 0;  // tiles whose loads have been issued: 0 .. issued-1
 
     auto issue_load = [&](uint32_t k) {
         const uint32_t g = tile_index(a, first, k);
-        const uint32_t j = job_of(a, g);
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t j = job_of(a, g, in_c);
+        const uint32_t t = g - in_c.start;
         if ((int)j != in.job) {
             const JobDesc* J = a.table ? a.table + j : &a.job;
             lane_runs_load(in, J->src, J, (int)j, lane);
@@ -1514,8 +1540,8 @@ static __device__ void producer(const CopyArgs& a, CopyShared& H, uint8_t* src_s
             break;
         }
         const uint32_t g = tile_index(a, first, k);
-        const uint32_t j = job_of(a, g);
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t j = job_of(a, g, out_c);
+        const uint32_t t = g - out_c.start;
         if ((int)j != out.job) {
             const JobDesc* J = a.table ? a.table + j : &a.job;
             lane_runs_load(out, J->dst, J, (int)j, lane);
@@ -1551,6 +1577,7 @@ static __device__ void load_producer(const CopyArgs& a, CopyShared& H, uint8_t* 
     const uint32_t NS = a.src_stages;
     volatile int* abort_flag = &H.abort;
     LaneRuns in;
+    JobCursor in_c;
     uint32_t issued = 0;        // tiles whose loads have been issued: 0 .. issued-1
     uint32_t s = 0, round = 0;  // k % NS, (k / NS) & 1
     for (uint32_t k = 0; k < count; ++k) {
@@ -1559,8 +1586,8 @@ static __device__ void load_producer(const CopyArgs& a, CopyShared& H, uint8_t* 
             break;
         }
         const uint32_t g = tile_index(a, first, k);
-        const uint32_t j = job_of(a, g);
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t j = job_of(a, g, in_c);
+        const uint32_t t = g - in_c.start;
         if ((int)j != in.job) {
             const JobDesc* J = a.table ? a.table + j : &a.job;
             lane_runs_load(in, J->src, J, (int)j, lane);
@@ -1591,6 +1618,7 @@ static __device__ void store_producer(const CopyArgs& a, CopyShared& H, uint8_t*
     const uint32_t ND = a.dst_stages;
     volatile int* abort_flag = &H.abort;
     LaneRuns out;
+    JobCursor out_c;
     uint32_t d = 0, round = 0;  // k % ND, (k / ND) & 1
     for (uint32_t k = 0; k < count; ++k) {
         if (!mbar_wait_bounded(&H.dfull[d], round)) {
@@ -1598,8 +1626,8 @@ static __device__ void store_producer(const CopyArgs& a, CopyShared& H, uint8_t*
             break;
         }
         const uint32_t g = tile_index(a, first, k);
-        const uint32_t j = job_of(a, g);
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t j = job_of(a, g, out_c);
+        const uint32_t t = g - out_c.start;
         if ((int)j != out.job) {
             const JobDesc* J = a.table ? a.table + j : &a.job;
             lane_runs_load(out, J->dst, J, (int)j, lane);
@@ -1646,10 +1674,11 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     uint32_t s = 0, d = 0;     // stages of tile k: k % NS, k % ND
     uint32_t dround = 0;       // parity of k / ND
     ItemShare share{0u, 0u, 0u, 0u};
+    JobCursor jc;
 
     for (uint32_t k = 0; k < count; ++k) {
         const uint32_t g = tile_index(a, first, k);
-        const uint32_t j = job_of(a, g);
+        const uint32_t j = job_of(a, g, jc);
         if ((int)j != cur_job) {
             consumer_sync();
             const uint2* from = reinterpret_cast<const uint2*>(a.table ? a.table + j : &a.job);
@@ -1665,7 +1694,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             }
         }
         const JobDesc& J = H.job;
-        const uint32_t t = g - (a.table ? a.tile_start[j] : 0u);
+        const uint32_t t = g - jc.start;
         const uint32_t nvalid = (t + 1u < J.ntiles) ? J.tile : (uint32_t)(J.n - (uint64_t)t * J.tile);
         uint8_t* simg = src_stage + s * a.src_stage_bytes;
         uint8_t* dimg = dst_stage + d * a.dst_stage_bytes;

@@ -934,7 +934,8 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
     }
     // Relative cost of a quad of each item, by which the consumer warps share
     // a tile.  Loops whose work grows with the element's bytes (Bytesplit's
-    // byte planes, whole-element moves) cost one unit per 4 bytes; the
+    // byte planes, whole-element moves, f64 <-> f32 element conversions) cost
+    // one unit per 4 bytes; the
     // converting loops cost about the same per record whatever the leaf's
     // size (their code stream dominates), one unit; record-by-record loops
     // (generic items, byte moves outside the specialised loops) more.
@@ -945,7 +946,8 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
             w = 6;
         } else if (it.op == ITEM_MOVE && it.fast == FK_GENERIC) {
             w = std::max(2, (int)it.size / std::max(1, (int)it.gran));
-        } else if ((it.fast >= FK_SPLIT2 && it.fast <= FK_JOIN8) || (it.fast >= FK_MOVE1 && it.fast <= FK_MOVE8)) {
+        } else if ((it.fast >= FK_SPLIT2 && it.fast <= FK_JOIN8) || (it.fast >= FK_MOVE1 && it.fast <= FK_MOVE8) ||
+                   it.fast == FK_CT_D_F32 || it.fast == FK_CT_F32_D) {
             w = std::max(1, (int)it.size / 4);
         }
         it.weight = (uint8_t)std::min(8, w);
