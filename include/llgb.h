@@ -273,17 +273,18 @@ llgb_status llgb_copy_config(const llgb_view* src, const llgb_view* dst,
  * zero) and a batch entry would run for this pair, planned on the host only:
  * no memory need be bound, nothing is launched.
  *   kernel_mode, batch_kernel_mode: 0 value loops; 1 value loops with
- *     AoSoA-organised bit leaves in the generic loop; 2 / 4 gather programs
- *     of 2 / 4 source words (a single copy, and the same pair in a batch or
- *     an arena copy);
+ *     AoSoA-organised bit leaves in the generic loop; 3 value loops with
+ *     AoSoA-organised bit leaves in the compile-time stream loops; 2 / 4
+ *     gather programs of 2 / 4 source words (a single copy, and the same pair
+ *     in a batch or an arena copy);
  *   tile_records, tiles: the tiling; items: work items per tile, of which
  *     generic_items convert values record by record (the others run loops
  *     specialised at compile time, or move bytes), and stream_items pack or
  *     unpack a SoA bit stream whose width and float format are compile-time
  *     constants of one of the library's specialised loops (integer widths 1,
  *     3, 7, 12, 17, 31 of 4-byte leaves; f64 and f32 leaves in the (E, M)
- *     formats E in {5, 8, 11}, M in {2, 10, 23, 52}); they run so in kernel
- *     mode 0.
+ *     formats E in {5, 8, 11}, M in {2, 10, 23, 52}), in kernel mode 0 for
+ *     SoA streams and mode 3 for streams organised as AoSoA.
  * All zero for n = 0.  Errors: INVALID_ARG, MISMATCH, UNSUPPORTED. */
 typedef struct llgb_plan_info {
     int32_t kernel_mode;

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libllgb.so")
-SOURCES = ["copy_mode0.cu", "copy_mode1.cu", "copy_gather.cu", "copy.cu", "nbody.cu", "noalloc.cu", "plan.cpp",
-           "capi.cpp"]
+SOURCES = ["copy_mode1.cu", "copy_mode0.cu", "copy_mode3.cu", "copy_gather.cu", "copy.cu", "nbody.cu", "noalloc.cu",
+           "plan.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

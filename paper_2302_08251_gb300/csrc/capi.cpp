@@ -126,7 +126,7 @@ void apply_staging(JobDesc* job, int staging)
 // else the general kernel (0).
 int job_mode(const JobDesc& J, int threads)
 {
-    if (J.seg) return 1;
+    if (J.seg) return J.seg;
     int mode = J.gather;
     if (mode == 0) return 0;
     // words the gather programs cover: every run (interleaved), or the whole
@@ -317,8 +317,8 @@ llgb_status plan_batch_job(const llgb_view* src, const llgb_view* dst, JobDesc* 
     apply_staging(job, c.staging);
     // few-tile jobs take the value loops; run-addressed bit jobs need mode 1 for them
     const uint32_t few = fit_gather && job->gather ? kFewGatherTiles : kFewTiles;
-    *mode = job->ntiles <= few ? (job->seg ? 1 : 0) : job_mode(*job, threads);
-    if (threads_out) *threads_out = *mode >= 2 ? threads : 0;
+    *mode = job->ntiles <= few ? job->seg : job_mode(*job, threads);
+    if (threads_out) *threads_out = gather_mode(*mode) ? threads : 0;
     return LLGB_OK;
 }
 
@@ -334,11 +334,11 @@ llgb_status check_pair(const llgb_view* src, const llgb_view* dst)
 // Kernel mode of a single copy's job under launch shape c on `grid` CTAs.
 int copy_mode(const JobDesc& J, const llgb_launch_config& c, int grid)
 {
-    int mode = c.engine == LLGB_ENGINE_VALUE ? (J.seg ? 1 : 0) : job_mode(J, c.threads);
+    int mode = c.engine == LLGB_ENGINE_VALUE ? J.seg : job_mode(J, c.threads);
     // a gather program is built once per job by every CTA: with at most two
     // tiles per CTA that costs more than it saves, and the value loops
     // (whole-element moves) need no program
-    if (c.engine == LLGB_ENGINE_AUTO && mode >= 2 && J.ntiles <= 2u * (uint32_t)grid) mode = 0;
+    if (c.engine == LLGB_ENGINE_AUTO && gather_mode(mode) && J.ntiles <= 2u * (uint32_t)grid) mode = 0;
     return mode;
 }
 
@@ -518,12 +518,12 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
         if (st != LLGB_OK) return fail(st, "batch entry " + std::to_string(k) + ": " + t_error);
         BatchGroup* g = nullptr;
         for (BatchGroup& x : groups)
-            if (x.mode == mode && (mode < 2 || x.threads == threads)) g = &x;
+            if (x.mode == mode && (!gather_mode(mode) || x.threads == threads)) g = &x;
         if (!g) {
             groups.emplace_back();
             g = &groups.back();
             g->mode = mode;
-            g->threads = mode >= 2 ? threads : 0;
+            g->threads = gather_mode(mode) ? threads : 0;
         }
         g->jobs.push_back(J);
         for (uint64_t s : src[k]->plan.blob_sizes) *bytes += s;
@@ -544,9 +544,10 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
         }
         if (total > 0xFFFFFFFFull) return fail(LLGB_ERR_UNSUPPORTED, "batch has too many tiles");
         g.starts.push_back((uint32_t)total);
-        const bool wide_gather = g.mode >= 2 && g.threads == 512;
+        const bool gather = gather_mode(g.mode);
+        const bool wide_gather = gather && g.threads == 512;
         int ctas = wide_gather ? 1 : 2;
-        uint16_t ns = g.mode >= 2 ? 4 : 2, nd = g.mode >= 2 ? (wide_gather ? 2 : 3) : 2;
+        uint16_t ns = gather ? 4 : 2, nd = gather ? (wide_gather ? 2 : 3) : 2;
         auto need = [&]() {
             return copy_shared_header_bytes() + (size_t)ns * (src_bytes + kStageZeroBytes) + (size_t)nd * dst_bytes;
         };
@@ -556,12 +557,11 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
             else ctas = 1;
         }
         if (!smem_fits(need(), 1)) return fail(LLGB_ERR_UNSUPPORTED, "batch tiles do not fit shared memory");
-        if (g.mode < 2 || g.threads == 0) g.threads = ctas == 1 ? 512 : 256;  // one CTA per SM: a full-size one
+        if (!gather || g.threads == 0) g.threads = ctas == 1 ? 512 : 256;  // one CTA per SM: a full-size one
         // a 256-thread gather group that fell to one CTA per SM keeps its 256 threads (its programs' size)
         g.smem = need();
         g.grid = (int)std::min<uint64_t>(total, (uint64_t)sms * ctas);
-        if (g.mode >= 2)
-            g.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.grid, total / kGatherTilesPerCta));
+        if (gather) g.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.grid, total / kGatherTilesPerCta));
         memset(&g.args, 0, sizeof g.args);
         g.args.njobs = (uint32_t)g.jobs.size();
         g.args.total_tiles = (uint32_t)total;
@@ -650,10 +650,10 @@ struct llgb_batch_arena {
 
 namespace {
 
-// Groups of at most 4 kernel modes, gather modes in two CTA sizes: a slot
-// holds max_pairs jobs, then the tile starts of every group (max_pairs + 6
+// Groups of at most 5 kernel modes, gather modes in two CTA sizes: a slot
+// holds max_pairs jobs, then the tile starts of every group (max_pairs + 7
 // entries).
-constexpr int kArenaGroups = 6;
+constexpr int kArenaGroups = 7;
 
 // ... and the CTA ranges of every group (at most 2 CTAs per SM, plus one).
 size_t arena_slot_bytes(int32_t max_pairs, int sms)
@@ -856,7 +856,7 @@ llgb_status llgb_copy_plan(const llgb_view* src, const llgb_view* dst, const llg
         out->tiles = J.ntiles;
         out->items = J.nitems;
         for (int k = 0; k < J.nitems; ++k) {
-            if (J.items[k].op == ITEM_VALUE && J.items[k].fast == FK_GENERIC) ++out->generic_items;
+            if (J.items[k].op == ITEM_VALUE && J.items[k].fast == FK_GENERIC && !J.items[k].spec) ++out->generic_items;
             if (J.items[k].spec) ++out->stream_items;
         }
         int bmode = 0, bthreads = 0;

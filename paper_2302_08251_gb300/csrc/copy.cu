@@ -2,7 +2,7 @@
 // and the bounded-wait self-test.
 //
 // The kernel itself is in copy_kernel.cuh; each mode is compiled in its own
-// translation unit (copy_mode0.cu, copy_mode1.cu, copy_gather.cu).
+// translation unit (copy_mode0.cu, copy_mode1.cu, copy_mode3.cu, copy_gather.cu).
 #include "copy_kernel.cuh"
 
 namespace llgb {
@@ -14,6 +14,9 @@ cudaError_t status_mode0(unsigned* out, bool reset);
 cudaError_t launch_mode1(const CopyArgs& args, int grid, int threads, size_t smem, cudaStream_t stream);
 cudaError_t prepare_mode1(size_t smem);
 cudaError_t status_mode1(unsigned* out, bool reset);
+cudaError_t launch_mode3(const CopyArgs& args, int grid, int threads, size_t smem, cudaStream_t stream);
+cudaError_t prepare_mode3(size_t smem);
+cudaError_t status_mode3(unsigned* out, bool reset);
 cudaError_t launch_gather(const CopyArgs& args, int mode, int grid, int threads, size_t smem, cudaStream_t stream);
 cudaError_t prepare_gather(int mode, size_t smem);
 cudaError_t status_gather(unsigned* out, bool reset);
@@ -54,6 +57,7 @@ cudaError_t prepare_copy(int mode, size_t smem_bytes)
 {
     switch (mode) {
     case 1: return prepare_mode1(smem_bytes);
+    case 3: return prepare_mode3(smem_bytes);
     case 2:
     case 4: return prepare_gather(mode, smem_bytes);
     default: return prepare_mode0(smem_bytes);
@@ -65,6 +69,7 @@ cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, s
 {
     switch (mode) {
     case 1: return launch_mode1(args, grid, threads, smem_bytes, stream);
+    case 3: return launch_mode3(args, grid, threads, smem_bytes, stream);
     case 2:
     case 4: return launch_gather(args, mode, grid, threads, smem_bytes, stream);
     default: return launch_mode0(args, grid, threads, smem_bytes, stream);
@@ -79,6 +84,7 @@ cudaError_t read_device_status(unsigned* out, bool reset)
     if ((e = unit_status(out, reset)) != cudaSuccess) return e;  // this unit: the self-test
     if ((e = status_mode0(out, reset)) != cudaSuccess) return e;
     if ((e = status_mode1(out, reset)) != cudaSuccess) return e;
+    if ((e = status_mode3(out, reset)) != cudaSuccess) return e;
     return status_gather(out, reset);
 }
 

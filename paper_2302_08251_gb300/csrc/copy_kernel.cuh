@@ -30,8 +30,8 @@
 // status word and returns.
 //
 // Each kernel mode is compiled in a translation unit of its own
-// (copy_mode0.cu, copy_mode1.cu, copy_gather.cu), so that the modes build in
-// parallel; every unit holds its own device status word, and the host reads
+// (copy_mode0.cu, copy_mode1.cu, copy_mode3.cu, copy_gather.cu), so that the
+// modes build in parallel; every unit holds its own device status word, and the host reads
 // them all (copy.cu).
 #pragma once
 
@@ -1115,14 +1115,16 @@ static __device__ __noinline__ void zero_streams(const JobDesc& J, uint8_t* dimg
 }
 
 // Quads [q0, q1) (128 records each) of one item.
-template <bool SEGOK>
+template <int MODE>
 __device__ __forceinline__ void run_item_quads(const JobDesc& J, const ItemDesc& I, const uint8_t* simg,
                                                uint8_t* dimg, uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
+    constexpr bool SEGOK = MODE == 1;  // the generic loop of AoSoA-organised bit leaves
     const Span sp{128u * q0 + (threadIdx.x & 31u), 128u * q1, 32u};
-    // kernel mode 0 holds the loops of the compile-time stream formats
-    if constexpr (!SEGOK) {
-        if (I.spec && run_spec(I, J, simg, dimg, q0, q1, nvalid)) return;
+    // the loops of the compile-time stream formats: SoA streams in kernel
+    // mode 0, any organisation in mode 3 (mode 1 runs them in its other loops)
+    if constexpr (MODE != 1) {
+        if (I.spec && run_spec<MODE == 3>(I, J, simg, dimg, q0, q1, nvalid)) return;
     }
     if (I.op == ITEM_MOVE && I.fast != FK_GENERIC && run_fast(I, J, simg, dimg, q0, q1, nvalid)) return;
     if (I.op == ITEM_MOVE) {
@@ -1188,14 +1190,14 @@ __device__ __forceinline__ ItemShare item_share(const JobDesc& J)
     return S;
 }
 
-template <bool SEGOK>
+template <int MODE>
 __device__ void run_items(const JobDesc& J, const uint8_t* simg, uint8_t* dimg, uint32_t nvalid, ItemShare S)
 {
     const uint32_t Q = J.tile >> 7;
     uint32_t it = S.item, q0 = S.quad;
     while (it < S.end_item || (it == S.end_item && q0 < S.end_quad)) {
         const uint32_t q1 = it == S.end_item ? S.end_quad : Q;
-        if (q1 > q0) run_item_quads<SEGOK>(J, J.items[it], simg, dimg, q0, q1, nvalid);
+        if (q1 > q0) run_item_quads<MODE>(J, J.items[it], simg, dimg, q0, q1, nvalid);
         ++it;
         q0 = 0;
     }
@@ -1666,7 +1668,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     const uint32_t NS = a.src_stages, ND = a.dst_stages;
     const uint32_t zero_word = (a.src_stage_bytes - kStageZeroBytes) / 4u;
     const bool warp_leader = (threadIdx.x & 31u) == 0;
-    GatherProgram<MODE> gp;
+    GatherProgram<gather_mode(MODE) ? MODE : 2> gp;
     uint32_t gather_words = 0;
     uint32_t phase = 0;        // per source stage: parity of the next full phase
     uint32_t zeroed = 0;       // destination stages whose padding bytes are zero (current job)
@@ -1687,8 +1689,9 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
             consumer_sync();
             cur_job = (int)j;
             zeroed = 0;
-            if (MODE <= 1) share = item_share(H.job);
-            if (MODE >= 2) {
+            if constexpr (!gather_mode(MODE)) {
+                share = item_share(H.job);
+            } else {
                 gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
                 build_gather<MODE>(H.job, zero_word, gather_words, gp);
             }
@@ -1726,14 +1729,14 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
         // (A gather program writes every word, zeros included.)  The store
         // of the stage's previous tile has read it (dempty), and that tile's
         // writers all arrived before the store was issued.
-        const bool items_here = MODE <= 1 || t >= J.nfull;
+        const bool items_here = !gather_mode(MODE) || t >= J.nfull;
         if (items_here && !(zeroed & (1u << d))) {
             uint4* z = reinterpret_cast<uint4*>(dimg);
             for (uint32_t w = ctid(); w < a.dst_stage_bytes / 16u; w += cnum()) z[w] = make_uint4(0, 0, 0, 0);
             zeroed |= 1u << d;
             sync_needed = true;
         }
-        if (MODE <= 1 && J.ored) {
+        if (!gather_mode(MODE) && J.ored) {
             zero_streams(J, dimg);
             sync_needed = true;
         }
@@ -1745,7 +1748,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                 for (uint32_t b = ctid(); b < Z.bytes; b += cnum()) p[b] = 0;
             }
         }
-        if (MODE >= 2) {
+        if constexpr (gather_mode(MODE)) {
             if (t < J.nfull) {
                 run_gather<MODE>(gp, simg, dimg, gather_words);
                 zeroed |= 1u << d;
@@ -1753,7 +1756,7 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                 run_moves(J, simg, dimg, nvalid);
             }
         } else {
-            run_items<MODE == 1>(J, simg, dimg, nvalid, share);
+            run_items<MODE>(J, simg, dimg, nvalid, share);
         }
         fence_proxy_async();
         __syncwarp();
@@ -1777,9 +1780,11 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
     }
 }
 
-// MODE 0: general items and packs.  MODE 1: the same, for jobs with bit
-// leaves organised as AoSoA.  MODE 2 / 4: every job is made of byte moves;
-// full tiles run gather programs of that form.
+// MODE 0: general items and packs (compile-time loops of SoA bit streams).
+// MODE 1: the same, for jobs whose bit leaves organised as AoSoA need the
+// generic loop.  MODE 3: the same, with the compile-time loops of bit leaves
+// organised as AoSoA.  MODE 2 / 4: every job is made of byte moves; full tiles
+// run gather programs of that form.
 template <int MODE>
 __global__ void __launch_bounds__(512, 1) copy_kernel(const __grid_constant__ CopyArgs a)
 {

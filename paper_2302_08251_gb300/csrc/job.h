@@ -22,9 +22,14 @@ constexpr int kMaxPacks = 16;   // bit-stream destination leaves
 constexpr int kImageSlack = 16; // bytes after every run in an image
 constexpr int kMaxZeros = 32;   // destination byte ranges owned by no leaf
 constexpr int kStageZeroBytes = 16;  // zero block at the end of every source stage
-// Warps of a CTA that issue its TMA copies: value kernels (mode 0) have a
-// load warp and a store warp; gather kernels one warp for both.
-constexpr unsigned producer_warps(int mode) { return mode <= 1 ? 2u : 1u; }
+// Kernel modes: 0 value loops; 1 value loops with the generic loop of
+// AoSoA-organised bit leaves; 2 / 4 gather programs of 2 / 4 source words;
+// 3 value loops with the compile-time stream loops of AoSoA-organised bit
+// leaves.
+constexpr bool gather_mode(int mode) { return mode == 2 || mode == 4; }
+// Warps of a CTA that issue its TMA copies: value kernels have a load warp
+// and a store warp; gather kernels one warp for both.
+constexpr unsigned producer_warps(int mode) { return gather_mode(mode) ? 1u : 2u; }
 
 // One contiguous run of a tile in a blob.  For tile t it covers
 // [gbase + t * tile_bytes, + tile_bytes) (the last tile: tail_bytes) and
@@ -182,7 +187,7 @@ struct JobDesc {
     uint8_t gather;      // full tiles use gather programs: 0 no, 2 or 4 source words
     uint8_t interleave;  // 4-word gathers: deal destination words round-robin over the runs
     uint8_t ored;        // some PackDesc has `ored` set: zero those streams before every tile
-    uint8_t seg;         // a bit leaf is organised as AoSoA: the job runs in kernel mode 1
+    uint8_t seg;         // kernel mode for AoSoA-organised bit leaves: 1 (generic loop), 3 (compile-time loops), else 0
     uint8_t pad[6];
 };
 

@@ -35,12 +35,14 @@ using namespace llgb;
 namespace {
 
 constexpr int kNoallocPairs = 64;      // most pairs one call accepts
-constexpr int kModes = 4;              // kernel modes: general, 2-word and 4-word gathers, AoSoA bits
+constexpr int kModes = 5;              // kernel modes: general, 2-word and 4-word gathers, AoSoA bits (generic, compile-time)
 constexpr int kMaxDevices = 64;
 constexpr size_t kTableBytes = (size_t)kNoallocPairs * sizeof(JobDesc);
-constexpr size_t kStartsBytes = (size_t)kModes * (kNoallocPairs + 1) * sizeof(uint32_t);
+constexpr int kStartsPerMode = (kNoallocPairs + 1 + 3) / 4 * 4;  // tile starts of one mode, padded to 16 bytes
+constexpr size_t kStartsBytes = (size_t)kModes * kStartsPerMode * sizeof(uint32_t);
 constexpr size_t kScratchBytes = (kTableBytes + kStartsBytes + 255) / 256 * 256;
 static_assert(kTableBytes % 16 == 0 && sizeof(JobDesc) % 8 == 0, "tables are moved in 16-byte words");
+static_assert(kStartsBytes % 16 == 0, "tile starts are moved in 16-byte words");
 
 // The descriptor tables and tile starts of the current call (about 370 KB).
 // Shared by every call on a device; see llgb_batch_copy_noalloc.
@@ -127,7 +129,7 @@ llgb_status scratch_address(void** out)
 // groups back to back, then the tile starts of all groups.
 struct Staging {
     JobDesc jobs[kNoallocPairs];
-    uint32_t starts[kModes][kNoallocPairs + 1];
+    uint32_t starts[kModes][kStartsPerMode];
 };
 static_assert(offsetof(Staging, starts) == kTableBytes, "staging mirrors the scratch array");
 thread_local Staging staging;
@@ -165,7 +167,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
     // Plan every pair and order the jobs by kernel mode.
     int mode_of[kNoallocPairs];
     int order[kNoallocPairs];
-    int count[kModes] = {0, 0, 0, 0};
+    int count[kModes] = {0, 0, 0, 0, 0};
     static thread_local JobDesc planned[kNoallocPairs];
     int njobs = 0;
     for (int32_t k = 0; k < n; ++k) {
@@ -180,12 +182,13 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
         int m = 0;
         st = internal_plan_pair(src[k], dst[k], &planned[njobs], &m, 256);
         if (st != LLGB_OK) return st;
-        mode_of[njobs] = m == 0 ? 0 : (m == 2 ? 1 : (m == 4 ? 2 : 3));
+        mode_of[njobs] = m == 0 ? 0 : (m == 2 ? 1 : (m == 4 ? 2 : (m == 1 ? 3 : 4)));
         ++count[mode_of[njobs]];
         ++njobs;
     }
     if (njobs == 0) return LLGB_OK;
-    int at[kModes] = {0, count[0], count[0] + count[1], count[0] + count[1] + count[2]};
+    int at[kModes] = {0, count[0], count[0] + count[1], count[0] + count[1] + count[2],
+                      count[0] + count[1] + count[2] + count[3]};
     for (int q = 0; q < njobs; ++q) order[at[mode_of[q]]++] = q;
     for (int q = 0; q < njobs; ++q) staging.jobs[q] = planned[order[q]];
 
@@ -232,7 +235,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
         memset(&a, 0, sizeof a);
         a.table = reinterpret_cast<const JobDesc*>(scratch) + first;
         a.tile_start = reinterpret_cast<const uint32_t*>(static_cast<unsigned char*>(scratch) + kTableBytes) +
-                       (size_t)g * (kNoallocPairs + 1);
+                       (size_t)g * kStartsPerMode;
         a.njobs = (uint32_t)count[g];
         a.total_tiles = (uint32_t)total;
         a.src_stage_bytes = src_bytes + kStageZeroBytes;
@@ -252,7 +255,7 @@ extern "C" llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const
     if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     for (int g = 0; g < kModes; ++g) {
         if (launch[g].grid == 0) continue;
-        const int mode = g == 0 ? 0 : (g == 1 ? 2 : (g == 2 ? 4 : 1));
+        const int mode = g == 0 ? 0 : (g == 1 ? 2 : (g == 2 ? 4 : (g == 3 ? 1 : 3)));
         e = launch_copy(launch[g].args, mode, launch[g].grid, launch[g].threads, launch[g].smem, s);
         if (e != cudaSuccess) return internal_fail(LLGB_ERR_CUDA, cudaGetErrorString(e));
     }

@@ -682,9 +682,11 @@ static bool affine_for(const LeafDesc& L, int V)
 }
 
 // Id of the compile-time stream format (stream_specs.h) of a VALUE item that
-// packs a 4- or 8-byte affine leaf into a SoA bit stream, or unpacks one, or
-// 0: the leaf's type and the stream's width (and float format) must match an
-// entry, and the affine leaf must allow the entry's records per lane.
+// packs a 4- or 8-byte affine leaf into a bit stream, or unpacks one, or 0:
+// the leaf's type and the stream's width (and float format) must match an
+// entry, and the affine leaf must allow the entry's records per lane.  The
+// stream may be organised as SoA or as AoSoA (runs of L >= 32 codes, which
+// the kernel-mode-1 loops address).
 static int stream_spec_id(const ItemDesc& it, const LeafDesc& A, const LeafDesc& B)
 {
     const bool pack = it.lop == L_DIRECT && (it.sop == S_BITS_INT || it.sop == S_BITS_FLOAT);
@@ -692,11 +694,12 @@ static int stream_spec_id(const ItemDesc& it, const LeafDesc& A, const LeafDesc&
     if (!pack && !unpack) return 0;
     const LeafDesc& P = pack ? A : B;  // the affine leaf
     const LeafDesc& S = pack ? B : A;  // the bit stream
-    if (P.kind != LEAF_AFFINE || S.kind != LEAF_BITS || S.lanes != 0) return 0;
+    if (P.kind != LEAF_AFFINE || S.kind != LEAF_BITS) return 0;
     const int is_float = (pack ? it.sop == S_BITS_FLOAT : it.lop == L_BITS_FLOAT) ? 1 : 0;
     const int size = it.size;
     for (const StreamSpecInfo& sp : kStreamSpecs) {
         if (sp.is_float != is_float || sp.leaf_bytes != size || sp.bits != (int)S.bits) continue;
+        if (sp.aosoa_only && S.lanes == 0) continue;
         if (is_float) {
             if (it.l_e != (size == 8 ? 11 : 8) || it.l_m != (size == 8 ? 52 : 23)) continue;
             if ((pack ? it.d_e : it.s_e) != sp.exp || (pack ? it.d_m : it.s_m) != sp.man) continue;
@@ -952,20 +955,31 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         }
         it.weight = (uint8_t)std::min(8, w);
     }
-    // A generic item on an AoSoA-organised bit leaf runs in kernel mode 1.
+    // Items on AoSoA-organised bit leaves choose the kernel mode: the generic
+    // loop needs mode 1; the compile-time stream loops of such leaves are in
+    // mode 3 (a job that needs both runs in mode 1, where the stream items take
+    // the loops with run-time widths).
     job->seg = 0;
     for (int k = 0; k < job->nitems; ++k) {
         const ItemDesc& it = job->items[k];
-        if (it.op != ITEM_VALUE || it.fast != FK_GENERIC) continue;
+        if (it.op != ITEM_VALUE) continue;
         const LeafDesc& A = job->src.leaves[it.src_leaf];
         const LeafDesc& B = job->dst.leaves[it.dst_leaf];
-        if ((A.kind == LEAF_BITS && A.lanes) || (B.kind == LEAF_BITS && B.lanes)) job->seg = 1;
+        if (!((A.kind == LEAF_BITS && A.lanes) || (B.kind == LEAF_BITS && B.lanes))) continue;
+        if (it.spec) {
+            if (job->seg == 0) job->seg = 3;
+        } else if (it.fast == FK_GENERIC) {
+            job->seg = 1;
+        }
     }
     for (int k = 0; k < job->nitems; ++k) {
         const ItemDesc& it = job->items[k];
         if (it.op != ITEM_VALUE || (it.sop != S_BITS_INT && it.sop != S_BITS_FLOAT)) continue;
         PackDesc& P = job->packs[pack_of[it.dst_leaf]];
-        P.ored = (it.fast == FK_GENERIC && !P.aligned) ? 1 : 0;
+        // a compile-time stream item stores whole words, except in kernel mode 1,
+        // where it runs the generic loop
+        const bool generic = it.fast == FK_GENERIC && !(it.spec && job->seg != 1);
+        P.ored = (generic && !P.aligned) ? 1 : 0;
         job->ored |= P.ored;
     }
     // Jobs made only of byte moves run full tiles through gather programs:

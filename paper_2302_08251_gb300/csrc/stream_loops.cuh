@@ -100,7 +100,56 @@ constexpr int chunk_read_words()
     return most;
 }
 
-template <class S>
+// Super-group addressing of a bit stream in the RUNS loops, which also take
+// streams organised as AoSoA: blocks of L records, each leaf's L codes one
+// run of L W bits (a whole number of words), runs `bstride` bytes apart.
+// Word k of super-group g's codes (read as one stream of 32 V W bits) lies at
+//   (g >> ksh) * bs + (g & kmask) * step + word_off(k)
+// past the leaf's first run:
+//   SoA (one run):   ksh 31, kmask all ones, step 4 C, word_off(k) = 4 k;
+//   L >= 32 V:       L / (32 V) super-groups per run: ksh = log2 of that,
+//                    bs = bstride, step = 4 C, word_off(k) = 4 k;
+//   L <  32 V:       R = 32 V / L runs per super-group: ksh 0, kmask 0,
+//                    bs = R bstride, step 0, word_off(k) = (k / wpr) bstride
+//                    + 4 (k mod wpr), wpr = L W / 32 words per run.
+struct SgAddr {
+    uint32_t ksh, kmask, bs, step;
+    uint32_t lshift, wpr, bstride;  // L < 32 V: run words and stride
+    bool split;                     // L < 32 V
+};
+
+__device__ __forceinline__ SgAddr sg_addr(const LeafDesc& L, uint32_t V, uint32_t W)
+{
+    SgAddr A{31u, 0xFFFFFFFFu, 0u, 4u * V * W, 0u, 0u, 0u, false};
+    if (L.lanes == 0) return A;
+    const uint32_t vsh = V == 4 ? 2u : (V == 2 ? 1u : 0u);
+    if (L.lshift >= 5u + vsh) {
+        A.ksh = L.lshift - 5u - vsh;
+        A.kmask = (1u << A.ksh) - 1u;
+        A.bs = L.bstride;
+        return A;
+    }
+    A.split = true;
+    A.ksh = 0u;
+    A.kmask = 0u;
+    A.step = 0u;
+    A.bs = (32u * V >> L.lshift) * L.bstride;
+    A.lshift = L.lshift;
+    A.wpr = (L.lanes * W) >> 5;
+    A.bstride = L.bstride;
+    return A;
+}
+
+__device__ __forceinline__ uint32_t sg_base(const SgAddr& A, uint32_t g) { return (g >> A.ksh) * A.bs + (g & A.kmask) * A.step; }
+
+__device__ __forceinline__ uint32_t sg_word_off(const SgAddr& A, uint32_t k)
+{
+    if (!A.split) return 4u * k;
+    const uint32_t run = k / A.wpr;
+    return run * A.bstride + 4u * (k - run * A.wpr);
+}
+
+template <class S, bool RUNS>
 __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
                                          uint32_t g0, uint32_t g1, uint32_t nvalid)
 {
@@ -113,14 +162,17 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
     const uint32_t lane = threadIdx.x & 31u;
     const LaneRun RA = affine_run<V, S::SZ>(J.src.leaves[I.src_leaf], lane);
     const uint32_t sa = smem_addr(simg) + RA.off;
-    const uint32_t da = smem_addr(dimg) + J.dst.leaves[I.dst_leaf].sbase + 4u * lane;
+    const LeafDesc& LB = J.dst.leaves[I.dst_leaf];
+    const uint32_t da = smem_addr(dimg) + LB.sbase + (RUNS ? 0u : 4u * lane);
+    const SgAddr GA = RUNS ? sg_addr(LB, V, W) : SgAddr{};
     // word k = lane + 32 m: merged chunk j0 from bit r on (lane src0), and the
     // next merged chunk (lane src1) from bit 0 on, shifted up by CC - r
-    uint32_t src0[ROUNDS], src1[ROUNDS], sh[ROUNDS], up[ROUNDS];
+    uint32_t src0[ROUNDS], src1[ROUNDS], sh[ROUNDS], up[ROUNDS], koff[ROUNDS];
     bool hisel[ROUNDS], mine[ROUNDS];
 #pragma unroll
     for (int m = 0; m < ROUNDS; ++m) {
         const uint32_t k = lane + 32u * m;
+        koff[m] = RUNS ? sg_word_off(GA, k < (uint32_t)C ? k : 0u) : 128u * m;
         const uint32_t j0 = 32u * k / CC;
         const uint32_t r = 32u * k - j0 * CC;
         src0[m] = (j0 * T) & 31u;
@@ -192,7 +244,7 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
             }
             const uint32_t lo = (uint32_t)ch;
             const uint32_t hi = WIDE ? (uint32_t)((uint64_t)ch >> 32) : 0u;
-            const uint32_t q = da + gg * (uint32_t)(4 * C);
+            const uint32_t q = da + (RUNS ? sg_base(GA, gg) : gg * (uint32_t)(4 * C));
 #pragma unroll
             for (int m = 0; m < ROUNDS; ++m) {
                 const uint32_t a_lo = __shfl_sync(0xFFFFFFFFu, lo, src0[m]);
@@ -200,7 +252,7 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
                 const uint32_t nx = NEXT ? __shfl_sync(0xFFFFFFFFu, lo, src1[m]) : 0u;
                 uint32_t word = __funnelshift_r(hisel[m] ? a_hi : a_lo, hisel[m] ? 0u : a_hi, sh[m]);
                 if (NEXT) word |= shl_c(nx, up[m]);
-                if (mine[m]) sts<4>(q + 128u * m, word);
+                if (mine[m]) sts<4>(q + koff[m], word);
             }
         }
     };
@@ -210,7 +262,7 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
     for (; g < g1; g += B) body(g, std::true_type{});
 }
 
-template <class S>
+template <class S, bool RUNS>
 __device__ __noinline__ void stream_unpack(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
                                            uint32_t g0, uint32_t g1, uint32_t nvalid)
 {
@@ -220,7 +272,17 @@ __device__ __noinline__ void stream_unpack(const ItemDesc& I, const JobDesc& J, 
     using Elem = typename S::Elem;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t bit = lane * (uint32_t)C;
-    const uint32_t sa = smem_addr(simg) + J.src.leaves[I.src_leaf].sbase + 4u * (bit >> 5);
+    const LeafDesc& LA = J.src.leaves[I.src_leaf];
+    const SgAddr GA = RUNS ? sg_addr(LA, V, W) : SgAddr{};
+    // the lane's chunk: its first word, and its bit in that word (a run holds
+    // a whole number of words, so the bit is the same in every organisation)
+    uint32_t woff = 4u * (bit >> 5);
+    if (RUNS && GA.split) {
+        const uint32_t rl = (uint32_t)V * lane;
+        const uint32_t run = rl >> GA.lshift;
+        woff = run * GA.bstride + 4u * (((rl - (run << GA.lshift)) * (uint32_t)W) >> 5);
+    }
+    const uint32_t sa = smem_addr(simg) + LA.sbase + woff;
     const uint32_t sh = bit & 31u;
     const LaneRun RB = affine_run<V, S::SZ>(J.dst.leaves[I.dst_leaf], lane);
     const uint32_t da = smem_addr(dimg) + RB.off;
@@ -236,7 +298,7 @@ __device__ __noinline__ void stream_unpack(const ItemDesc& I, const JobDesc& J, 
                 for (int v = 0; v < V; ++v) c[b][v] = 0;
                 continue;
             }
-            const uint32_t p = sa + (g + b) * (uint32_t)(4 * C);
+            const uint32_t p = sa + (RUNS ? sg_base(GA, g + b) : (g + b) * (uint32_t)(4 * C));
             const uint32_t w0 = (uint32_t)lds<4>(p);
             const uint32_t w1 = NW > 1 ? (uint32_t)lds<4>(p + 4u) : 0u;
             const uint32_t w2 = NW > 2 ? (uint32_t)lds<4>(p + 8u) : 0u;
@@ -296,17 +358,23 @@ __device__ __noinline__ void stream_unpack(const ItemDesc& I, const JobDesc& J, 
 
 // Runs a VALUE item over quads [q0, q1) (128 records each) in the loop of its
 // compile-time format (ItemDesc::spec); false when it has none.
+// RUNS: the loops that also address AoSoA-organised streams (kernel mode 3).
+template <bool RUNS>
 __device__ __forceinline__ bool run_spec(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
                                          uint32_t q0, uint32_t q1, uint32_t nvalid)
 {
     const bool pack = I.sop == S_BITS_INT || I.sop == S_BITS_FLOAT;
     switch (I.spec) {
-#define LLGB_SPEC_CASE(id, fl, sz, e, m, w)                                                                \
+#define LLGB_SPEC_CASE(id, fl, sz, e, m, w, ao)                                                            \
     case id: {                                                                                             \
         using S = StreamSpec<fl, sz, e, m, w>;                                                             \
-        if (pack) stream_pack<S>(I, J, simg, dimg, q0 * (4u / S::V), q1 * (4u / S::V), nvalid);          \
-        else stream_unpack<S>(I, J, simg, dimg, q0 * (4u / S::V), q1 * (4u / S::V), nvalid);             \
-        return true;                                                                                       \
+        if constexpr (ao && !RUNS) {                                                                       \
+            return false;                                                                                  \
+        } else {                                                                                           \
+            if (pack) stream_pack<S, RUNS>(I, J, simg, dimg, q0 * (4u / S::V), q1 * (4u / S::V), nvalid);\
+            else stream_unpack<S, RUNS>(I, J, simg, dimg, q0 * (4u / S::V), q1 * (4u / S::V), nvalid);   \
+            return true;                                                                                   \
+        }                                                                                                  \
     }
         LLGB_STREAM_SPECS(LLGB_SPEC_CASE)
 #undef LLGB_SPEC_CASE

@@ -356,24 +356,34 @@ def test_plan_few_tiles_take_the_value_loops():
     assert p["kernel_mode"] == 0 and p["batch_kernel_mode"] == 0
 
 
-def test_plan_bit_streams_run_specialised_loops_in_mode_0():
-    for m in ({"kind": "bitpack_int", "bits": 12}, {"kind": "bitpack_int", "bits": 12, "lanes": 256}):
+def test_plan_bit_streams_run_specialised_loops():
+    # SoA streams in kernel mode 0; AoSoA-organised ones in mode 3 (its loops
+    # address runs of a block)
+    for m, mode in (({"kind": "bitpack_int", "bits": 12}, 0), ({"kind": "bitpack_int", "bits": 12, "lanes": 256}, 3),
+                    ({"kind": "bitpack_int", "bits": 9}, 0)):
         p = plan_of(synth.INT6, {"kind": "soa_mb"}, m, 1 << 20)
-        assert p["kernel_mode"] == 0 and p["generic_items"] == 0 and p["items"] == 6, m
+        assert p["kernel_mode"] == mode and p["generic_items"] == 0 and p["items"] == 6, m
 
 
 @pytest.mark.parametrize("n", [1, 100, 1 << 20])
-def test_plan_short_bit_runs_take_mode_1_also_in_batches(n):
-    # 32-lane runs hold a quarter of a 128-record super-group: generic loop,
-    # kernel mode 1, however few the tiles
+def test_plan_short_bit_runs_take_modes_3_and_1_also_in_batches(n):
+    # 32-lane runs hold a quarter of a 128-record super-group, however few the
+    # tiles: the compile-time loop of a configured width in kernel mode 3, the
+    # generic loop otherwise in mode 1
     p = plan_of(synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12, "lanes": 32}, n)
-    assert p["kernel_mode"] == 1 and p["batch_kernel_mode"] == 1 and p["generic_items"] == 6
+    assert p["kernel_mode"] == 3 and p["batch_kernel_mode"] == 3
+    assert p["stream_items"] == 6 and p["generic_items"] == 0
+    p = plan_of(synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 11, "lanes": 32}, n)
+    assert p["kernel_mode"] == 1 and p["batch_kernel_mode"] == 1
+    assert p["stream_items"] == 0 and p["generic_items"] == 6
 
 
-def test_plan_engine_value_keeps_run_addressed_jobs_in_mode_1():
+def test_plan_engine_value_keeps_run_addressed_jobs_in_modes_3_and_1():
     cfg = {"tile_records": 1024, "src_stages": 2, "dst_stages": 2, "threads": 512, "ctas_per_sm": 1,
            "engine": "value"}
     p = plan_of(synth.INT6, {"kind": "bitpack_int", "bits": 7, "lanes": 64}, {"kind": "aos"}, 50000, cfg)
+    assert p["kernel_mode"] == 3 and p["tile_records"] == 1024
+    p = plan_of(synth.INT6, {"kind": "bitpack_int", "bits": 6, "lanes": 64}, {"kind": "aos"}, 50000, cfg)
     assert p["kernel_mode"] == 1 and p["tile_records"] == 1024
 
 
@@ -403,10 +413,17 @@ def test_plan_configured_float_formats_run_compile_time_stream_loops(e, m):
 
 
 def test_plan_other_widths_and_organisations_keep_the_run_time_loops():
-    for m in ({"kind": "bitpack_int", "bits": 5}, {"kind": "bitpack_int", "bits": 12, "lanes": 256},
-              {"kind": "bitpack_int", "bits": 12, "field_bits": [12, 12, 12, 12, 12, 9]}):
+    for m in ({"kind": "bitpack_int", "bits": 5}, {"kind": "bitpack_int", "bits": 12, "field_bits": [12, 12, 12, 12, 12, 9]}):
         p = plan_of(synth.INT6, {"kind": "soa_mb"}, m, 1 << 20)
         assert p["stream_items"] == (5 if "field_bits" in m else 0), m
+    # the AoSoA organisation of a configured width takes the compile-time loops of mode 1
+    p = plan_of(synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12, "lanes": 256}, 1 << 20)
+    assert p["stream_items"] == 6 and p["kernel_mode"] == 3
+    # f64 / f32 as E8M23 run the compile-time loops only when organised as AoSoA
+    fmt = {"kind": "bitpack_float", "exp": 8, "man": 23}
+    assert plan_of(synth.MIXED_F, {"kind": "soa_mb"}, fmt, 1 << 20)["stream_items"] == 0
+    p = plan_of(synth.MIXED_F, {"kind": "soa_mb"}, dict(fmt, lanes=32), 1 << 20)
+    assert p["stream_items"] == 4 and p["kernel_mode"] == 3 and p["generic_items"] == 0
     p = plan_of(synth.MIXED_F, {"kind": "soa_mb"}, {"kind": "bitpack_float", "exp": 6, "man": 9}, 1 << 20)
     assert p["stream_items"] == 0 and p["generic_items"] == 0
 

@@ -170,3 +170,37 @@ def test_batched_with_plain_pairs(noalloc):
         assert_same_bytes(d, want, str(m))
     if not noalloc:
         batch.close()
+
+
+# ---- the compile-time stream loops on AoSoA-organised streams (kernel mode 3):
+# every configured width and float format, runs shorter than a super-group
+# (32 lanes), one run per super-group (64 or 128) and several super-groups per
+# run (256); ragged counts over several tiles ----
+
+@pytest.mark.parametrize("lanes", [32, 64, 256])
+@pytest.mark.parametrize("bits", [1, 3, 7, 12, 17, 31])
+def test_configured_integer_widths_in_aosoa_streams(bits, lanes):
+    m = {"kind": "bitpack_int", "bits": bits, "lanes": lanes}
+    n = 70001
+    fields = synth.uniform_fields(synth.INT6, n, bits * 7 + lanes)  # wrap and sign-extend
+    src = oracle_view(synth.INT6, {"kind": "soa_mb"}, fields)
+    packed = oracle.OracleView(synth.INT6, m, n)
+    src.copy_to(packed)
+    for s, d in (({"kind": "soa_mb"}, m), (m, {"kind": "soa_mb"}), (m, {"kind": "aos"})):
+        rec = llgb.Record(synth.INT6)
+        views = [llgb.View(rec, x, (n,)) for x in (s, d)]
+        p = llgb.llgb_copy_plan(*views)
+        assert p["stream_items"] == 6 and p["kernel_mode"] == 3, (s, d)
+        del views
+        run_pair(synth.INT6, fields, s, d)
+
+
+@pytest.mark.parametrize("lanes", [32, 64, 256])
+@pytest.mark.parametrize("em", [(e, m) for e in (5, 8, 11) for m in (2, 10, 23, 52)], ids=lambda x: f"E{x[0]}M{x[1]}")
+def test_configured_float_formats_in_aosoa_streams(em, lanes):
+    m = {"kind": "bitpack_float", "exp": em[0], "man": em[1], "lanes": lanes}
+    n = 40003
+    fields = synth.mixed_f(n, em[0] * 100 + em[1] + lanes)
+    fields[0][:64] = synth.special_f64(64, 3)[:64]  # zeros, subnormals, INF, NaN: the general routine
+    for s, d in (({"kind": "soa_mb"}, m), (m, {"kind": "soa_mb"})):
+        run_pair(synth.MIXED_F, fields, s, d)

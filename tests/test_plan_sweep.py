@@ -117,7 +117,7 @@ def test_random_mapping_pairs_plan_like_the_oracle(seed):
                     for lanes in lane_counts(maps[0]) + lane_counts(maps[1]):
                         assert p["tile_records"] % lanes == 0, (maps, p)
                     assert p["tile_records"] % q == 0 and p["tiles"] * p["tile_records"] >= n > (p["tiles"] - 1) * p["tile_records"]
-                    assert p["kernel_mode"] in (0, 1, 2, 4) and p["batch_kernel_mode"] in (0, 1, 2, 4)
+                    assert p["kernel_mode"] in (0, 1, 2, 3, 4) and p["batch_kernel_mode"] in (0, 1, 2, 3, 4)
                     assert 0 <= p["generic_items"] <= p["items"]
         for h in hs:
             L.llgb_view_destroy(h)

@@ -33,6 +33,10 @@ PAIRS = [
     (synth.MIXED_F, {"kind": "soa_mb"}, {"kind": "bitpack_float", "exp": 8, "man": 23}),
     (synth.MIXED_F, {"kind": "aos"}, {"kind": "changetype", "ct": [("f64", "f32")],
                                       "inner": {"kind": "soa_mb"}}),
+    # bit streams organised as AoSoA: a configured width (kernel mode 3) and
+    # another one (the generic loop, mode 1)
+    (synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 12, "lanes": 32}),
+    (synth.INT6, {"kind": "soa_mb"}, {"kind": "bitpack_int", "bits": 11, "lanes": 32}),
 ]
 
 
