@@ -387,8 +387,11 @@ llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const* src, llgb
 /* Autotuner: time candidate launch shapes of llgb_copy(src, dst) on `stream`
  * (each candidate runs the copy 4 times; dst is written) -- first tile
  * records, stages, threads and CTAs per SM with TMA staging, then the staging
- * schemes (llgb_staging) of the fastest shape -- keep the fastest for this
- * mapping pair and power-of-two record count, and use it in later llgb_copy,
+ * schemes (llgb_staging) of the fastest shape.  The default shape and the
+ * four fastest are timed twice more (best of three); a shape or staging
+ * scheme replaces the default only when it is at least 2% faster, so that
+ * run-to-run noise does not pick a shape.  The result is kept for this
+ * mapping pair and power-of-two record count, and used in later llgb_copy,
  * llgb_batch_create, llgb_batch_arena_copy and llgb_batch_copy_noalloc calls
  * of this process.  A batch entry whose record count has no tuned shape takes
  * the pair's shape tuned for the largest count (in a batch, other entries

@@ -1284,21 +1284,55 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
                         c.dst_stages = nd;
                         cands.push_back(c);
                     }
-        float best_ms = 1e30f;
+        // Timings on a shared memory system vary by a few percent from run to
+        // run: the four fastest shapes and the default are timed twice more
+        // and keep their best time, and a shape replaces the default only when
+        // that is at least kMargin faster.
+        constexpr float kMargin = 0.02f;
+        std::vector<std::pair<float, size_t>> timed;
+        for (size_t i = 0; i < cands.size(); ++i) {
+            const float ms = time_shape(cands[i]);
+            if (ms >= 0.0f) timed.push_back({ms, i});
+        }
+        std::sort(timed.begin(), timed.end());
+        std::vector<size_t> finalists{0};
+        for (size_t i = 0; i < timed.size() && finalists.size() < 5; ++i)
+            if (timed[i].second != 0) finalists.push_back(timed[i].second);
+        auto best_of = [&](const llgb_launch_config& c, float first) {
+            float ms = first;
+            for (int r = 0; r < 2; ++r) {
+                const float t = time_shape(c);
+                if (t >= 0.0f && (ms < 0.0f || t < ms)) ms = t;
+            }
+            return ms;
+        };
+        auto first_time = [&](size_t i) {
+            for (const auto& t : timed)
+                if (t.second == i) return t.first;
+            return -1.0f;
+        };
+        const float base_ms = best_of(base, first_time(0));
+        float best_ms = base_ms >= 0.0f ? base_ms : 1e30f;
         llgb_launch_config winner = base;
-        for (const llgb_launch_config& c : cands) {
-            const float ms = time_shape(c);
+        for (size_t k = 1; k < finalists.size(); ++k) {
+            const float ms = best_of(cands[finalists[k]], first_time(finalists[k]));
             if (ms >= 0.0f && ms < best_ms) {
                 best_ms = ms;
-                winner = c;
+                winner = cands[finalists[k]];
             }
         }
-        // 2. the staging scheme of the winning shape
+        if (base_ms >= 0.0f && best_ms > (1.0f - kMargin) * base_ms) {
+            winner = base;
+            best_ms = base_ms;
+        }
+        // 2. the staging scheme of the winning shape, under the same margin
+        const llgb_launch_config shape = winner;
+        const float shape_ms = best_ms;
         for (int staging : {LLGB_STAGING_PLAIN_STORE, LLGB_STAGING_PLAIN_LOAD, LLGB_STAGING_PLAIN}) {
-            llgb_launch_config c = winner;
+            llgb_launch_config c = shape;
             c.staging = staging;
-            const float ms = time_shape(c);
-            if (ms >= 0.0f && ms < best_ms) {
+            const float ms = best_of(c, time_shape(c));
+            if (ms >= 0.0f && ms < best_ms && ms <= (1.0f - kMargin) * shape_ms) {
                 best_ms = ms;
                 winner = c;
             }
