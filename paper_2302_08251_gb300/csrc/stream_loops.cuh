@@ -48,6 +48,27 @@ __device__ __forceinline__ uint64_t conv_fast(uint64_t x, bool& bad)
     constexpr int K = SM - DM;
     constexpr int E_LO = (SB - DB + 1) > 1 ? (SB - DB + 1) : 1;
     constexpr int E_HI = ((1 << DE) - 2 + SB - DB) < ((1 << SE) - 2) ? ((1 << DE) - 2 + SB - DB) : ((1 << SE) - 2);
+    if constexpr (SE + SM == 63 && K >= 33 && 1 + DE + DM <= 32 && DE <= 12) {
+        // f64 narrowed to at most 19 mantissa bits: exponent and kept bits lie
+        // in the high word, and the low word only tells, as a sticky bit with
+        // the lowest kept bit, whether the dropped bits reach past a tie --
+        // the 64-bit sum's carry out of the low word -- so the rounding runs
+        // on the high word alone
+        const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
+        const uint32_t ah = hi & 0x7FFFFFFFu;
+        bad = ah - ((uint32_t)E_LO << (SM - 32)) >= ((uint32_t)(E_HI - E_LO + 1) << (SM - 32));
+        constexpr uint32_t C32 = (uint32_t)(((1ll << (K - 33)) - 1ll) + (int64_t)(DB - SB) * (1ll << (SM - 32)));
+        const uint32_t carry = (uint32_t)(lo != 0u) | ((ah >> (K - 32)) & 1u);
+        const uint32_t r = (ah + C32 + carry) >> (K - 32);
+        return (uint64_t)(((hi >> 31) << (DE + DM)) | r);
+    } else if constexpr (SE + SM == 31 && K > 0 && DE + SM <= 31) {
+        // f32 narrowed to a format whose rebiased exponent still fits the word
+        const uint32_t x32 = (uint32_t)x, a32 = x32 & 0x7FFFFFFFu;
+        bad = (a32 >> SM) - (uint32_t)E_LO > (uint32_t)(E_HI - E_LO);
+        constexpr uint32_t C32 = (uint32_t)(((1ll << (K - 1)) - 1ll) + (int64_t)(DB - SB) * (1ll << SM));
+        const uint32_t r = (a32 + C32 + ((a32 >> K) & 1u)) >> K;
+        return (uint64_t)(((x32 >> 31) << (DE + DM)) | r);
+    }
     constexpr uint64_t AMASK = (SE + SM >= 64) ? ~0ull : ((1ull << (SE + SM)) - 1ull);
     const uint64_t a = x & AMASK;
     if constexpr (SM >= 32) {  // the exponent field lies in the high word
@@ -86,6 +107,9 @@ struct StreamSpec {
     static constexpr int CC = T * C;                // merged chunk bits (32 .. 64)
     static constexpr int ROUNDS = (C + 31) / 32;    // output words per lane per super-group
     static constexpr int B = 4 / V;                 // super-groups per iteration (4 records per lane)
+    // pack: integer codes of 4-record lanes take two super-groups per
+    // iteration (two independent shuffle chains; measured faster), floats one
+    static constexpr int BP = (V == 4 && !FLOAT) ? 2 : B;
     using Elem = typename std::conditional<SZ == 8, uint64_t, uint32_t>::type;
     using Code = typename std::conditional<(W > 32), uint64_t, uint32_t>::type;
     static constexpr uint64_t CODE_MASK = W >= 64 ? ~0ull : ((1ull << W) - 1ull);
@@ -158,7 +182,7 @@ template <class S, bool RUNS>
 __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
                                          uint32_t g0, uint32_t g1, uint32_t nvalid)
 {
-    constexpr int V = S::V, W = S::W, C = S::C, T = S::T, CC = S::CC, ROUNDS = S::ROUNDS, B = S::B;
+    constexpr int V = S::V, W = S::W, C = S::C, T = S::T, CC = S::CC, ROUNDS = S::ROUNDS, B = S::BP;
     constexpr bool WIDE = CC > 32;              // merged chunks have a high word
     constexpr bool NEXT = (CC % 32) != 0;       // a word can reach into the next merged chunk
     using Elem = typename S::Elem;
@@ -188,15 +212,16 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
         mine[m] = k < (uint32_t)C;
     }
 
-    // SoA streams whose merged chunks are not a whole number of words, when
-    // every lane holds its own chunk (T = 1) or a single record (V = 1): the
-    // lane holding a chunk stores the words whose first bit the chunk covers
-    // (one or two), and, after the warp has stored those, ORs the chunk's
-    // leading bits into the word where the chunk starts -- each word has one
-    // plain writer and at most one OR, and no word needs shuffles.  Where
-    // 2 to 4 lanes of several records merge a chunk, the shuffles are fewer
-    // per record and the assembly below was measured faster.
-    constexpr bool PIECES = !RUNS && NEXT && (T == 1 || V == 1);
+    // Merged chunks that are not a whole number of words, when every lane
+    // holds its own chunk (T = 1) or a single record (V = 1): the lane
+    // holding a chunk stores the words whose first bit the chunk covers (one
+    // or two), and, after the warp has stored those, ORs the chunk's leading
+    // bits into the word where the chunk starts -- each word has one plain
+    // writer and at most one OR, and no word needs shuffles.  Where 2 to 4
+    // lanes of several records merge a chunk, the shuffles are fewer per
+    // record and the assembly below was measured faster.  The three words a
+    // lane touches are lane constants, in either organisation.
+    constexpr bool PIECES = NEXT && (T == 1 || V == 1);
     const bool holder = (lane % (uint32_t)T) == 0u;
     const uint32_t cs = (lane / (uint32_t)T) * (uint32_t)CC;  // the merged chunk's first bit
     const uint32_t ka0 = (cs + 31u) >> 5;                       // its first word with a plain store
@@ -204,6 +229,9 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
     const bool two_a = ((cs + (uint32_t)CC - 1u) >> 5) > ka0;   // a second plain word
     const uint32_t sb = cs & 31u;                               // the chunk's start inside word cs / 32
     const uint32_t pbase = smem_addr(dimg) + LB.sbase;
+    const uint32_t off_a0 = RUNS ? sg_word_off(GA, ka0) : 4u * ka0;
+    const uint32_t off_a1 = RUNS ? sg_word_off(GA, two_a ? ka0 + 1u : ka0) : 4u * ka0 + 4u;
+    const uint32_t off_b = RUNS ? sg_word_off(GA, cs >> 5) : 4u * (cs >> 5);
 
     auto body = [&](uint32_t g, auto check_tag) {
         constexpr bool CHECK = decltype(check_tag)::value;
@@ -267,13 +295,13 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
             const uint32_t lo = (uint32_t)ch;
             const uint32_t hi = WIDE ? (uint32_t)((uint64_t)ch >> 32) : 0u;
             if constexpr (PIECES) {
-                const uint32_t q = pbase + gg * (uint32_t)(4 * C);
+                const uint32_t q = pbase + (RUNS ? sg_base(GA, gg) : gg * (uint32_t)(4 * C));
                 if (holder) {
-                    sts<4>(q + 4u * ka0, __funnelshift_r(lo, hi, a0));
-                    if (two_a) sts<4>(q + 4u * ka0 + 4u, hi >> a0);
+                    sts<4>(q + off_a0, __funnelshift_r(lo, hi, a0));
+                    if (two_a) sts<4>(q + off_a1, hi >> a0);
                 }
                 __syncwarp();
-                if (holder && sb != 0u) red_or_shared_addr(q + 4u * (cs >> 5), lo << sb);
+                if (holder && sb != 0u) red_or_shared_addr(q + off_b, lo << sb);
                 continue;
             }
             const uint32_t q = da + (RUNS ? sg_base(GA, gg) : gg * (uint32_t)(4 * C));
