@@ -88,11 +88,6 @@ __device__ __forceinline__ uint64_t conv_fast(uint64_t x, bool& bad)
     return (((x >> (SE + SM)) & 1ull) << (DE + DM)) | r;
 }
 
-__device__ __forceinline__ void red_or_shared_addr(uint32_t addr, uint32_t v)
-{
-    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
 // One entry of stream_specs.h: leaf type, code format and loop shape.
 template <int FL, int SZ_, int E_, int M_, int W_>
 struct StreamSpec {
@@ -212,26 +207,24 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
         mine[m] = k < (uint32_t)C;
     }
 
-    // Merged chunks that are not a whole number of words, when every lane
-    // holds its own chunk (T = 1) or a single record (V = 1): the lane
-    // holding a chunk stores the words whose first bit the chunk covers (one
-    // or two), and, after the warp has stored those, ORs the chunk's leading
-    // bits into the word where the chunk starts -- each word has one plain
-    // writer and at most one OR, and no word needs shuffles.  Where 2 to 4
-    // lanes of several records merge a chunk, the shuffles are fewer per
-    // record and the assembly below was measured faster.  The three words a
-    // lane touches are lane constants, in either organisation.
-    constexpr bool PIECES = NEXT && (T == 1 || V == 1);
+    // Chunks of one lane (T = 1) that are not a whole number of words: the
+    // lane writes every word whose first bit lies in its chunk -- one, or two
+    // when a second word starts inside -- and the last of them takes its
+    // remaining bits from the low bits of the next lane's chunk, fetched with
+    // one shuffle.  One shuffle per super-group instead of three per output
+    // word, and each word has a single writer.  The words a lane writes are
+    // lane constants, in either organisation.  Where 2 to 4 lanes merge a
+    // chunk, the shuffle assembly below was measured faster.
+    constexpr bool PIECES = NEXT && T == 1;
     const bool holder = (lane % (uint32_t)T) == 0u;
     const uint32_t cs = (lane / (uint32_t)T) * (uint32_t)CC;  // the merged chunk's first bit
-    const uint32_t ka0 = (cs + 31u) >> 5;                       // its first word with a plain store
+    const uint32_t ka0 = (cs + 31u) >> 5;                       // its first word starting inside
     const uint32_t a0 = 32u * ka0 - cs;                         // ... which starts a0 bits into the chunk
-    const bool two_a = ((cs + (uint32_t)CC - 1u) >> 5) > ka0;   // a second plain word
-    const uint32_t sb = cs & 31u;                               // the chunk's start inside word cs / 32
+    const bool two_a = ((cs + (uint32_t)CC - 1u) >> 5) > ka0;   // a second word starts inside
+    const uint32_t up_last = (uint32_t)CC - (two_a ? a0 + 32u : a0);  // the last word's bits from this chunk (1..32)
     const uint32_t pbase = smem_addr(dimg) + LB.sbase;
     const uint32_t off_a0 = RUNS ? sg_word_off(GA, ka0) : 4u * ka0;
-    const uint32_t off_a1 = RUNS ? sg_word_off(GA, two_a ? ka0 + 1u : ka0) : 4u * ka0 + 4u;
-    const uint32_t off_b = RUNS ? sg_word_off(GA, cs >> 5) : 4u * (cs >> 5);
+    const uint32_t off_last = two_a ? (RUNS ? sg_word_off(GA, ka0 + 1u) : 4u * ka0 + 4u) : off_a0;
 
     auto body = [&](uint32_t g, auto check_tag) {
         constexpr bool CHECK = decltype(check_tag)::value;
@@ -295,13 +288,13 @@ __device__ __noinline__ void stream_pack(const ItemDesc& I, const JobDesc& J, co
             const uint32_t lo = (uint32_t)ch;
             const uint32_t hi = WIDE ? (uint32_t)((uint64_t)ch >> 32) : 0u;
             if constexpr (PIECES) {
+                const uint32_t nlo = __shfl_down_sync(0xFFFFFFFFu, lo, T);  // the next chunk's low bits
                 const uint32_t q = pbase + (RUNS ? sg_base(GA, gg) : gg * (uint32_t)(4 * C));
                 if (holder) {
-                    sts<4>(q + off_a0, __funnelshift_r(lo, hi, a0));
-                    if (two_a) sts<4>(q + off_a1, hi >> a0);
+                    const uint32_t first = __funnelshift_r(lo, hi, a0);
+                    if (two_a) sts<4>(q + off_a0, first);
+                    sts<4>(q + off_last, (two_a ? hi >> a0 : first) | shl_c(nlo, up_last));
                 }
-                __syncwarp();
-                if (holder && sb != 0u) red_or_shared_addr(q + off_b, lo << sb);
                 continue;
             }
             const uint32_t q = da + (RUNS ? sg_base(GA, gg) : gg * (uint32_t)(4 * C));
