@@ -177,6 +177,19 @@ bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config
     return best_bucket >= 0;
 }
 
+// A job whose every item packs an integer leaf into a bit stream in a
+// specialised loop: little consumer work per byte read.
+static bool int_pack_job(const JobDesc& J)
+{
+    if (J.nitems == 0) return false;
+    for (int i = 0; i < J.nitems; ++i) {
+        const ItemDesc& it = J.items[i];
+        if (it.op != ITEM_VALUE || it.lop != L_DIRECT || it.sop != S_BITS_INT) return false;
+        if (it.fast == FK_GENERIC && it.spec == 0) return false;
+    }
+    return true;
+}
+
 // Default launch shape (from launch-shape sweeps on GB300).
 //  * Gather jobs (byte permutations) run two 256-thread CTAs per SM on
 //    ~12 KB tiles (a thread's gather program covers at most a fixed number
@@ -185,6 +198,11 @@ bool tuned_config(const llgb_view* src, const llgb_view* dst, llgb_launch_config
 //  * Other jobs run one 512-thread CTA per SM with two source and two
 //    destination stages of the largest tile that fits (at most 4096
 //    records): per-tile costs are then spread over the most records.
+//    Integer-stream packs, whose consumers have little to do per byte
+//    read, run two 256-thread CTAs per SM instead: each has its own load
+//    pipeline, and together they keep more bytes in flight (b = 1 pack
+//    0.80 -> 0.91, b = 12 0.94 -> 0.98 of measured HBM); float packs and
+//    unpacks measured faster with one 512-thread CTA.
 // Small views keep at least two tiles per CTA.
 // for_batch: the pair is one entry of a batch, whose other entries keep the
 // SMs busy, so a small view keeps its full-size tile.
@@ -221,11 +239,12 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
         c.dst_stages = 3;
         tile = (uint64_t)(12288.0 / std::max(std::max(sb, db), 1.0)) / q * q;
     } else {
-        c.threads = 512;
-        c.ctas_per_sm = 1;
+        const bool light = int_pack_job(probe);
+        c.threads = light ? 256 : 512;
+        c.ctas_per_sm = light ? 2 : 1;
         c.src_stages = 2;
         c.dst_stages = 2;
-        const double budget = 227.0 * 1024 - (double)copy_shared_header_bytes() - 64.0;
+        const double budget = 227.0 * 1024 / c.ctas_per_sm - (double)copy_shared_header_bytes() - 64.0;
         tile = (uint64_t)(budget / (2.0 * (std::max(sb, 1.0) + std::max(db, 1.0)))) / q * q;
         tile = std::min<uint64_t>(tile, 4096 / q * q);
     }

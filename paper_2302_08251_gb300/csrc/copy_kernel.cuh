@@ -948,6 +948,52 @@ __device__ __forceinline__ void planes_to_rows(uint32_t (&w)[SZ])
     }
 }
 
+// The quads [g0, g1) of a split or join whose planes are vector runs at one
+// common step (SoA-like planes) and whose records are all valid: one plane
+// address step per quad and no per-plane or per-record checks.  Returns the
+// first quad it left to split_loop (g0 when the planes do not qualify).  A
+// function of its own, so that the general loop's per-plane state does not
+// add to the registers the kernel keeps across the call.
+template <int SZ, bool JOIN>
+__device__ __noinline__ uint32_t split_uni(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
+                                           uint32_t g0, uint32_t g1, uint32_t nvalid)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t sa = smem_addr(simg), da = smem_addr(dimg);
+    const LaneRun RW = affine_run<4, SZ>(JOIN ? J.dst.leaves[I.dst_leaf] : J.src.leaves[I.src_leaf], lane);
+    bool uni = RW.vec;
+    uint32_t pbase[SZ], pstep = 0;
+#pragma unroll
+    for (int j = 0; j < SZ; ++j) {
+        const LaneRun RP = affine_run<4, 1>(JOIN ? J.src.leaves[I.src_leaf + j] : J.dst.leaves[I.dst_leaf + j], lane);
+        if (j == 0) pstep = RP.step;
+        uni = uni && RP.vec && RP.step == pstep;
+        pbase[j] = (JOIN ? sa : da) + RP.off;
+    }
+    if (!uni) return g0;
+    const uint32_t gfull = min(g1, max(g0, nvalid / 128u));
+    uint32_t wa = (JOIN ? da : sa) + RW.off + g0 * RW.step, pa = g0 * pstep;
+    for (uint32_t g = g0; g < gfull; ++g, wa += RW.step, pa += pstep) {
+        uint32_t w[SZ];
+        if (!JOIN) {
+            uint64_t x[4];
+            ld_run<4, SZ, uint64_t>(wa, RW, x);
+            elems_to_words<4, SZ, uint64_t>(x, w);
+            rows_to_planes<SZ>(w);
+#pragma unroll
+            for (int j = 0; j < SZ; ++j) sts<4>(pbase[j] + pa, w[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < SZ; ++j) w[j] = (uint32_t)lds<4>(pbase[j] + pa);
+            planes_to_rows<SZ>(w);
+            uint64_t x[4];
+            words_to_elems<4, SZ, uint64_t>(w, x);
+            st_run<4, SZ, uint64_t>(wa, RW, x);
+        }
+    }
+    return gfull;
+}
+
 // JOIN false: leaf -> planes (store side split); true: planes -> leaf.
 template <int SZ, bool JOIN>
 __device__ __noinline__ void split_loop(const ItemDesc& I, const JobDesc& J, const uint8_t* simg, uint8_t* dimg,
@@ -1074,12 +1120,12 @@ __device__ __forceinline__ bool run_fast(const ItemDesc& I, const JobDesc& J, co
         LLGB_FAST1(FK_MOVE2, FL_AFF, FS_AFF, 2, 2, FC_NONE, false, 4)
         LLGB_FAST1(FK_MOVE4, FL_AFF, FS_AFF, 4, 4, FC_NONE, false, 4)
         LLGB_FAST1(FK_MOVE8, FL_AFF, FS_AFF, 8, 8, FC_NONE, false, 2)
-    case FK_SPLIT2: split_loop<2, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
-    case FK_SPLIT4: split_loop<4, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
-    case FK_SPLIT8: split_loop<8, false>(I, J, simg, dimg, q0, q1, nvalid); return true;
-    case FK_JOIN2: split_loop<2, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
-    case FK_JOIN4: split_loop<4, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
-    case FK_JOIN8: split_loop<8, true>(I, J, simg, dimg, q0, q1, nvalid); return true;
+    case FK_SPLIT2: split_loop<2, false>(I, J, simg, dimg, split_uni<2, false>(I, J, simg, dimg, q0, q1, nvalid), q1, nvalid); return true;
+    case FK_SPLIT4: split_loop<4, false>(I, J, simg, dimg, split_uni<4, false>(I, J, simg, dimg, q0, q1, nvalid), q1, nvalid); return true;
+    case FK_SPLIT8: split_loop<8, false>(I, J, simg, dimg, split_uni<8, false>(I, J, simg, dimg, q0, q1, nvalid), q1, nvalid); return true;
+    case FK_JOIN2: split_loop<2, true>(I, J, simg, dimg, split_uni<2, true>(I, J, simg, dimg, q0, q1, nvalid), q1, nvalid); return true;
+    case FK_JOIN4: split_loop<4, true>(I, J, simg, dimg, split_uni<4, true>(I, J, simg, dimg, q0, q1, nvalid), q1, nvalid); return true;
+    case FK_JOIN8: split_loop<8, true>(I, J, simg, dimg, split_uni<8, true>(I, J, simg, dimg, q0, q1, nvalid), q1, nvalid); return true;
     default: return false;
     }
 #undef LLGB_FAST_SAME

@@ -328,6 +328,40 @@ def test_copy_config_tiles_hold_whole_bit_blocks(lanes):
     L.llgb_view_destroy(b)
 
 
+def _default_shape(record, src_map, dst_map, n=1 << 26):
+    L = llgb.lib()
+    _, a = _handle(record, src_map, n)
+    _, b = _handle(record, dst_map, n)
+    c = llgb.LaunchConfig()
+    llgb.check(L.llgb_copy_config(a, b, ctypes.byref(c)))
+    L.llgb_view_destroy(a)
+    L.llgb_view_destroy(b)
+    return c.as_dict()
+
+
+@pytest.mark.parametrize("dst", [{"kind": "bitpack_int", "bits": 1}, {"kind": "bitpack_int", "bits": 12},
+                                 {"kind": "bitpack_int", "bits": 12, "lanes": 32}])
+def test_integer_stream_packs_default_to_two_256_thread_ctas(dst):
+    c = _default_shape(synth.INT6, {"kind": "soa_mb"}, dst)
+    assert (c["threads"], c["ctas_per_sm"], c["src_stages"], c["dst_stages"]) == (256, 2, 2, 2)
+    assert 1024 <= c["tile_records"] <= 4096 and c["tile_records"] % 128 == 0
+
+
+@pytest.mark.parametrize("src, dst", [
+    ({"kind": "soa_mb"}, {"kind": "bitpack_float", "exp": 8, "man": 10}),
+    ({"kind": "bitpack_float", "exp": 8, "man": 10}, {"kind": "soa_mb"}),
+    ({"kind": "soa_mb"}, {"kind": "bytesplit", "inner": {"kind": "soa_mb"}}),
+])
+def test_float_packs_unpacks_and_bytesplit_keep_one_512_thread_cta(src, dst):
+    c = _default_shape(synth.MIXED_F, src, dst, 1 << 25)
+    assert (c["threads"], c["ctas_per_sm"]) == (512, 1)
+
+
+def test_integer_unpacks_keep_one_512_thread_cta():
+    c = _default_shape(synth.INT6, {"kind": "bitpack_int", "bits": 12}, {"kind": "soa_mb"})
+    assert (c["threads"], c["ctas_per_sm"]) == (512, 1)
+
+
 # ---- planner decisions, read with llgb_copy_plan (host only) ----
 
 def plan_of(record, src_map, dst_map, n, cfg=None):
