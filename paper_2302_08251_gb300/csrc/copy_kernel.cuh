@@ -1283,8 +1283,13 @@ struct GatherMax {
 };
 
 // Source image byte feeding destination image byte o, or -1 (no leaf: zero).
-__device__ __forceinline__ int32_t gather_source(const JobDesc& J, uint32_t o)
+// Source byte of destination image byte o, or -1 (padding, zero fill).
+// *run receives how many of the following destination bytes (o + 1, ...)
+// continue the same item's bytes of the same element, and so come from the
+// following source bytes.
+__device__ __forceinline__ int32_t gather_source(const JobDesc& J, uint32_t o, uint32_t* run)
 {
+    *run = 0;
     const SideDesc& D = J.dst;
     for (int g = 0; g < D.nleaves; ++g) {
         const LeafDesc& L = D.leaves[g];
@@ -1307,6 +1312,7 @@ __device__ __forceinline__ int32_t gather_source(const JobDesc& J, uint32_t o)
         for (int it = 0; it < J.nitems; ++it) {
             const ItemDesc& I = J.items[it];
             if (I.dst_leaf != g || e < I.dst_byte || e >= (uint32_t)I.dst_byte + I.size) continue;
+            *run = (uint32_t)I.dst_byte + I.size - e - 1u;
             return (int32_t)(eoff(leaf_regs(J.src.leaves[I.src_leaf]), r) + I.src_byte + (e - I.dst_byte));
         }
         return -1;
@@ -1346,9 +1352,18 @@ __device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_wor
         const uint32_t w = FORM == 4 ? gather_slot_word(J, ctid() + k * cnum(), nwords)
                                      : (ctid() + k * cnum() < nwords ? ctid() + k * cnum() : 0xFFFFFFFFu);
         uint32_t word[4], byte[4];
+        // one lookup per run of an item's contiguous bytes: a word of a
+        // 4-byte field takes one, not four
+        int32_t src = -1;
+        uint32_t run = 0;
 #pragma unroll 1
         for (int b = 0; b < 4; ++b) {
-            const int32_t src = w != 0xFFFFFFFFu ? gather_source(J, 4u * w + b) : -1;
+            if (src >= 0 && run > 0) {
+                ++src;
+                --run;
+            } else {
+                src = w != 0xFFFFFFFFu ? gather_source(J, 4u * w + b, &run) : -1;
+            }
             word[b] = src < 0 ? zero_word : (uint32_t)src >> 2;
             byte[b] = src < 0 ? 0u : (uint32_t)src & 3u;
         }
