@@ -223,6 +223,15 @@ llgb_status llgb_view_bind(llgb_view* view, void* const* dev_ptrs, int32_t n);
  * every byte of every dst blob that no (i, f) owns is written with zero.
  * Both views must have the same record (leaf types) and the same n; index
  * types may differ.  src and dst blobs must not overlap.  Queued on `stream`.
+ * A copy that runs gather programs (byte permutations, such as every pair of
+ * plain mappings) takes them from a cache of the library: the first copy of
+ * a tile layout on a device (outside stream capture) allocates its program,
+ * at most ~150 KB, with cudaMalloc, builds it with a small kernel on a
+ * stream of the library's own and waits for that kernel; later copies of
+ * the same layout, on any stream, only read it.  The cache holds at most
+ * 64 MB per process and is never freed; past that, and during capture, every
+ * CTA of the copy builds its program itself (slower for copies of a few
+ * hundred MB or less, same bytes).
  * Errors: MISMATCH, UNBOUND, UNSUPPORTED, CUDA. */
 llgb_status llgb_copy(const llgb_view* src, llgb_view* dst, void* stream);
 
@@ -312,7 +321,11 @@ llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst,
  * current device, released by llgb_batch_destroy).  Each launch moves every
  * pair exactly as llgb_copy would, same bytes.  Views keep their bound blobs
  * for the life of the batch (rebinding a view requires a new batch).  Pairs
- * with n = 0 are skipped.  Errors: as llgb_copy, plus OOM. */
+ * with n = 0 are skipped.  Gather jobs take their programs from the cache
+ * that llgb_copy describes (creation may allocate and wait for the build
+ * kernel once per new tile layout); batch arenas and the allocation-free
+ * batch do not use the cache, and their CTAs build programs themselves.
+ * Errors: as llgb_copy, plus OOM. */
 typedef struct llgb_batch llgb_batch;
 
 llgb_status llgb_batch_create(int32_t n, const llgb_view* const* src, llgb_view* const* dst,

@@ -121,6 +121,114 @@ void apply_staging(JobDesc* job, int staging)
     if (staging & LLGB_STAGING_PLAIN_LOAD) job->src.bulk_ok = 0;
 }
 
+// Gather programs built once on the GPU and shared by every CTA of every
+// copy whose job has the same tile-local layout (the program depends on the
+// leaves' image addressing, the items, the tile and the CTA's consumer
+// count -- not on record counts or blob addresses).  Kept for the process:
+// at most kProgramCacheBytes of device memory; past that, and during stream
+// capture, jobs carry no program and every CTA builds its own.
+constexpr size_t kProgramCacheBytes = 64u << 20;
+
+struct ProgramEntry {
+    JobDesc key;
+    int device = -1, mode = 0;
+    uint32_t consumers = 0;
+    uint32_t* dev = nullptr;
+};
+
+std::mutex prog_mu;
+std::multimap<uint64_t, ProgramEntry> prog_cache;
+size_t prog_bytes = 0;
+std::map<int, cudaStream_t> prog_streams;  // per device: the stream programs are built on
+
+static_assert(sizeof(JobDesc) % 8 == 0, "program keys are hashed in 8-byte words");
+
+JobDesc program_key(const JobDesc& J)
+{
+    JobDesc k = J;
+    k.n = 0;
+    k.ntiles = k.nfull = 0;
+    k.program = 0;
+    for (SideDesc* S : {&k.src, &k.dst}) {
+        memset(S->blobs, 0, sizeof S->blobs);
+        S->bulk_ok = 0;
+        for (SegDesc& g : S->segs) {
+            g.gbase = 0;
+            g.tail_bytes = 0;
+        }
+    }
+    k.nzeros = 0;
+    memset(k.zeros, 0, sizeof k.zeros);
+    return k;
+}
+
+// FNV-1a over 8-byte words (n a multiple of 8; JobDesc is).
+uint64_t hash_words(const void* p, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i + 8 <= n; i += 8) {
+        uint64_t w;
+        memcpy(&w, static_cast<const unsigned char*>(p) + i, 8);
+        h = (h ^ w) * 1099511628211ull;
+    }
+    return h;
+}
+
+// Device address of J's gather program for `mode` CTAs of `threads`
+// threads, built (once per layout, device and consumer count) on a stream of
+// the library's own and waited for, so that copies on any stream may use it;
+// 0 when none can be had (the caller's stream is capturing, the cache is
+// full, or a CUDA call failed).
+uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t caller)
+{
+    if (!gather_mode(mode) || J.gather == 0) return 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(caller, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 0;
+    }
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return 0;
+    const uint32_t consumers = (uint32_t)threads - 32u * producer_warps(mode);
+    static thread_local JobDesc key;
+    key = program_key(J);
+    const uint64_t h = hash_words(&key, sizeof key) ^ ((uint64_t)device << 56) ^ ((uint64_t)mode << 48) ^ consumers;
+    std::lock_guard<std::mutex> lock(prog_mu);
+    auto range = prog_cache.equal_range(h);
+    for (auto it = range.first; it != range.second; ++it) {
+        const ProgramEntry& e = it->second;
+        if (e.device == device && e.mode == mode && e.consumers == consumers && memcmp(&e.key, &key, sizeof key) == 0)
+            return (uint64_t)(uintptr_t)e.dev;
+    }
+    const size_t bytes = gather_program_words(mode, consumers) * 4u;
+    if (prog_bytes + bytes > kProgramCacheBytes) return 0;
+    cudaStream_t& ps = prog_streams[device];
+    if (!ps && cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
+        ps = nullptr;
+        cudaGetLastError();
+        return 0;
+    }
+    uint32_t* dev = nullptr;
+    if (cudaMalloc(&dev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (launch_gather_program(J, mode, consumers, dev, ps) != cudaSuccess || cudaStreamSynchronize(ps) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dev);
+        return 0;
+    }
+    ProgramEntry e;
+    e.key = key;
+    e.device = device;
+    e.mode = mode;
+    e.consumers = consumers;
+    e.dev = dev;
+    prog_cache.emplace(h, e);
+    prog_bytes += bytes;
+    return (uint64_t)(uintptr_t)dev;
+}
+
 // Kernel mode of a planned job under a launch shape: its gather form when the
 // gather programs cover the destination image with the consumer threads,
 // else the general kernel (0).
@@ -413,6 +521,7 @@ llgb_status run_copy(const llgb_view* src, llgb_view* dst, const llgb_launch_con
     const int mode = copy_mode(args.job, c, grid);
     if (c.threads / 32 <= (int)producer_warps(mode))
         return fail(LLGB_ERR_INVALID_ARG, "launch config leaves no consumer warp");
+    if (gather_mode(mode)) args.job.program = gather_program(args.job, mode, c.threads, s);
     cudaError_t e = launch_copy(args, mode, grid, c.threads, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
     if (library_shape) {
@@ -519,8 +628,10 @@ void balance_ctas(BatchGroup& g)
 // group gets its launch shape: stages sized for the largest images of the
 // group; value groups run two 256-thread CTAs per SM where they fit, else one
 // of 512; 256-thread gather groups two CTAs, 512-thread ones one.
+// programs: gather jobs get their programs from the program cache (which may
+// allocate and wait for a small build kernel); otherwise every CTA builds them.
 llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const* dst, std::vector<BatchGroup>* out,
-                        uint64_t* bytes, uint64_t* tiles)
+                        uint64_t* bytes, uint64_t* tiles, bool programs = false, cudaStream_t stream = nullptr)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
@@ -544,6 +655,7 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
             g->mode = mode;
             g->threads = gather_mode(mode) ? threads : 0;
         }
+        if (programs && gather_mode(mode)) J.program = gather_program(J, mode, threads, stream);
         g->jobs.push_back(J);
         for (uint64_t s : src[k]->plan.blob_sizes) *bytes += s;
         for (uint64_t s : dst[k]->plan.blob_sizes) *bytes += s;
@@ -685,7 +797,7 @@ size_t arena_slot_bytes(int32_t max_pairs, int sms)
 llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch* b)
 {
     cudaGetDevice(&b->device);
-    llgb_status st = plan_groups(n, src, dst, &b->groups, &b->bytes, &b->tiles);
+    llgb_status st = plan_groups(n, src, dst, &b->groups, &b->bytes, &b->tiles, true);
     if (st != LLGB_OK) return st;
     for (BatchGroup& g : b->groups) {
         const size_t table_bytes = g.jobs.size() * sizeof(JobDesc);

@@ -1282,7 +1282,6 @@ struct GatherMax {
     static constexpr int value = FORM == 2 ? 16 : (FORM == 4 ? 12 : 1);
 };
 
-// Source image byte feeding destination image byte o, or -1 (no leaf: zero).
 // Source byte of destination image byte o, or -1 (padding, zero fill).
 // *run receives how many of the following destination bytes (o + 1, ...)
 // continue the same item's bytes of the same element, and so come from the
@@ -1291,19 +1290,34 @@ __device__ __forceinline__ int32_t gather_source(const JobDesc& J, uint32_t o, u
 {
     *run = 0;
     const SideDesc& D = J.dst;
+    // d / bs, from the previous leaf's quotient when the strides agree: the
+    // leaves of one AoS record or AoSoA block lie within one stride of each
+    // other, so the quotient moves by at most one and needs no division
+    uint32_t qs = 0, qb = 0;
+    auto blocks = [&](uint32_t d, uint32_t bs) -> uint32_t {
+        if (bs == qs) {
+            const uint32_t t = qb * bs;
+            if (d >= t && d - t < bs) return qb;
+            if (d < t && t - d <= bs) return --qb;
+            if (d >= t + bs && d - t - bs < bs) return ++qb;
+        }
+        qs = bs;
+        qb = d / bs;
+        return qb;
+    };
     for (int g = 0; g < D.nleaves; ++g) {
         const LeafDesc& L = D.leaves[g];
         if (o < L.sbase) continue;
         const uint32_t d = o - L.sbase;
         uint32_t r, e;
         if (L.lanes == 1) {
-            r = d / L.bstride;
+            r = blocks(d, L.bstride);
             e = d - r * L.bstride;
             if (e >= L.size || r >= J.tile) continue;
         } else {
-            const uint32_t blk = d / L.bstride;
+            const uint32_t blk = blocks(d, L.bstride);
             const uint32_t rem = d - blk * L.bstride;
-            const uint32_t lane = rem / L.size;
+            const uint32_t lane = (L.size & (L.size - 1u)) == 0u ? rem >> (__ffs(L.size) - 1) : rem / L.size;
             e = rem - lane * L.size;
             if (lane >= L.lanes) continue;
             r = blk * L.lanes + lane;
@@ -1341,66 +1355,83 @@ __device__ __forceinline__ uint32_t gather_slot_word(const JobDesc& J, uint32_t 
     return p < seg_words ? J.dst.segs[seg].sbase / 4u + p : 0xFFFFFFFFu;
 }
 
+// The gather program entry of destination word w (0xFFFFFFFF: none): source
+// word indices i0 | i1 << 16 (and i2 | i3 << 16 for the 4-word form) and
+// the PRMT selectors that assemble the word from them.  Padding bytes read
+// source word zero_word.
+template <int FORM>
+__device__ __forceinline__ void gather_slot(const JobDesc& J, uint32_t zero_word, uint32_t w, uint32_t& i01,
+                                            uint32_t& s01, uint32_t& i23, uint32_t& q2)
+{
+    uint32_t word[4], byte[4];
+    // one lookup per run of an item's contiguous bytes: a word of a 4-byte
+    // field takes one, not four
+    int32_t src = -1;
+    uint32_t run = 0;
+#pragma unroll 1
+    for (int b = 0; b < 4; ++b) {
+        if (src >= 0 && run > 0) {
+            ++src;
+            --run;
+        } else {
+            src = w != 0xFFFFFFFFu ? gather_source(J, 4u * w + b, &run) : -1;
+        }
+        word[b] = src < 0 ? zero_word : (uint32_t)src >> 2;
+        byte[b] = src < 0 ? 0u : (uint32_t)src & 3u;
+    }
+    uint32_t u[4] = {word[0], word[0], word[0], word[0]};
+    int nu = 1;
+#pragma unroll
+    for (int b = 1; b < 4; ++b) {
+        bool seen = false;
+        for (int x = 0; x < 4; ++x) seen |= (x < nu && u[x] == word[b]);
+        if (!seen) {
+            if (nu == 1) u[1] = word[b];
+            else if (nu == 2) u[2] = word[b];
+            else u[3] = word[b];
+            ++nu;
+        }
+    }
+    uint32_t q0 = 0, q1 = 0;
+    q2 = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t sh = 4u * b;
+        if (word[b] == u[0]) {
+            q0 |= byte[b] << sh;
+            q2 |= (uint32_t)b << sh;
+        } else if (word[b] == u[1]) {
+            q0 |= (4u + byte[b]) << sh;
+            q2 |= (uint32_t)b << sh;
+        } else if (word[b] == u[2]) {
+            q1 |= byte[b] << sh;
+            q2 |= (4u + b) << sh;
+        } else {
+            q1 |= (4u + byte[b]) << sh;
+            q2 |= (4u + b) << sh;
+        }
+    }
+    if (FORM == 2 && nu > 2) atomicOr(&g_device_status, 0x100u);  // planner broke its promise
+    i01 = u[0] | (u[1] << 16);
+    s01 = q0 | (q1 << 16);
+    i23 = u[2] | (u[3] << 16);
+}
+
+// Every consumer thread derives its own slots of the job's program (slot k
+// of consumer c is destination word c + k * consumers, or, interleaved, the
+// word that gather_slot_word deals it).
 template <int FORM>
 __device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_word, uint32_t nwords,
                                              GatherProgram<FORM>& G)
 {
-    // Rolled over k so that gather_source is expanded once; each result is
+    // Rolled over k so that gather_slot is expanded once; each result is
     // steered into its register slot by an unrolled select.
 #pragma unroll 1
     for (int k = 0; k < GatherProgram<FORM>::K; ++k) {
         const uint32_t w = FORM == 4 ? gather_slot_word(J, ctid() + k * cnum(), nwords)
                                      : (ctid() + k * cnum() < nwords ? ctid() + k * cnum() : 0xFFFFFFFFu);
-        uint32_t word[4], byte[4];
-        // one lookup per run of an item's contiguous bytes: a word of a
-        // 4-byte field takes one, not four
-        int32_t src = -1;
-        uint32_t run = 0;
-#pragma unroll 1
-        for (int b = 0; b < 4; ++b) {
-            if (src >= 0 && run > 0) {
-                ++src;
-                --run;
-            } else {
-                src = w != 0xFFFFFFFFu ? gather_source(J, 4u * w + b, &run) : -1;
-            }
-            word[b] = src < 0 ? zero_word : (uint32_t)src >> 2;
-            byte[b] = src < 0 ? 0u : (uint32_t)src & 3u;
-        }
-        uint32_t u[4] = {word[0], word[0], word[0], word[0]};
-        int nu = 1;
-#pragma unroll
-        for (int b = 1; b < 4; ++b) {
-            bool seen = false;
-            for (int x = 0; x < 4; ++x) seen |= (x < nu && u[x] == word[b]);
-            if (!seen) {
-                if (nu == 1) u[1] = word[b];
-                else if (nu == 2) u[2] = word[b];
-                else u[3] = word[b];
-                ++nu;
-            }
-        }
-        uint32_t q0 = 0, q1 = 0, q2 = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint32_t sh = 4u * b;
-            if (word[b] == u[0]) {
-                q0 |= byte[b] << sh;
-                q2 |= (uint32_t)b << sh;
-            } else if (word[b] == u[1]) {
-                q0 |= (4u + byte[b]) << sh;
-                q2 |= (uint32_t)b << sh;
-            } else if (word[b] == u[2]) {
-                q1 |= byte[b] << sh;
-                q2 |= (4u + b) << sh;
-            } else {
-                q1 |= (4u + byte[b]) << sh;
-                q2 |= (4u + b) << sh;
-            }
-        }
-        if (FORM == 2 && nu > 2) atomicOr(&g_device_status, 0x100u);  // planner broke its promise
-        const uint32_t i01 = u[0] | (u[1] << 16), s01 = q0 | (q1 << 16);
-        const uint32_t i23 = u[2] | (u[3] << 16);
+        uint32_t i01, s01, i23, q2;
+        gather_slot<FORM>(J, zero_word, w, i01, s01, i23, q2);
 #pragma unroll
         for (int kk = 0; kk < GatherProgram<FORM>::K; ++kk) {
             if (kk == k) {
@@ -1415,6 +1446,83 @@ __device__ __forceinline__ void build_gather(const JobDesc& J, uint32_t zero_wor
             }
         }
     }
+}
+
+// A job's gather program in global memory, built once by
+// gather_program_kernel for CTAs of `cn` consumer threads: a header
+// {kProgramMagic, cn, FORM, K}, then per slot k the words of GatherProgram
+// (2 for the 2-word form: idx01, sel01; 5 for the 4-word form: idx01,
+// sel01, idx23, sel2, destination word), word f of slot k of consumer c at
+// (k F + f) cn + c, so that a CTA's consumers read them with coalesced
+// loads.  Source indices name the padding word kZeroMarker, which a loading
+// CTA replaces by its own zero word (a batch sizes stages for its largest
+// job).
+constexpr uint32_t kProgramMagic = 0x6C6C6770u;
+constexpr uint32_t kProgramHeader = 4;
+constexpr uint32_t kZeroMarker = 0xFFFFu;  // above every image word index (images < 256 KB)
+
+template <int FORM>
+__device__ __host__ constexpr uint32_t gather_program_fields() { return FORM == 2 ? 2u : 5u; }
+
+template <int FORM>
+__global__ void gather_program_kernel(const JobDesc job, uint32_t cn, uint32_t* __restrict__ out)
+{
+    constexpr uint32_t K = GatherMax<FORM>::value, F = gather_program_fields<FORM>();
+    __shared__ JobDesc J;
+    {
+        const uint2* from = reinterpret_cast<const uint2*>(&job);
+        uint2* to = reinterpret_cast<uint2*>(&J);
+        for (uint32_t w = threadIdx.x; w < sizeof(JobDesc) / 8u; w += blockDim.x) to[w] = from[w];
+    }
+    __syncthreads();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        out[0] = kProgramMagic;
+        out[1] = cn;
+        out[2] = (uint32_t)FORM;
+        out[3] = K;
+    }
+    if (i >= K * cn) return;
+    const uint32_t k = i / cn, c = i - k * cn, x = c + k * cn;
+    const uint32_t nwords = (J.dst.img_bytes - kImageSlack) / 4u;
+    const uint32_t w = FORM == 4 ? gather_slot_word(J, x, nwords) : (x < nwords ? x : 0xFFFFFFFFu);
+    uint32_t i01, s01, i23, q2;
+    gather_slot<FORM>(J, kZeroMarker, w, i01, s01, i23, q2);
+    uint32_t* o = out + kProgramHeader;
+    o[(k * F + 0u) * cn + c] = i01;
+    o[(k * F + 1u) * cn + c] = s01;
+    if constexpr (FORM == 4) {
+        o[(k * F + 2u) * cn + c] = i23;
+        o[(k * F + 3u) * cn + c] = q2;
+        o[(k * F + 4u) * cn + c] = w == 0xFFFFFFFFu ? 0xFFFFu : (w & 0xFFFFu);
+    }
+}
+
+// This consumer thread's slots from a built program; false (nothing loaded)
+// when the program was built for another consumer count or form.
+template <int FORM>
+__device__ __forceinline__ bool load_gather(const uint32_t* prog, uint32_t zero_word, GatherProgram<FORM>& G)
+{
+    constexpr uint32_t K = GatherMax<FORM>::value, F = gather_program_fields<FORM>();
+    const uint32_t cn = cnum(), c = ctid();
+    if (prog[0] != kProgramMagic || prog[1] != cn || prog[2] != (uint32_t)FORM || prog[3] != K) return false;
+    const uint32_t* o = prog + kProgramHeader;
+    auto fix = [&](uint32_t v) {
+        const uint32_t lo = v & 0xFFFFu, hi = v >> 16;
+        return (lo == kZeroMarker ? zero_word : lo) | ((hi == kZeroMarker ? zero_word : hi) << 16);
+    };
+#pragma unroll
+    for (uint32_t k = 0; k < K; ++k) {
+        G.idx01[k] = fix(o[(k * F + 0u) * cn + c]);
+        G.sel01[k] = o[(k * F + 1u) * cn + c];
+        if constexpr (FORM == 4) {
+            G.idx23[k] = fix(o[(k * F + 2u) * cn + c]);
+            G.sel2[k] = o[(k * F + 3u) * cn + c];
+            const uint32_t w = o[(k * F + 4u) * cn + c] & 0xFFFFu;
+            G.dstw[k / 2] = (k & 1u) ? (G.dstw[k / 2] & 0xFFFFu) | (w << 16) : w;
+        }
+    }
+    return true;
 }
 
 template <int FORM>
@@ -1754,7 +1862,8 @@ __device__ void consumer(const CopyArgs& a, CopyShared& H, uint8_t* src_stage, u
                 share = item_share(H.job);
             } else {
                 gather_words = (H.job.dst.img_bytes - kImageSlack) / 4u;
-                build_gather<MODE>(H.job, zero_word, gather_words, gp);
+                const uint32_t* prog = reinterpret_cast<const uint32_t*>(H.job.program);
+                if (!(prog && load_gather<MODE>(prog, zero_word, gp))) build_gather<MODE>(H.job, zero_word, gather_words, gp);
             }
         }
         const JobDesc& J = H.job;

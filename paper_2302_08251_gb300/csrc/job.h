@@ -189,6 +189,7 @@ struct JobDesc {
     uint8_t ored;        // some PackDesc has `ored` set: zero those streams before every tile
     uint8_t seg;         // kernel mode for AoSoA-organised bit leaves: 1 (generic loop), 3 (compile-time loops), else 0
     uint8_t pad[6];
+    uint64_t program;    // device address of the job's gather program (gather_program_kernel), or 0: every CTA builds it
 };
 
 // Launch-wide parameters of the copy kernel.

@@ -15,6 +15,12 @@ namespace llgb {
 cudaError_t launch_copy(const CopyArgs& args, int mode, int grid, int threads, size_t smem_bytes,
                         cudaStream_t stream);
 int gather_words_per_thread(int mode);
+// copy_gather.cu: a job's gather program for CTAs of `consumers` consumer
+// threads (JobDesc::program), built on the GPU into `out`, which holds
+// gather_program_words(mode, consumers) words.
+size_t gather_program_words(int mode, uint32_t consumers);
+cudaError_t launch_gather_program(const JobDesc& job, int mode, uint32_t consumers, uint32_t* out,
+                                  cudaStream_t stream);
 // Raise the copy kernel's dynamic shared memory limit for `mode` to smem_bytes
 // (done by launch_copy too; call it before capturing a graph).
 cudaError_t prepare_copy(int mode, size_t smem_bytes);

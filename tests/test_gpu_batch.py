@@ -157,3 +157,39 @@ def test_batch_of_large_jobs_with_opposite_image_sizes():
         for g_blob, e_blob in zip(d.blob_bytes(), dst_o.blobs):
             assert np.array_equal(g_blob, e_blob)
     batch.close()
+
+
+GATHER_PAIRS = [
+    (synth.PARTICLE, {"kind": "aos"}, {"kind": "soa_mb"}),
+    (synth.PARTICLE, {"kind": "soa_mb"}, {"kind": "aos"}),
+    (synth.CFD, {"kind": "soa_mb"}, {"kind": "aosoa", "lanes": 32}),
+    (synth.CFD, {"kind": "aosoa", "lanes": 8}, {"kind": "aosoa", "lanes": 32}),
+    (synth.CFD, {"kind": "aos", "packed": 1}, {"kind": "soa_sb"}),
+]
+
+
+@pytest.mark.parametrize("pair", range(len(GATHER_PAIRS)))
+def test_shared_and_per_cta_gather_programs_give_the_same_bytes(pair):
+    # llgb_copy and llgb_batch take the job's gather program from the
+    # library's program cache (built once by a small kernel); a batch arena
+    # does not use the cache, so every CTA builds its own.  All three must
+    # store the oracle's bytes.
+    rec, sm, dm = GATHER_PAIRS[pair]
+    n = 400_000 + 77  # many tiles per CTA: the copy runs its gather kernel mode
+    src_o = oracle_view(rec, sm, fields_for(rec, n, 90 + pair))
+    dst_o = oracle.OracleView(rec, dm, n)
+    src_o.copy_to(dst_o)
+    src = device_view_of(src_o)
+    d_copy, d_batch, d_arena = (empty_device_view(rec, dm, n, fill=f) for f in (0xAB, 0x5A, 0x3C))
+    assert llgb.llgb_copy_plan(src, d_copy)["kernel_mode"] in (2, 4)
+    llgb.llgb_copy(src, d_copy)
+    batch = llgb.Batch([(src, d_batch)])
+    batch.launch()
+    arena = llgb.Arena(max_pairs=4, slots=2)
+    arena.copy([(src, d_arena)])
+    sync_and_check_status()
+    for d in (d_copy, d_batch, d_arena):
+        got = d.blob_bytes()
+        assert all(np.array_equal(g, e) for g, e in zip(got, dst_o.blobs))
+    batch.close()
+    arena.close()
