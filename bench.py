@@ -439,6 +439,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "traffic": traffic,
+                         "per": "step (one launch per row; achieved and traffic both per step)",
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                          "kernel": "llgb::copy_kernel", "spec_frac_8tbs": round(achieved / 8000.0, 4)},
             "rows": rows_out,

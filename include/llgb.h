@@ -323,8 +323,10 @@ llgb_status llgb_copy_with(const llgb_view* src, llgb_view* dst,
  * for the life of the batch (rebinding a view requires a new batch).  Pairs
  * with n = 0 are skipped.  Gather jobs take their programs from the cache
  * that llgb_copy describes (creation may allocate and wait for the build
- * kernel once per new tile layout); batch arenas and the allocation-free
- * batch do not use the cache, and their CTAs build programs themselves.
+ * kernel once per new tile layout).  A batch arena uses the programs the
+ * cache already holds (a lookup: it allocates and waits for nothing) and has
+ * its CTAs build the others; the allocation-free batch does not use the
+ * cache.
  * Errors: as llgb_copy, plus OOM. */
 typedef struct llgb_batch llgb_batch;
 

@@ -178,15 +178,11 @@ uint64_t hash_words(const void* p, size_t n)
 // threads, built (once per layout, device and consumer count) on a stream of
 // the library's own and waited for, so that copies on any stream may use it;
 // 0 when none can be had (the caller's stream is capturing, the cache is
-// full, or a CUDA call failed).
-uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t caller)
+// full, or a CUDA call failed).  build false: a lookup only, which allocates
+// and waits for nothing (0 if the layout has no program yet).
+uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t caller, bool build = true)
 {
     if (!gather_mode(mode) || J.gather == 0) return 0;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(caller, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
-        cudaGetLastError();
-        return 0;
-    }
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return 0;
     const uint32_t consumers = (uint32_t)threads - 32u * producer_warps(mode);
@@ -201,7 +197,12 @@ uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t ca
             return (uint64_t)(uintptr_t)e.dev;
     }
     const size_t bytes = gather_program_words(mode, consumers) * 4u;
-    if (prog_bytes + bytes > kProgramCacheBytes) return 0;
+    if (!build || prog_bytes + bytes > kProgramCacheBytes) return 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(caller, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaStream_t& ps = prog_streams[device];
     if (!ps && cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
         ps = nullptr;
@@ -628,10 +629,13 @@ void balance_ctas(BatchGroup& g)
 // group gets its launch shape: stages sized for the largest images of the
 // group; value groups run two 256-thread CTAs per SM where they fit, else one
 // of 512; 256-thread gather groups two CTAs, 512-thread ones one.
-// programs: gather jobs get their programs from the program cache (which may
-// allocate and wait for a small build kernel); otherwise every CTA builds them.
+// Gather jobs' programs: kProgramsBuild takes them from the program cache,
+// building missing ones (which may allocate and wait for a small build
+// kernel); kProgramsLookup takes only those the cache already holds; the
+// CTAs build the rest, and every program with kProgramsNone.
+enum { kProgramsNone = 0, kProgramsLookup = 1, kProgramsBuild = 2 };
 llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const* dst, std::vector<BatchGroup>* out,
-                        uint64_t* bytes, uint64_t* tiles, bool programs = false, cudaStream_t stream = nullptr)
+                        uint64_t* bytes, uint64_t* tiles, int programs = kProgramsNone, cudaStream_t stream = nullptr)
 {
     const DeviceInfo dev = device_info();
     const int sms = dev.sms > 0 ? dev.sms : 152;
@@ -655,7 +659,8 @@ llgb_status plan_groups(int32_t n, const llgb_view* const* src, llgb_view* const
             g->mode = mode;
             g->threads = gather_mode(mode) ? threads : 0;
         }
-        if (programs && gather_mode(mode)) J.program = gather_program(J, mode, threads, stream);
+        if (programs != kProgramsNone && gather_mode(mode))
+            J.program = gather_program(J, mode, threads, stream, programs == kProgramsBuild);
         g->jobs.push_back(J);
         for (uint64_t s : src[k]->plan.blob_sizes) *bytes += s;
         for (uint64_t s : dst[k]->plan.blob_sizes) *bytes += s;
@@ -797,7 +802,7 @@ size_t arena_slot_bytes(int32_t max_pairs, int sms)
 llgb_status batch_build(int32_t n, const llgb_view* const* src, llgb_view* const* dst, llgb_batch* b)
 {
     cudaGetDevice(&b->device);
-    llgb_status st = plan_groups(n, src, dst, &b->groups, &b->bytes, &b->tiles, true);
+    llgb_status st = plan_groups(n, src, dst, &b->groups, &b->bytes, &b->tiles, kProgramsBuild);
     if (st != LLGB_OK) return st;
     for (BatchGroup& g : b->groups) {
         const size_t table_bytes = g.jobs.size() * sizeof(JobDesc);
@@ -1321,7 +1326,7 @@ llgb_status llgb_batch_arena_copy(llgb_batch_arena* a, int32_t n, const llgb_vie
         if (device != a->device) return fail(LLGB_ERR_INVALID_ARG, "arena used on another device than it was made on");
         std::lock_guard<std::mutex> lock(a->mu);
         uint64_t bytes = 0, tiles = 0;
-        llgb_status st = plan_groups(n, src, dst, &a->groups, &bytes, &tiles);
+        llgb_status st = plan_groups(n, src, dst, &a->groups, &bytes, &tiles, kProgramsLookup);
         if (st != LLGB_OK || a->groups.empty()) return st;
         const int slot = a->next;
         a->next = (a->next + 1) % a->nslots;

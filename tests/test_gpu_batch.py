@@ -171,8 +171,9 @@ GATHER_PAIRS = [
 @pytest.mark.parametrize("pair", range(len(GATHER_PAIRS)))
 def test_shared_and_per_cta_gather_programs_give_the_same_bytes(pair):
     # llgb_copy and llgb_batch take the job's gather program from the
-    # library's program cache (built once by a small kernel); a batch arena
-    # does not use the cache, so every CTA builds its own.  All three must
+    # library's program cache (built once by a small kernel), and a batch
+    # arena takes it from there when the cache has it; the allocation-free
+    # batch never uses the cache, so every CTA builds its own.  All four must
     # store the oracle's bytes.
     rec, sm, dm = GATHER_PAIRS[pair]
     n = 400_000 + 77  # many tiles per CTA: the copy runs its gather kernel mode
@@ -180,15 +181,16 @@ def test_shared_and_per_cta_gather_programs_give_the_same_bytes(pair):
     dst_o = oracle.OracleView(rec, dm, n)
     src_o.copy_to(dst_o)
     src = device_view_of(src_o)
-    d_copy, d_batch, d_arena = (empty_device_view(rec, dm, n, fill=f) for f in (0xAB, 0x5A, 0x3C))
+    d_copy, d_batch, d_arena, d_free = (empty_device_view(rec, dm, n, fill=f) for f in (0xAB, 0x5A, 0x3C, 0x77))
     assert llgb.llgb_copy_plan(src, d_copy)["kernel_mode"] in (2, 4)
     llgb.llgb_copy(src, d_copy)
     batch = llgb.Batch([(src, d_batch)])
     batch.launch()
     arena = llgb.Arena(max_pairs=4, slots=2)
     arena.copy([(src, d_arena)])
+    llgb.llgb_batch_copy_noalloc([(src, d_free)])
     sync_and_check_status()
-    for d in (d_copy, d_batch, d_arena):
+    for d in (d_copy, d_batch, d_arena, d_free):
         got = d.blob_bytes()
         assert all(np.array_equal(g, e) for g, e in zip(got, dst_o.blobs))
     batch.close()
