@@ -923,12 +923,49 @@ def main():
     ap.add_argument("--scale", type=int, default=1, help="divide record counts (profiling)")
     ap.add_argument("--nbody-only", action="store_true",
                     help="run only W + K n-body steps on 65,536 SoA particles (profiling)")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="N",
+                    help="run only one batch of the first N serving-workload requests of at most "
+                         "3e6 records, W + K launches (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.nbody_only:
         return run_nbody_only(args)
+    if args.batch_only:
+        return run_batch_only(args)
     return run_gpu(args)
+
+
+def run_batch_only(args):
+    """One llgb_batch of the first N requests (of at most 3e6 records) of the
+    serving workload, launched W + K times, for profiling the batch kernel;
+    prints the batch's size and the mean time of the K timed launches."""
+    import torch
+    from paper_2302_08251_gb300 import llgb, serve
+    reqs = [r for r in serve.workload(count=4096) if r.n <= 3_000_000][:args.batch_only]
+    ex = serve.GpuExecutor(streams=1, seed=11)
+    pairs, nbytes = [], 0
+    for r in reqs:
+        ex.allocate(r)
+        src, dst, _ = r.views
+        pairs.append((src, dst))
+        nbytes += ex.nbytes(r)
+    batch = llgb.Batch(pairs)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.launch(stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        batch.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / max(1, args.steps)
+    assert llgb.llgb_device_status(reset=True) == 0
+    print(json.dumps({"batch_entries": len(pairs), "bytes": nbytes, "info": batch.info(),
+                      "ms_per_launch": round(ms, 4), "GB/s": round(nbytes / ms / 1e6, 1)}))
+    return 0
 
 
 def run_nbody_only(args):

@@ -225,7 +225,8 @@ llgb_status llgb_view_bind(llgb_view* view, void* const* dev_ptrs, int32_t n);
  * types may differ.  src and dst blobs must not overlap.  Queued on `stream`.
  * A copy that runs gather programs (byte permutations, such as every pair of
  * plain mappings) takes them from a cache of the library: the first copy of
- * a tile layout on a device (outside stream capture) allocates its program,
+ * a tile layout on a device and CUDA context (outside stream capture; a
+ * device reset starts the cache anew) allocates its program,
  * at most ~150 KB, with cudaMalloc, builds it with a small kernel on a
  * stream of the library's own and waits for that kernel; later copies of
  * the same layout, on any stream, only read it.  The cache holds at most

@@ -3,6 +3,7 @@
 // Host-side validation, planning and launch.  No exception leaves this file:
 // every entry point catches and turns failures into an llgb_status with a
 // thread-local message.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -132,14 +133,43 @@ constexpr size_t kProgramCacheBytes = 64u << 20;
 struct ProgramEntry {
     JobDesc key;
     int device = -1, mode = 0;
+    uint64_t context = 0;  // a device reset makes a new context, and the old buffers invalid
     uint32_t consumers = 0;
     uint32_t* dev = nullptr;
 };
 
+// Identity of the CUDA context current on this thread (0 if it cannot be
+// read), through the driver entry points the runtime hands out.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+uint64_t context_identity()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
 std::mutex prog_mu;
 std::multimap<uint64_t, ProgramEntry> prog_cache;
 size_t prog_bytes = 0;
-std::map<int, cudaStream_t> prog_streams;  // per device: the stream programs are built on
+std::map<std::pair<int, uint64_t>, cudaStream_t> prog_streams;  // per device and context: the stream programs are built on
 
 static_assert(sizeof(JobDesc) % 8 == 0, "program keys are hashed in 8-byte words");
 
@@ -185,6 +215,8 @@ uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t ca
     if (!gather_mode(mode) || J.gather == 0) return 0;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return 0;
+    const uint64_t context = context_identity();
+    if (context == 0) return 0;  // no way to tell a reset device's buffers from live ones
     const uint32_t consumers = (uint32_t)threads - 32u * producer_warps(mode);
     static thread_local JobDesc key;
     key = program_key(J);
@@ -193,7 +225,8 @@ uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t ca
     auto range = prog_cache.equal_range(h);
     for (auto it = range.first; it != range.second; ++it) {
         const ProgramEntry& e = it->second;
-        if (e.device == device && e.mode == mode && e.consumers == consumers && memcmp(&e.key, &key, sizeof key) == 0)
+        if (e.device == device && e.context == context && e.mode == mode && e.consumers == consumers &&
+            memcmp(&e.key, &key, sizeof key) == 0)
             return (uint64_t)(uintptr_t)e.dev;
     }
     const size_t bytes = gather_program_words(mode, consumers) * 4u;
@@ -203,7 +236,7 @@ uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t ca
         cudaGetLastError();
         return 0;
     }
-    cudaStream_t& ps = prog_streams[device];
+    cudaStream_t& ps = prog_streams[{device, context}];
     if (!ps && cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
         ps = nullptr;
         cudaGetLastError();
@@ -222,6 +255,7 @@ uint64_t gather_program(const JobDesc& J, int mode, int threads, cudaStream_t ca
     ProgramEntry e;
     e.key = key;
     e.device = device;
+    e.context = context;
     e.mode = mode;
     e.consumers = consumers;
     e.dev = dev;
