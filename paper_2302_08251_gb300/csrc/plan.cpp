@@ -833,6 +833,11 @@ llgb_status plan_job(const ViewPlan& src, const std::vector<void*>& src_ptrs, co
         const Recipe a = src.recipes[f], b = dst.recipes[f];
         const int32_t t = src.types[f];
         if (b.op == L_NULL) continue;  // the destination stores nothing (Null)
+        // A Null source loads 0, whose bytes are all zero: a destination that
+        // stores bytes (plain or byte planes) then holds exactly the zero fill
+        // of bytes no item owns, so the leaf needs no item -- and a job of
+        // otherwise byte moves keeps its gather programs.
+        if (a.op == L_NULL && (b.op == L_DIRECT || b.op == L_SPLIT)) continue;
         const int size = type_size(t);
         const bool a_bytes = a.op == L_DIRECT || a.op == L_SPLIT;
         const bool b_bytes = b.op == L_DIRECT || b.op == L_SPLIT;

@@ -510,3 +510,15 @@ def test_autotune_file_round_trip_and_rejects(tmp_path):
     llgb.llgb_autotune_clear()
     llgb.llgb_autotune_save(str(out))
     assert '"entries": {\n}}' in out.read_text()
+
+
+def test_null_sourced_leaves_leave_a_byte_move_job_on_gather_programs():
+    # a Null part loads 0: into a byte-stored destination that is the zero
+    # fill of unowned bytes, so the job keeps only byte moves
+    null_mass = {"kind": "split", "fields": [6], "inner": {"kind": "null"}, "rest": {"kind": "soa_mb"}}
+    p = plan_of(synth.PARTICLE, null_mass, {"kind": "aos"}, 1 << 20)
+    assert p["kernel_mode"] in (2, 4) and p["items"] == 6 and p["generic_items"] == 0
+    # a bit-packed destination still takes the value loops for every leaf
+    p = plan_of(synth.INT6, {"kind": "split", "fields": [5], "inner": {"kind": "null"}, "rest": {"kind": "soa_mb"}},
+                {"kind": "bitpack_int", "bits": 12}, 1 << 20)
+    assert p["kernel_mode"] == 0 and p["items"] == 6
