@@ -335,9 +335,12 @@ static bool int_pack_job(const JobDesc& J)
 
 // Default launch shape (from launch-shape sweeps on GB300).
 //  * Gather jobs (byte permutations) run two 256-thread CTAs per SM on
-//    ~12 KB tiles (a thread's gather program covers at most a fixed number
-//    of destination words) -- or, with four or more destination runs per
-//    tile, one 512-thread CTA on ~30 KB tiles.
+//    tiles of up to ~16 KB, shrunk until the CTA's gather programs cover
+//    them (a thread's program holds a fixed number of destination words):
+//    the largest such tile keeps the most bytes in flight (2^26-record
+//    particle SoA -> AoS: 384-record tiles 0.84, 512-record tiles 0.97 of
+//    measured HBM) -- or, with four or more destination runs per tile, one
+//    512-thread CTA on ~30 KB tiles.
 //  * Other jobs run one 512-thread CTA per SM with two source and two
 //    destination stages of the largest tile that fits (at most 4096
 //    records): per-tile costs are then spread over the most records.
@@ -380,7 +383,7 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
         c.ctas_per_sm = 2;
         c.src_stages = 4;
         c.dst_stages = 3;
-        tile = (uint64_t)(12288.0 / std::max(std::max(sb, db), 1.0)) / q * q;
+        tile = (uint64_t)(16384.0 / std::max(std::max(sb, db), 1.0)) / q * q;
     } else {
         const bool light = int_pack_job(probe);
         c.threads = light ? 256 : 512;
