@@ -401,8 +401,9 @@ llgb_status llgb_batch_copy_noalloc(int32_t n, const llgb_view* const* src, llgb
                                     void* stream);
 
 /* Autotuner: time candidate launch shapes of llgb_copy(src, dst) on `stream`
- * (each candidate runs the copy 4 times; dst is written) -- first tile
- * records, stages, threads and CTAs per SM with TMA staging, then the staging
+ * (each candidate runs the copy 4 times; dst is written) -- first the
+ * default shape at other stage counts, and tile records, stages, threads and
+ * CTAs per SM with TMA staging, then the staging
  * schemes (llgb_staging) of the fastest shape.  The default shape and the
  * four fastest are timed twice more (best of three); a shape or staging
  * scheme replaces the default only when it is at least 2% faster, so that

@@ -1445,9 +1445,19 @@ llgb_status llgb_autotune(const llgb_view* src, llgb_view* dst, void* stream, ll
         };
         // 1. tile size, threads and CTAs per SM, pipeline depths (TMA staging)
         std::vector<llgb_launch_config> cands{base};
+        // the default shape with other pipeline depths (which of 3 and 4
+        // source stages is faster differs from pair to pair)
+        for (int ns : {2, 3, 4, 5})
+            for (int nd : {2, 3, 4}) {
+                llgb_launch_config c = base;
+                if (ns == base.src_stages && nd == base.dst_stages) continue;
+                c.src_stages = ns;
+                c.dst_stages = nd;
+                cands.push_back(c);
+            }
         for (double target : {6144.0, 12288.0, 24576.0, 49152.0, 73728.0})
             for (int threads : {256, 512})
-                for (int ns : {2, 4})
+                for (int ns : {2, 3, 4})
                     for (int nd : {2, 3}) {
                         llgb_launch_config c{};
                         c.tile_records = (int32_t)std::max<uint64_t>(q, (uint64_t)(target / per_rec) / q * q);
