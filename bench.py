@@ -872,7 +872,13 @@ def serving_bench(device, args):
 def e2e_bench(wl, stream, args):
     """The same step through host buffers: every row's source blobs go
     host->device from pinned memory, the copy runs, the destination blobs
-    come back device->host, all inside the timed region."""
+    come back device->host, all inside the timed region.  Copies in and out
+    run on streams of their own, ordered by events: a row's copy-in waits for
+    the last re-layout that read the same source view (rows of one record
+    and source mapping share it), a row's re-layout for its copy-in and for
+    the previous step's copy-out of its destination, and its copy-out for its
+    re-layout -- so copies in run ahead while copies out follow, both
+    directions of the full-duplex host link busy at once."""
     import torch
     from paper_2302_08251_gb300 import llgb
     hosts = {}
@@ -884,30 +890,56 @@ def e2e_bench(wl, stream, args):
             for h, b in zip(hosts[sid], r["src"].blobs):
                 h.copy_(b)
     out_max = max(max(b.numel() for b in r["dst"].blobs) for r in wl.rows)
-    host_out = torch.empty(out_max, dtype=torch.uint8, pin_memory=True)
+    host_out = torch.empty(out_max, dtype=torch.uint8, pin_memory=True)  # copy-outs run in order on one stream
     h2d = sum(sum(b.numel() for b in r["src"].blobs) for r in wl.rows)
     d2h = sum(sum(b.numel() for b in r["dst"].blobs) for r in wl.rows)
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    K = len(wl.rows)
+    ev_in = [torch.cuda.Event() for _ in range(K)]
+    ev_kern = [torch.cuda.Event() for _ in range(K)]
+    ev_out = [torch.cuda.Event() for _ in range(K)]
+    for k in range(K):  # recorded once, so that the first step's waits are satisfied
+        ev_out[k].record(stream)
+
+    last_read = {}  # source view -> event of the last re-layout that read it
 
     def step():
-        for r in wl.rows:
-            for h, b in zip(hosts[id(r["src"])], r["src"].blobs):
-                b.copy_(h, non_blocking=True)
+        for k, r in enumerate(wl.rows):
+            sid = id(r["src"])
+            if sid in last_read:
+                s_in.wait_event(last_read[sid])
+            with torch.cuda.stream(s_in):
+                for h, b in zip(hosts[id(r["src"])], r["src"].blobs):
+                    b.copy_(h, non_blocking=True)
+            ev_in[k].record(s_in)
+            stream.wait_event(ev_in[k])
+            stream.wait_event(ev_out[k])
             llgb.llgb_copy(r["src"], r["dst"], stream)
-            for b in r["dst"].blobs:
-                host_out[:b.numel()].copy_(b, non_blocking=True)
+            ev_kern[k].record(stream)
+            last_read[sid] = ev_kern[k]
+            s_out.wait_event(ev_kern[k])
+            with torch.cuda.stream(s_out):
+                for b in r["dst"].blobs:
+                    host_out[:b.numel()].copy_(b, non_blocking=True)
+            ev_out[k].record(s_out)
+
     step()
     torch.cuda.synchronize()
     reps = max(1, min(args.steps, 3))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    s_in.wait_event(a)
+    s_out.wait_event(a)
     for _ in range(reps):
         step()
+    stream.wait_stream(s_in)
+    stream.wait_stream(s_out)
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
     return {"value": round(wl.bytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
-            "steps": reps}
+            "steps": reps, "overlap": "copies in run ahead on one stream, copies out follow on another"}
 
 
 def main():
