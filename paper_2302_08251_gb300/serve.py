@@ -190,6 +190,27 @@ class GpuExecutor:
         self.seed = seed
         self.keep = keep  # keep each finished request's views in r.result (tests)
 
+    def warm(self, pairs, n: int = 1 << 16) -> None:
+        """Before serving: plan one batch of n-record views per (record,
+        source mapping, destination mapping) in `pairs` and drop it, so that
+        the library's cache holds the gather programs of those layouts (the
+        arena only looks programs up; it builds none).  Allocates and waits,
+        once per layout."""
+        import json
+        torch = self.torch
+        seen = set()
+        for record, src_map, dst_map in pairs:
+            key = (tuple(record), json.dumps(src_map, sort_keys=True), json.dumps(dst_map, sort_keys=True))
+            if key in seen:
+                continue
+            seen.add(key)
+            rec = self._record(record)
+            with torch.cuda.device(self.device):
+                src = self.llgb.View(rec, src_map, (n,), device=self.device)
+                dst = self.llgb.View(rec, dst_map, (n,), device=self.device)
+                self.llgb.Batch([(src, dst)]).close()
+            del src, dst
+
     def _record(self, rec):
         key = tuple(rec)
         if key not in self._records:
