@@ -65,6 +65,8 @@ def test_batches_from_different_ticks_overlap_on_the_device():
     ensure_library()
     reqs = serve.workload(count=32, rate_hz=100000.0, n_lo=3e6, n_hi=1e7, seed=29)
     ex = serve.GpuExecutor(streams=4, seed=9, keep=True)
+    # the arena then takes the gather programs of these pairs from the cache
+    ex.warm([(r.record, r.src_map, r.dst_map) for r in reqs])
     srv = serve.Server(ex, budget_bytes=32 * serve.GB, deadline_s=60.0, max_batch=2)
     stats = srv.run(reqs)
     sync_and_check_status()
