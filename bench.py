@@ -938,9 +938,44 @@ def e2e_bench(wl, stream, args):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    link = host_link_rates(hosts, wl, host_out, s_in, s_out)
     return {"value": round(wl.bytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
-            "steps": reps, "overlap": "copies in run ahead on one stream, copies out follow on another"}
+            "steps": reps, "overlap": "copies in run ahead on one stream, copies out follow on another",
+            "host_link_GBs": link,
+            "transfer_frac_of_link": round((h2d + d2h) / (ms * 1e-3) / 1e9 / link["both"], 4)}
+
+
+def host_link_rates(hosts, wl, host_out, s_in, s_out):
+    """Copy rates of the host link from the e2e leg's own pinned buffers: one
+    source blob in, a destination blob out, and both at once (GB/s)."""
+    import torch
+    src_h, src_d = max(((h, b) for r in wl.rows for h, b in zip(hosts[id(r["src"])], r["src"].blobs)),
+                       key=lambda hb: hb[0].numel())
+    dst_d = max((b for r in wl.rows for b in r["dst"].blobs), key=lambda b: b.numel())
+    nb = min(src_h.numel(), dst_d.numel(), host_out.numel())
+
+    def timed(h2d, d2h):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s_in.wait_event(a)
+        s_out.wait_event(a)
+        if h2d:
+            with torch.cuda.stream(s_in):
+                src_d[:nb].copy_(src_h[:nb], non_blocking=True)
+        if d2h:
+            with torch.cuda.stream(s_out):
+                host_out[:nb].copy_(dst_d[:nb], non_blocking=True)
+        cur = torch.cuda.current_stream()
+        cur.wait_stream(s_in)
+        cur.wait_stream(s_out)
+        b.record()
+        b.synchronize()
+        return nb * (int(h2d) + int(d2h)) / (a.elapsed_time(b) * 1e-3) / 1e9
+
+    return {k: round(max(timed(*f) for _ in range(3)), 1)
+            for k, f in (("h2d", (True, False)), ("d2h", (False, True)), ("both", (True, True)))}
 
 
 def main():
