@@ -393,6 +393,12 @@ llgb_status default_config(const llgb_view* src, const llgb_view* dst, llgb_laun
         const double budget = 227.0 * 1024 / c.ctas_per_sm - (double)copy_shared_header_bytes() - 64.0;
         tile = (uint64_t)(budget / (2.0 * (std::max(sb, 1.0) + std::max(db, 1.0)))) / q * q;
         tile = std::min<uint64_t>(tile, 4096 / q * q);
+        // integer-stream packs: a multiple of 256 records, so that every
+        // stream run of a tile is whole 32-byte sectors (measured: b = 1
+        // pack 0.88 at 2176 records, 0.94 at 2048; b = 31 0.93 at 1152,
+        // 0.96 at 1024; b = 17 the other way, 0.96 at 1408, 0.94 at 1280)
+        const uint64_t q256 = std::max<uint64_t>(q, 256u / q * q);
+        if (light && q256 % q == 0 && tile >= 2 * q256) tile = tile / q256 * q256;
     }
     if (tile < q) tile = q;
     if (!for_batch) {
