@@ -409,10 +409,11 @@ def run_gpu(args):
                                "frac": round(gbs / hbm, 4)}
     traffic = profiled_traffic()
 
+    # end to end through host buffers (first among the extras: it measured
+    # 179-269 GB/s after the n-body leg, 255-262 GB/s on its own)
+    e2e = e2e_bench(wl, stream, args) if rank == 0 and not args.no_extras else None
     # n-body consumer (65,536 particles through AoS / SoA / AoSoA32 views)
     nbody = nbody_bench(device, args) if rank == 0 and not args.no_extras else None
-    # end to end through host buffers
-    e2e = e2e_bench(wl, stream, args) if rank == 0 and not args.no_extras else None
     batched = serving = sweeps = None
     step_bytes = wl.bytes
     if rank == 0 and not args.no_extras:
