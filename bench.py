@@ -211,8 +211,9 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
+    # the kernels, and the planner and launch shapes that decide what they run
     for f in ("copy_kernel.cuh", "copy.cu", "copy_mode0.cu", "copy_mode1.cu", "copy_mode3.cu", "copy_gather.cu",
-              "stream_loops.cuh", "stream_specs.h", "fconv.cuh", "job.h"):
+              "stream_loops.cuh", "stream_specs.h", "fconv.cuh", "job.h", "plan.cpp", "capi.cpp"):
         with open(os.path.join(ROOT, "paper_2302_08251_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
