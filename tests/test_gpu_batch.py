@@ -4,6 +4,8 @@ A batch must move every pair exactly as one llgb_copy per pair does (same
 bytes, padding included), with or without a CUDA graph, for mixed mapping
 pairs, records and sizes (1 record, ragged tails, empty views).
 """
+import random
+
 import numpy as np
 import pytest
 import torch
@@ -11,7 +13,9 @@ import torch
 import oracle
 from paper_2302_08251_gb300 import llgb, synth
 from helpers import oracle_view
-from gpu_util import device_view_of, empty_device_view, ensure_library, sync_and_check_status
+from gpu_util import assert_same_bytes, device_view_of, empty_device_view, ensure_library, sync_and_check_status
+from test_gpu_random_pairs import random_field
+from test_plan_sweep import leaf_mapping, random_record
 
 pytestmark = pytest.mark.gpu
 
@@ -194,4 +198,56 @@ def test_shared_and_per_cta_gather_programs_give_the_same_bytes(pair):
         got = d.blob_bytes()
         assert all(np.array_equal(g, e) for g, e in zip(got, dst_o.blobs))
     batch.close()
+    arena.close()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_pairs_in_one_batch_arena_and_allocation_free_call(seed):
+    # 24 seeded random records and mapping pairs (as in the random single-copy
+    # sweep: plain, bit-packed in both organisations, Bytesplit, ChangeType,
+    # Split with Null, nested), 0 to 100,007 records each, mixed in one batch
+    # (graph and stream launches), one arena copy and one allocation-free
+    # call: the jobs of every kernel mode share launch groups and descriptor
+    # tables, and every destination must hold the oracle's bytes
+    g = random.Random(5000 + seed)
+    vals = np.random.default_rng(6000 + seed)
+    cases = []
+    for _ in range(200):
+        if len(cases) == 24:
+            break
+        leaves = random_record(g)
+        types = [t for _, t in leaves]
+        n = g.choice([0, 1, 129, 1000, 4097, 20003, 100_007])
+        src_map, dst_map = (leaf_mapping(g, types, 0) for _ in range(2))
+        try:
+            src_o = oracle_view(leaves, src_map, [random_field(t, n, vals) for t in types]) if n else \
+                oracle.OracleView(leaves, src_map, 0)
+            dst_o = oracle.OracleView(leaves, dst_map, n)
+        except ValueError:
+            continue  # a mapping the oracle does not take for these leaves
+        try:
+            src = device_view_of(src_o) if n else empty_device_view(leaves, src_map, 0)
+            llgb.llgb_copy_plan(src, empty_device_view(leaves, dst_map, n))
+        except llgb.LlgbError as err:
+            assert err.status == llgb.ERR_UNSUPPORTED, (src_map, dst_map, err)
+            continue
+        if n:
+            src_o.copy_to(dst_o)
+        cases.append((leaves, dst_map, n, src, dst_o))
+    assert len(cases) == 24
+    outs = [[empty_device_view(leaves, dm, n, fill=f) for leaves, dm, n, _, _ in cases]
+            for f in (0xAB, 0x5A, 0x3C, 0x77)]
+    pairs = [[(c[3], d) for c, d in zip(cases, out)] for out in outs]
+    graph_batch, stream_batch = llgb.Batch(pairs[0]), llgb.Batch(pairs[1])
+    graph_batch.launch(use_graph=True)
+    stream_batch.launch()
+    arena = llgb.Arena(max_pairs=24, slots=2)
+    arena.copy(pairs[2])
+    llgb.llgb_batch_copy_noalloc(pairs[3])
+    sync_and_check_status()
+    for how, out in zip(("graph batch", "batch", "arena", "allocation-free"), outs):
+        for (leaves, dm, n, _, dst_o), d in zip(cases, out):
+            assert_same_bytes(d, dst_o, f"{how}: {leaves} n={n} -> {dm}")
+    graph_batch.close()
+    stream_batch.close()
     arena.close()
